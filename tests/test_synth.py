@@ -1,0 +1,62 @@
+"""The seeded input generators: determinism, domain and shape."""
+import numpy as np
+
+import oracle
+import synth
+
+
+def test_deterministic_and_thread_independent():
+    a = synth.disk(200001, 5)
+    b = synth.disk(200001, 5)
+    assert np.array_equal(a, b)
+    # prefix property: point i depends only on (seed, stream, i)
+    c = synth.disk(1000, 5)
+    assert np.array_equal(a[:1000], c)
+
+
+def test_splitmix64_reference_value():
+    # SplitMix64 finaliser applied to 0 (the first output of a generator
+    # seeded with 0), a published reference value.
+    assert synth.mix64(0) == 0xE220A8397B1DCDAF
+
+
+def test_domain_and_shapes():
+    r24 = float(1 << 24)
+    sq = synth.square(100000, 1, 1 << 20)
+    assert oracle.check_domain(sq) and np.abs(sq).max() <= (1 << 20)
+    dk = synth.disk(100000, 1)
+    assert oracle.check_domain(dk)
+    assert ((dk.astype(np.float64) ** 2).sum(1) <= r24 * r24).all()
+    ga = synth.gaussian(100000, 1)
+    assert oracle.check_domain(ga)
+    s = ga.astype(np.float64).std(0)
+    assert np.all(np.abs(s / float(1 << 22) - 1) < 0.02)
+
+
+def test_near_edge_points_on_inner_side_within_one_unit():
+    poly = np.array([[0, 0], [1000003, 17], [700001, 900007], [-5, 400001]], dtype=np.int32)
+    # also an edge with many interior lattice points (gcd > 1)
+    poly2 = np.array([[0, 0], [600, 0], [600, 300], [0, 300]], dtype=np.int32)
+    for P in (poly, poly2):
+        q = synth.near_edge(20000, P, 3).astype(np.int64)
+        m = len(P)
+        on = 0
+        for x, y in q:
+            best = None
+            for k in range(m):
+                a, b = P[k].astype(np.int64), P[(k + 1) % m].astype(np.int64)
+                o = (b[0] - a[0]) * (y - a[1]) - (b[1] - a[1]) * (x - a[0])
+                d = o / np.hypot(*(b - a))
+                best = d if best is None or abs(d) < abs(best) else best
+            assert 0 <= best <= 1.0 + 1e-9
+            on += best == 0
+        assert on > 0
+
+
+def test_set_plan_log_uniform():
+    sizes, shapes = synth.set_plan(4096)
+    assert sizes.min() >= 1000 and sizes.max() <= 4_000_000
+    assert set(np.unique(shapes).tolist()) == {0, 1, 2}
+    mean = sizes.mean()
+    want = (4e6 - 1e3) / np.log(4e6 / 1e3)  # mean of a log-uniform law
+    assert abs(mean / want - 1) < 0.08
