@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the CudaPre hull pipeline on GB300 (arXiv 1405.3454).
+
+One step = one hull_compute over one synthetic set: 16-extreme search and
+polygon (Steps 1-2), strict-inside discard + compaction (Step 3), radix sort
+and monotone chain of the survivors (the hull of the remaining points).
+
+Workload: 268,435,456 lattice points uniform in the disk of radius 2^24
+(2 GiB float32 xy, seeded), the paper's circle data at HBM-bound scale.  The
+input (2 GiB) is larger than L2 (129 MB), so no L2 flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
+independent set (weak scaling, no collective on the data path).
+--impl reference times the CPU oracle on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoints/s prefilter+hull and % of HBM roofline, exact vs FP32-filtered; p99 latency"
+UNIT = "Gpoints/s"
+N_POINTS = 1 << 28
+SEED = 1405345
+WORKLOAD = ("single set of 268,435,456 points (2 GiB float32 xy), integer values uniform in a disk "
+            "of radius 2^24 centred at origin (seeded)")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("k_extremes.cu", "k_filter.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1405_3454_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per point of `kernel` from an ncu capture summarised under
+    profiles/ (a line 'TRAFFIC <kernel> <source-hash> <bytes-per-point>'),
+    or None if absent or taken on different kernel source."""
+    want = kernel_source_hash()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(pdir, fn)):
+            m = re.match(r"^TRAFFIC\s+(\S+)\s+(\S+)\s+([0-9.]+)\s*$", line.strip())
+            if m and m.group(1) == kernel and m.group(2) == want:
+                return float(m.group(3))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(n_sample: int, seed: int):
+    """The CPU oracle (as it stands, single-threaded) on the first n_sample
+    points of the workload's generator stream: (Gpoints/s, seconds)."""
+    import oracle
+    import synth
+    xy = synth.disk(n_sample, seed)
+    oracle.cudapre(xy[:1024])  # load the library outside the timing
+    t0 = time.perf_counter()
+    oracle.cudapre(xy)
+    dt = time.perf_counter() - t0
+    return n_sample / dt / 1e9, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    # Bounded samples: 2^22 points per step (a few seconds of CPU each).
+    n_sample = 1 << 22
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n_sample, SEED)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_sample(n_sample, SEED)
+        times.append(dt)
+    t = sum(times) / len(times)
+    v = n_sample / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_points_per_step": n_sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "first 2^22 points of the disk workload's generator stream per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1405_3454_gb300 as cp
+    import synth
+    from paper_1405_3454_gb300 import _build
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    cp.load()
+    n = args.n
+    host = synth.disk(n, SEED + rank)  # each rank: its own independent set
+    d_xy = torch.from_numpy(host).cuda()
+    fp32 = cp.Options(filter=cp.HULL_FILTER_FP32)
+    exact = cp.Options(filter=cp.HULL_FILTER_EXACT)
+    ws_bytes = cp.hull_workspace_bytes(n)
+    ws = cp.workspace(ws_bytes)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+
+    def step(opt):
+        code = cp.hull_compute(d_xy.data_ptr(), n, ws.data_ptr(), ws_bytes, out.data_ptr(), cnt.data_ptr(), opt, sh)
+        if code:
+            raise cp.HullError(code, "hull_compute")
+
+    def prefilter_step(opt):
+        code = cp.hull_prefilter(d_xy.data_ptr(), n, ws.data_ptr(), ws_bytes, out.data_ptr(), cnt.data_ptr(), 0,
+                                 opt, sh)
+        if code:
+            raise cp.HullError(code, "hull_prefilter")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, opt, steps, timer=None):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if timer:
+            timer.attach()
+        e0.record(stream)
+        for _ in range(steps):
+            fn(opt)
+        e1.record(stream)
+        if timer:
+            timer.detach()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / steps)
+
+    for _ in range(args.warmup):
+        step(fp32)
+    torch.cuda.synchronize()
+
+    # Headline: the FP32-filtered pipeline (bit-identical to plain exact).
+    timer = cp.StageTimer(max_calls=max(args.steps, 1))
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = cp.launch_count()
+    ms = timed(step, fp32, args.steps, timer)
+    launches = cp.launch_count() - l0
+    clk = clocks.stop()
+    stage_ms, calls = timer.read()
+    per_call = {k: v / max(calls, 1) for k, v in stage_ms.items()}
+    n_surv, n_esc = cp.read_counters(ws)
+    n_hull = int(cnt.item())
+    value = world * n / (ms * 1e-3) / 1e9
+
+    # Plain exact method (binary64 projections, int64 orientation for every edge).
+    for _ in range(2):
+        step(exact)
+    ms_exact = timed(step, exact, max(3, args.steps // 4))
+    # Prefilter alone (Steps 1-3), both forms.
+    for _ in range(2):
+        prefilter_step(fp32)
+    ms_pre = timed(prefilter_step, fp32, args.steps)
+    ms_pre_exact = timed(prefilter_step, exact, max(3, args.steps // 4))
+
+    # Roofline of the dominant single kernel of the prefilter.
+    peak, peak_kind = peaks()
+    bytes_ext = 8.0 * n
+    bytes_flt = 8.0 * n + 12.0 * n_surv
+    cand = {"k_extremes32": (per_call["extremes"], bytes_ext), "k_filter": (per_call["filter"], bytes_flt)}
+    dom = max(cand, key=lambda k: cand[k][0])
+    dms, dbytes = cand[dom]
+    achieved = dbytes / (dms * 1e-3) / 1e9
+    tpp = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": (tpp * n if tpp is not None else None),
+                "algorithmic_bytes": dbytes}
+    stages_out = {k: {"ms": per_call[k]} for k in per_call}
+    stages_out["extremes"].update({"GBps": bytes_ext / (per_call["extremes"] * 1e-3) / 1e9 if per_call["extremes"] else None})
+    stages_out["filter"].update({"GBps": bytes_flt / (per_call["filter"] * 1e-3) / 1e9 if per_call["filter"] else None})
+    pre_bytes = 16.0 * n + 12.0 * n_surv
+    prefilter = {"value": world * n / (ms_pre * 1e-3) / 1e9, "unit": UNIT, "ms": ms_pre,
+                 "hbm_frac": (16.0 * n + 4.0 * n_surv) / (ms_pre * 1e-3) / 1e9 / peak,
+                 "exact_value": world * n / (ms_pre_exact * 1e-3) / 1e9}
+
+    # End to end through the public API: pinned host input -> device, the
+    # call, the hull read back; every step.
+    pinned = torch.from_numpy(host).pin_memory()
+    host_cnt = torch.empty(1, dtype=torch.int64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 10))
+
+    def e2e_step():
+        d_xy.copy_(pinned, non_blocking=True)
+        step(fp32)
+        host_cnt.copy_(cnt, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        k = int(host_cnt.item())
+        res = out[:k].cpu()
+        return k, res
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        k, _ = e2e_step()
+        d2h += 8 + 4 * k
+    barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+    e2e = {"value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": d2h // e2e_steps}
+
+    cpu = None
+    if world == 1 and rank == 0 and not args.no_cpu:
+        ns = 1 << 25
+        v, dt = cpu_oracle_sample(ns, SEED)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first 2^25 points of the same disk generator stream (%.1f s, single thread)" % dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64+int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": n, "mode": "fp32-filtered (bit-identical to plain exact)",
+                       "angles": "cumulative 0/30/75/120", "l2": "inputs (2 GiB) larger than L2; no flush",
+                       "parallelism": "independent set per GPU" if world > 1 else "single GPU"},
+            "variants": {"plain_exact": {"value": world * n / (ms_exact * 1e-3) / 1e9, "ms_per_step": ms_exact},
+                         "fp32_filtered": {"value": value, "ms_per_step": ms},
+                         "prefilter_only": prefilter},
+            "stages_ms_per_step": stages_out,
+            "survivors": n_surv, "escalations": n_esc, "hull_vertices": n_hull,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    timer.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

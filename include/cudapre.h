@@ -1,0 +1,191 @@
+/* cudapre.h -- C ABI of the GB300 (sm_103a) implementation of the CudaPre
+ * convex-hull preprocessing method: G. Mei, "A Straightforward Preprocessing
+ * Approach for Accelerating Convex Hull Computations on the GPU",
+ * arXiv 1405.3454.
+ *
+ * The method (section 2):
+ *   Step 1  16 extreme points: min/max of x and y in the original point set
+ *           and in three rotated copies of it;
+ *   Step 2  the convex polygon of those points by Andrew's monotone chain
+ *           (the paper's correction note: reference [6] is Andrew's algorithm);
+ *   Step 3  discard every point strictly inside that polygon;
+ *   then    the convex hull of the remaining points (section 3, case (2)).
+ * Every step runs on the GPU; the host only enqueues work.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Points     float32 xy interleaved, point i at xy[2i], xy[2i+1].  The
+ *            address must be 8-byte aligned.  Coordinates must be finite,
+ *            integer-valued and within [-2^24, 2^24]; then every orientation
+ *            test is exact in int64 and every result is bit-exact.  Outside
+ *            that domain results are undefined unless options.validate is set,
+ *            in which case the call flags HULL_DEVICE_DOMAIN (see
+ *            hull_get_device_status) and produces empty results.
+ * Rotations  counter-clockwise, x' = x c - y s, y' = x s + y c, evaluated as
+ *            RN(RN(x*c) - RN(y*s)) and RN(RN(x*s) + RN(y*c)) in binary64 with
+ *            c, s the correctly rounded closed forms.  Ties go to the lowest
+ *            index.
+ * Extremes   16 slots, slot 4g+k for rotation group g (0 = original set) and
+ *            k = 0 argmin x', 1 argmax x', 2 argmin y', 3 argmax y'.
+ * Inside     strictly inside: points on the polygon boundary remain.  A
+ *            polygon with fewer than 3 vertices discards nothing.
+ * Hull       strictly convex (collinear boundary points are not vertices),
+ *            counter-clockwise from the lexicographically smallest (x, y)
+ *            vertex; among equal coordinates the lowest index is reported.
+ * Memory     the caller owns every buffer (inputs, outputs, workspace), all in
+ *            device memory unless stated.  The library allocates nothing.
+ * Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *            Calls are asynchronous: they return after enqueueing.  Counts
+ *            are written to device memory.  A workspace must not be shared by
+ *            calls that may overlap on the GPU; distinct workspaces are
+ *            independent and may be used from different host threads.
+ * Errors     the return value reports argument and launch errors; conditions
+ *            found on the device are recorded in the workspace and read with
+ *            hull_get_device_status.
+ */
+#ifndef CUDAPRE_H
+#define CUDAPRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hull_status {
+  HULL_OK = 0,
+  HULL_ERR_INVALID_ARG = 1, /* null pointer, negative or too large size, misalignment */
+  HULL_ERR_DOMAIN = 2,      /* reported by hull_get_device_status: input outside the domain */
+  HULL_ERR_WORKSPACE = 3,   /* workspace smaller than the matching *_workspace_bytes */
+  HULL_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+  HULL_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  HULL_ERR_BUDGET = 6,      /* request larger than the configured memory budget */
+  HULL_ERR_UNSUPPORTED = 7  /* option value not supported */
+} hull_status;
+
+/* Angle tables for Step 1 (section 2).  CUMULATIVE reads "rotate in 30, 45
+ * and 45 degrees" as 30, 75 and 120 degrees from the original set; ABSOLUTE
+ * is the 30, 45, 60 degrees of Figure 1 and section 5. */
+#define HULL_ANGLES_CUMULATIVE 0
+#define HULL_ANGLES_ABSOLUTE 1
+
+/* Arithmetic of the inside test and of the extreme search.
+ * EXACT: binary64 projections for every point and an int64 orientation test
+ *        for every edge -- the plain method.
+ * FP32:  float32 projections and orientation tests with a static error
+ *        bound; only decisions inside the bound are escalated to binary64 /
+ *        int64.  Results are bit-identical to EXACT. */
+#define HULL_FILTER_EXACT 0
+#define HULL_FILTER_FP32 1
+
+typedef struct hull_options {
+  int32_t angles;        /* HULL_ANGLES_*; default CUMULATIVE */
+  int32_t filter;        /* HULL_FILTER_*; default FP32 */
+  int32_t validate;      /* nonzero: check the input domain on the device first */
+  int32_t block;         /* threads per block of the streaming kernels; 0 = tuned */
+  int32_t grid;          /* blocks of the streaming kernels; 0 = tuned */
+  int32_t reserved[11];  /* must be zero */
+} hull_options;
+
+/* Device-side condition bits (hull_get_device_status). */
+#define HULL_DEVICE_DOMAIN 1u   /* validate found a coordinate outside the domain */
+#define HULL_DEVICE_TIMEOUT 2u  /* a bounded wait expired */
+#define HULL_DEVICE_OVERFLOW 4u /* an internal capacity was exceeded */
+
+/* Fills *opt with the defaults (cumulative angles, FP32 filter, no validation,
+ * tuned launch shapes). */
+void hull_default_options(hull_options* opt);
+
+/* Bytes of workspace needed by hull_prefilter for n points (opt may be NULL
+ * for the defaults).  The workspace needs no initialisation. */
+size_t hull_prefilter_workspace_bytes(int64_t n, const hull_options* opt);
+
+/* Bytes of workspace needed by hull_compute for n points. */
+size_t hull_workspace_bytes(int64_t n, const hull_options* opt);
+
+/* Steps 1-3 of section 2 on one point set.
+ *   d_xy             n points (see Points above); n in [0, 2^32 - 1].
+ *   d_ws, ws_bytes   workspace of at least hull_prefilter_workspace_bytes(n).
+ *   d_survivor_idx   room for n uint32: indices of the points NOT strictly
+ *                    inside the polygon of the extremes, in unspecified order
+ *                    (compare as a set).
+ *   d_n_survivors    one int64: the number of survivors.
+ *   d_extreme_idx    16 uint32 (may be NULL): the extreme indices, see
+ *                    Extremes above; all 0xFFFFFFFF when n == 0.
+ * The polygon stays in the workspace (hull_read_polygon). */
+hull_status hull_prefilter(const float* d_xy, int64_t n, void* d_ws, size_t ws_bytes,
+                           uint32_t* d_survivor_idx, int64_t* d_n_survivors,
+                           uint32_t* d_extreme_idx, const hull_options* opt, void* stream);
+
+/* The whole method on one point set: Steps 1-3, compaction of the survivors,
+ * then the hull of the survivors by a device radix sort and Andrew's
+ * monotone chain (section 3, case (2)).
+ *   d_ws             at least hull_workspace_bytes(n).
+ *   d_hull_idx       room for n uint32: hull vertex indices, see Hull above.
+ *   d_n_hull         one int64: the number of hull vertices (0 when n == 0). */
+hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_bytes,
+                         uint32_t* d_hull_idx, int64_t* d_n_hull,
+                         const hull_options* opt, void* stream);
+
+/* Number of survivors and of FP32 decisions escalated to the exact test by
+ * the last hull_prefilter / hull_compute on this workspace.  Synchronises the
+ * stream.  Either output pointer may be NULL (host memory). */
+hull_status hull_read_counters(const void* d_ws, int64_t* h_n_survivors,
+                               int64_t* h_n_escalated, void* stream);
+
+/* The Step-2 polygon of the last call on this workspace: *h_m vertices,
+ * h_xy[2k], h_xy[2k+1] their integer coordinates counter-clockwise from the
+ * lexicographic minimum (room for 32 int32), h_idx[k] their point indices
+ * (room for 16 uint32; may be NULL).  Synchronises the stream (host memory). */
+hull_status hull_read_polygon(const void* d_ws, int32_t* h_m, int32_t* h_xy,
+                              uint32_t* h_idx, void* stream);
+
+/* Device-side condition bits (HULL_DEVICE_*) recorded by the last call on this
+ * workspace; synchronises the stream.  Returns HULL_OK when no bit is set,
+ * else the matching error code. */
+hull_status hull_get_device_status(const void* d_ws, uint32_t* h_bits, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* hull_strerror(hull_status s);
+
+/* The projection constants this library uses: out[0..3] = sqrt(3)/2,
+ * (sqrt(6)-sqrt(2))/4, (sqrt(6)+sqrt(2))/4, sqrt(2)/2 (host memory). */
+void hull_constants(double* out);
+
+/* ABI version of this header. */
+int32_t hull_abi_version(void);
+
+/* ---- Instrumentation (not part of the method) -------------------------- */
+
+/* Stages of one call, in launch order: domain check, extremes + polygon
+ * (Steps 1-2), inside test + compaction (Step 3), sort of the survivors,
+ * monotone chain of the survivors. */
+#define HULL_STAGES 5
+
+/* Opaque stage timer: CUDA events recorded on the call's stream at every
+ * stage boundary (host objects; no device memory). */
+typedef struct hull_timer hull_timer;
+
+/* Creates a timer with room for max_calls calls; NULL on failure. */
+hull_timer* hull_timer_create(int32_t max_calls);
+void hull_timer_destroy(hull_timer* t);
+
+/* Subsequent hull_prefilter / hull_compute calls made by this host thread
+ * record their stage boundaries into t (NULL detaches).  Calls beyond the
+ * timer's capacity are not recorded. */
+void hull_timer_attach(hull_timer* t);
+
+/* Waits for the recorded events, writes the per-stage time summed over the
+ * recorded calls to h_ms[HULL_STAGES] (milliseconds) and the number of
+ * recorded calls to *h_calls, then clears the timer. */
+hull_status hull_timer_read(hull_timer* t, float* h_ms, int32_t* h_calls);
+
+/* Number of kernels this library has enqueued in this process so far. */
+int64_t hull_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUDAPRE_H */

@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so with g++ -O2 -ffp-contract=off (no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-shared", "-fPIC",
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-Wno-stringop-overflow", "-shared", "-fPIC",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB

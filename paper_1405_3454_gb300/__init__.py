@@ -1,0 +1,286 @@
+"""GB300-native CudaPre: convex-hull preprocessing on the GPU (arXiv 1405.3454).
+
+A thin ctypes binding over the C ABI in ``include/cudapre.h`` (library
+``libcudapre.so`` built in-tree by ``_build.build()``).  This module only
+marshals arguments: every step of the method runs in the CUDA kernels.
+PyTorch provides device memory and streams.  There is no CPU fallback: if the
+library is missing every call raises.
+
+Entry points (same names as the C ABI):
+  hull_prefilter  Steps 1-3 of section 2: survivors of the 16-extreme filter.
+  hull_compute    the whole method: the convex hull via the filter.
+Convenience wrappers ``prefilter`` and ``compute`` allocate outputs and a
+workspace with torch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcudapre.so")
+
+HULL_OK = 0
+HULL_ANGLES_CUMULATIVE = 0
+HULL_ANGLES_ABSOLUTE = 1
+HULL_FILTER_EXACT = 0
+HULL_FILTER_FP32 = 1
+HULL_DEVICE_DOMAIN = 1
+HULL_DEVICE_TIMEOUT = 2
+HULL_DEVICE_OVERFLOW = 4
+NONE_IDX = 0xFFFFFFFF
+
+# Exported symbols declared in include/cudapre.h.
+ABI_SYMBOLS = (
+    "hull_default_options", "hull_prefilter_workspace_bytes", "hull_workspace_bytes",
+    "hull_prefilter", "hull_compute", "hull_read_counters", "hull_read_polygon",
+    "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version",
+    "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
+)
+HULL_STAGES = 5
+STAGE_NAMES = ("validate", "extremes", "filter", "sort", "chain")
+
+
+class HullOptions(ctypes.Structure):
+    _fields_ = [("angles", ctypes.c_int32), ("filter", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+
+
+class HullError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s" % (where, strerror(code)))
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libcudapre.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libcudapre.so not built (run __graft_entry__.build() or "
+                           "paper_1405_3454_gb300._build.build()): %s" % p)
+    lib = ctypes.CDLL(p)
+    P, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+    OP = ctypes.POINTER(HullOptions)
+    st = ctypes.c_int
+    lib.hull_default_options.argtypes = [OP]
+    lib.hull_default_options.restype = None
+    lib.hull_prefilter_workspace_bytes.argtypes = [i64, OP]
+    lib.hull_prefilter_workspace_bytes.restype = sz
+    lib.hull_workspace_bytes.argtypes = [i64, OP]
+    lib.hull_workspace_bytes.restype = sz
+    lib.hull_prefilter.argtypes = [P, i64, P, sz, P, P, P, OP, P]
+    lib.hull_prefilter.restype = st
+    lib.hull_compute.argtypes = [P, i64, P, sz, P, P, OP, P]
+    lib.hull_compute.restype = st
+    lib.hull_read_counters.argtypes = [P, P, P, P]
+    lib.hull_read_counters.restype = st
+    lib.hull_read_polygon.argtypes = [P, P, P, P, P]
+    lib.hull_read_polygon.restype = st
+    lib.hull_get_device_status.argtypes = [P, P, P]
+    lib.hull_get_device_status.restype = st
+    lib.hull_strerror.argtypes = [st]
+    lib.hull_strerror.restype = ctypes.c_char_p
+    lib.hull_constants.argtypes = [P]
+    lib.hull_constants.restype = None
+    lib.hull_abi_version.argtypes = []
+    lib.hull_abi_version.restype = ctypes.c_int32
+    lib.hull_timer_create.argtypes = [ctypes.c_int32]
+    lib.hull_timer_create.restype = P
+    lib.hull_timer_destroy.argtypes = [P]
+    lib.hull_timer_destroy.restype = None
+    lib.hull_timer_attach.argtypes = [P]
+    lib.hull_timer_attach.restype = None
+    lib.hull_timer_read.argtypes = [P, P, P]
+    lib.hull_timer_read.restype = st
+    lib.hull_launch_count.argtypes = []
+    lib.hull_launch_count.restype = ctypes.c_int64
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().hull_strerror(code).decode()
+    except Exception:
+        return "hull_status %d" % code
+
+
+def _check(code: int, where: str):
+    if code != HULL_OK:
+        raise HullError(code, where)
+
+
+@dataclass
+class Options:
+    angles: int = HULL_ANGLES_CUMULATIVE
+    filter: int = HULL_FILTER_FP32
+    validate: bool = False
+    block: int = 0
+    grid: int = 0
+
+    def c(self) -> HullOptions:
+        o = HullOptions()
+        load().hull_default_options(ctypes.byref(o))
+        o.angles, o.filter, o.validate = int(self.angles), int(self.filter), int(bool(self.validate))
+        o.block, o.grid = int(self.block), int(self.grid)
+        return o
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check_points(xy):
+    import torch
+    if not isinstance(xy, torch.Tensor) or not xy.is_cuda:
+        raise TypeError("xy must be a CUDA torch.Tensor")
+    if xy.dtype != torch.float32 or xy.dim() != 2 or xy.shape[1] != 2 or not xy.is_contiguous():
+        raise ValueError("xy must be a contiguous float32 tensor of shape [n, 2]")
+    return int(xy.shape[0])
+
+
+# --------------------------------------------------------------------------
+# C-ABI mirrors (raw pointers as ints, stream handle as int).
+
+def hull_prefilter_workspace_bytes(n: int, opt: Options | None = None) -> int:
+    return int(load().hull_prefilter_workspace_bytes(n, ctypes.byref((opt or Options()).c())))
+
+
+def hull_workspace_bytes(n: int, opt: Options | None = None) -> int:
+    return int(load().hull_workspace_bytes(n, ctypes.byref((opt or Options()).c())))
+
+
+def hull_prefilter(d_xy: int, n: int, d_ws: int, ws_bytes: int, d_survivor_idx: int, d_n_survivors: int,
+                   d_extreme_idx: int, opt: Options | None, stream: int) -> int:
+    o = (opt or Options()).c()
+    return load().hull_prefilter(d_xy, n, d_ws, ws_bytes, d_survivor_idx, d_n_survivors, d_extreme_idx or None,
+                                 ctypes.byref(o), stream or None)
+
+
+def hull_compute(d_xy: int, n: int, d_ws: int, ws_bytes: int, d_hull_idx: int, d_n_hull: int,
+                 opt: Options | None, stream: int) -> int:
+    o = (opt or Options()).c()
+    return load().hull_compute(d_xy, n, d_ws, ws_bytes, d_hull_idx, d_n_hull, ctypes.byref(o), stream or None)
+
+
+# --------------------------------------------------------------------------
+# Tensor-level wrappers.
+
+def workspace(nbytes: int, device=None):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def prefilter(xy, opt: Options | None = None, ws=None, stream=None):
+    """Steps 1-3 on one set.  Returns (survivor_idx int32 [n] (uint32 bits),
+    n_survivors int64 [1], extreme_idx int32 [16] (uint32 bits), ws).
+    Only the first n_survivors entries of survivor_idx are defined."""
+    import torch
+    n = _check_points(xy)
+    opt = opt or Options()
+    need = hull_prefilter_workspace_bytes(n, opt)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, xy.device)
+    surv = torch.empty(max(n, 1), dtype=torch.int32, device=xy.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=xy.device)
+    ext = torch.empty(16, dtype=torch.int32, device=xy.device)
+    _check(hull_prefilter(_ptr(xy), n, _ptr(ws), ws.numel(), _ptr(surv), _ptr(cnt), _ptr(ext), opt,
+                          _stream_handle(stream)), "hull_prefilter")
+    return surv, cnt, ext, ws
+
+
+def compute(xy, opt: Options | None = None, ws=None, stream=None):
+    """The whole method on one set.  Returns (hull_idx int32 [n] (uint32 bits),
+    n_hull int64 [1], ws).  Only the first n_hull entries are defined."""
+    import torch
+    n = _check_points(xy)
+    opt = opt or Options()
+    need = hull_workspace_bytes(n, opt)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, xy.device)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=xy.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=xy.device)
+    _check(hull_compute(_ptr(xy), n, _ptr(ws), ws.numel(), _ptr(out), _ptr(cnt), opt, _stream_handle(stream)),
+           "hull_compute")
+    return out, cnt, ws
+
+
+def read_counters(ws, stream=None):
+    ns, ne = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().hull_read_counters(_ptr(ws), ctypes.byref(ns), ctypes.byref(ne), _stream_handle(stream)),
+           "hull_read_counters")
+    return int(ns.value), int(ne.value)
+
+
+def read_polygon(ws, stream=None):
+    """(m, xy [m][2] list, vertex point indices [m] list) of the last call's Step-2 polygon."""
+    m = ctypes.c_int32(0)
+    xy = (ctypes.c_int32 * 32)()
+    idx = (ctypes.c_uint32 * 16)()
+    _check(load().hull_read_polygon(_ptr(ws), ctypes.byref(m), xy, idx, _stream_handle(stream)),
+           "hull_read_polygon")
+    k = int(m.value)
+    return k, [[xy[2 * i], xy[2 * i + 1]] for i in range(k)], [int(idx[i]) for i in range(k)]
+
+
+def device_status(ws, stream=None):
+    bits = ctypes.c_uint32(0)
+    code = load().hull_get_device_status(_ptr(ws), ctypes.byref(bits), _stream_handle(stream))
+    return int(code), int(bits.value)
+
+
+def constants():
+    arr = (ctypes.c_double * 4)()
+    load().hull_constants(arr)
+    return {"s3": arr[0], "c75": arr[1], "s75": arr[2], "h": arr[3]}
+
+
+def as_index(t, count=None):
+    """uint32 bits stored in an int32 tensor -> int64 indices (host numpy)."""
+    import numpy as np
+    a = t.cpu().numpy().view(np.uint32).astype(np.int64)
+    return a if count is None else a[: int(count)]
+
+
+class StageTimer:
+    """Per-stage device time of the calls made on this host thread while attached."""
+
+    def __init__(self, max_calls: int = 256):
+        self._t = load().hull_timer_create(max_calls)
+        if not self._t:
+            raise RuntimeError("hull_timer_create failed")
+
+    def attach(self):
+        load().hull_timer_attach(self._t)
+
+    def detach(self):
+        load().hull_timer_attach(None)
+
+    def read(self):
+        """(dict stage -> total ms, number of recorded calls); clears the timer."""
+        ms = (ctypes.c_float * HULL_STAGES)()
+        calls = ctypes.c_int32(0)
+        _check(load().hull_timer_read(self._t, ms, ctypes.byref(calls)), "hull_timer_read")
+        return {STAGE_NAMES[i]: float(ms[i]) for i in range(HULL_STAGES)}, int(calls.value)
+
+    def close(self):
+        if self._t:
+            load().hull_timer_destroy(self._t)
+            self._t = None
+
+
+def launch_count() -> int:
+    return int(load().hull_launch_count())

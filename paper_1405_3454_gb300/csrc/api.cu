@@ -1,0 +1,310 @@
+// api.cu -- the C ABI (include/cudapre.h): argument checks, workspace layout
+// and the launch sequence of each entry point.  Host code only enqueues; no
+// step of the method runs on the host.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cudapre {
+
+int device_sm_count() {
+  static int cache[64];
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+}  // namespace cudapre
+
+// Stage timer (instrumentation only): CUDA events at stage boundaries.
+struct hull_timer {
+  int cap = 0;
+  int calls = 0;
+  std::vector<cudaEvent_t> ev;  // cap x (HULL_STAGES + 1)
+};
+
+namespace cudapre {
+namespace {
+thread_local hull_timer* g_timer = nullptr;
+
+// Marks boundary `b` (0..HULL_STAGES) of the current call.
+void mark(int b, cudaStream_t st) {
+  hull_timer* t = g_timer;
+  if (!t || t->calls >= t->cap) return;
+  cudaEventRecord(t->ev[(size_t)t->calls * (HULL_STAGES + 1) + b], st);
+  if (b == HULL_STAGES) ++t->calls;
+}
+
+constexpr int64_t MAX_N = 0xFFFFFFFFll;  // indices are uint32
+constexpr int64_t MAX_BLOCKS = 4096;     // per-block partials of the extreme search
+
+struct Layout {
+  size_t header = 0, blockres = 0, keys_a = 0, vals_a = 0, keys_b = 0, vals_b = 0, tilecnt = 0,
+         cnt = 0, total = 0;
+};
+
+Layout layout(int64_t n, bool full) {
+  Layout L;
+  size_t off = HEADER_BYTES;
+  L.header = 0;
+  L.blockres = off;
+  off += align_up(sizeof(BlockBest) * NSLOT * MAX_BLOCKS, 256);
+  if (full) {
+    const int64_t cap = std::max<int64_t>(n, 1);
+    L.keys_a = off; off += align_up(8 * (size_t)cap, 256);
+    L.vals_a = off; off += align_up(4 * (size_t)cap, 256);
+    L.keys_b = off; off += align_up(8 * (size_t)cap, 256);
+    L.vals_b = off; off += align_up(4 * (size_t)cap, 256);
+    L.tilecnt = off; off += align_up(4 * 256 * (size_t)sort_tiles(cap), 256);
+    const int64_t nch0 = (cap + CHAIN_C0 - 1) / CHAIN_C0;
+    L.cnt = off; off += align_up(4 * 4 * (size_t)nch0, 256);
+  }
+  L.total = off;
+  return L;
+}
+
+hull_status check_opts(const hull_options* o) {
+  if (!o) return HULL_OK;
+  if (o->angles != HULL_ANGLES_CUMULATIVE && o->angles != HULL_ANGLES_ABSOLUTE) return HULL_ERR_UNSUPPORTED;
+  if (o->filter != HULL_FILTER_EXACT && o->filter != HULL_FILTER_FP32) return HULL_ERR_UNSUPPORTED;
+  if (o->block < 0 || o->grid < 0 || o->grid > MAX_BLOCKS) return HULL_ERR_INVALID_ARG;
+  for (int k = 0; k < 11; ++k) if (o->reserved[k] != 0) return HULL_ERR_UNSUPPORTED;
+  return HULL_OK;
+}
+
+hull_options opts_or_default(const hull_options* o) {
+  hull_options d;
+  hull_default_options(&d);
+  return o ? *o : d;
+}
+
+hull_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HULL_OK : HULL_ERR_CUDA; }
+
+#define HULL_TRY(expr)                               \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return HULL_ERR_CUDA;     \
+  } while (0)
+
+// Steps 1-3 shared by hull_prefilter and hull_compute.
+hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& L,
+                          uint32_t* surv_idx, unsigned long long* surv_key, uint32_t* ext_out,
+                          const hull_options& o, cudaStream_t st) {
+  WsHeader* h = reinterpret_cast<WsHeader*>(ws + L.header);
+  mark(0, st);
+  HULL_TRY(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
+  if (o.validate) HULL_TRY(launch_validate(d_xy, n, h, st));
+  mark(1, st);
+  HULL_TRY(launch_extremes(d_xy, n, o.angles, o.filter, h,
+                           reinterpret_cast<BlockBest*>(ws + L.blockres), o.grid, o.block, ext_out, st));
+  mark(2, st);
+  HULL_TRY(launch_filter(d_xy, n, o.filter, h, surv_idx, surv_key, o.grid, o.block, st));
+  mark(3, st);
+  return HULL_OK;
+}
+
+hull_status check_common(const float* d_xy, int64_t n, void* d_ws) {
+  if (n < 0 || n > MAX_N) return HULL_ERR_INVALID_ARG;
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return HULL_ERR_INVALID_ARG;
+  if (n > 0 && (!d_xy || (reinterpret_cast<uintptr_t>(d_xy) & 7u))) return HULL_ERR_INVALID_ARG;
+  return HULL_OK;
+}
+
+}  // namespace
+}  // namespace cudapre
+
+using namespace cudapre;
+
+extern "C" {
+
+int32_t hull_abi_version(void) { return 1; }
+
+void hull_default_options(hull_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->angles = HULL_ANGLES_CUMULATIVE;
+  opt->filter = HULL_FILTER_FP32;
+}
+
+void hull_constants(double* out) {
+  if (!out) return;
+  out[0] = K_S3;
+  out[1] = K_C75;
+  out[2] = K_S75;
+  out[3] = K_H;
+}
+
+const char* hull_strerror(hull_status s) {
+  switch (s) {
+    case HULL_OK: return "HULL_OK";
+    case HULL_ERR_INVALID_ARG: return "HULL_ERR_INVALID_ARG: invalid argument";
+    case HULL_ERR_DOMAIN: return "HULL_ERR_DOMAIN: input outside the integer [-2^24, 2^24] domain";
+    case HULL_ERR_WORKSPACE: return "HULL_ERR_WORKSPACE: workspace too small";
+    case HULL_ERR_CUDA: return "HULL_ERR_CUDA: CUDA runtime or launch error";
+    case HULL_ERR_TIMEOUT: return "HULL_ERR_TIMEOUT: a bounded device wait expired";
+    case HULL_ERR_BUDGET: return "HULL_ERR_BUDGET: request exceeds the memory budget";
+    case HULL_ERR_UNSUPPORTED: return "HULL_ERR_UNSUPPORTED: unsupported option";
+  }
+  return "unknown hull_status";
+}
+
+size_t hull_prefilter_workspace_bytes(int64_t n, const hull_options* opt) {
+  (void)opt;
+  return layout(std::max<int64_t>(n, 0), false).total;
+}
+
+size_t hull_workspace_bytes(int64_t n, const hull_options* opt) {
+  (void)opt;
+  return layout(std::max<int64_t>(n, 0), true).total;
+}
+
+hull_status hull_prefilter(const float* d_xy, int64_t n, void* d_ws, size_t ws_bytes,
+                           uint32_t* d_survivor_idx, int64_t* d_n_survivors,
+                           uint32_t* d_extreme_idx, const hull_options* opt, void* stream) {
+  hull_status s = check_common(d_xy, n, d_ws);
+  if (s != HULL_OK) return s;
+  if ((s = check_opts(opt)) != HULL_OK) return s;
+  if (!d_n_survivors || (n > 0 && !d_survivor_idx)) return HULL_ERR_INVALID_ARG;
+  const Layout L = layout(n, false);
+  if (ws_bytes < L.total) return HULL_ERR_WORKSPACE;
+  const hull_options o = opts_or_default(opt);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(d_ws);
+  s = run_prefilter(d_xy, n, ws, L, d_survivor_idx, nullptr, d_extreme_idx, o, st);
+  if (s != HULL_OK) return s;
+  s = cuda_status(launch_copy_count(reinterpret_cast<WsHeader*>(ws), d_n_survivors, st));
+  mark(4, st);
+  mark(5, st);
+  return s;
+}
+
+hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_bytes,
+                         uint32_t* d_hull_idx, int64_t* d_n_hull, const hull_options* opt,
+                         void* stream) {
+  hull_status s = check_common(d_xy, n, d_ws);
+  if (s != HULL_OK) return s;
+  if ((s = check_opts(opt)) != HULL_OK) return s;
+  if (!d_n_hull || (n > 0 && !d_hull_idx)) return HULL_ERR_INVALID_ARG;
+  const Layout L = layout(n, true);
+  if (ws_bytes < L.total) return HULL_ERR_WORKSPACE;
+  const hull_options o = opts_or_default(opt);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(d_ws);
+  WsHeader* h = reinterpret_cast<WsHeader*>(ws);
+  auto* ka = reinterpret_cast<unsigned long long*>(ws + L.keys_a);
+  auto* va = reinterpret_cast<uint32_t*>(ws + L.vals_a);
+  auto* kb = reinterpret_cast<unsigned long long*>(ws + L.keys_b);
+  auto* vb = reinterpret_cast<uint32_t*>(ws + L.vals_b);
+  s = run_prefilter(d_xy, n, ws, L, va, ka, nullptr, o, st);
+  if (s != HULL_OK) return s;
+  const int64_t cap = std::max<int64_t>(n, 1);
+  HULL_TRY(launch_sort(cap, h, ka, va, kb, vb, reinterpret_cast<uint32_t*>(ws + L.tilecnt), st));
+  mark(4, st);
+  // sorted data in (kb, vb); the upper chains go to (ka, va)
+  HULL_TRY(launch_chain(cap, h, kb, vb, ka, va, reinterpret_cast<uint32_t*>(ws + L.cnt), d_hull_idx,
+                        d_n_hull, st));
+  mark(5, st);
+  return HULL_OK;
+}
+
+hull_status hull_read_counters(const void* d_ws, int64_t* h_n_survivors, int64_t* h_n_escalated,
+                               void* stream) {
+  if (!d_ws) return HULL_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader hh;
+  HULL_TRY(cudaMemcpyAsync(&hh, d_ws, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
+  HULL_TRY(cudaStreamSynchronize(st));
+  if (h_n_survivors) *h_n_survivors = (int64_t)hh.n_surv;
+  if (h_n_escalated) *h_n_escalated = (int64_t)hh.n_escalated;
+  return HULL_OK;
+}
+
+hull_status hull_read_polygon(const void* d_ws, int32_t* h_m, int32_t* h_xy, uint32_t* h_idx,
+                              void* stream) {
+  if (!d_ws || !h_m || !h_xy) return HULL_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader hh;
+  HULL_TRY(cudaMemcpyAsync(&hh, d_ws, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
+  HULL_TRY(cudaStreamSynchronize(st));
+  *h_m = hh.poly.m;
+  for (int k = 0; k < hh.poly.m && k < MAXV; ++k) {
+    h_xy[2 * k] = hh.poly.vx[k];
+    h_xy[2 * k + 1] = hh.poly.vy[k];
+    if (h_idx) h_idx[k] = hh.poly.vidx[k];
+  }
+  return HULL_OK;
+}
+
+hull_status hull_get_device_status(const void* d_ws, uint32_t* h_bits, void* stream) {
+  if (!d_ws) return HULL_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t bits = 0;
+  HULL_TRY(cudaMemcpyAsync(&bits, d_ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  HULL_TRY(cudaStreamSynchronize(st));
+  if (h_bits) *h_bits = bits;
+  if (bits & HULL_DEVICE_DOMAIN) return HULL_ERR_DOMAIN;
+  if (bits & HULL_DEVICE_TIMEOUT) return HULL_ERR_TIMEOUT;
+  if (bits) return HULL_ERR_CUDA;
+  return HULL_OK;
+}
+
+hull_timer* hull_timer_create(int32_t max_calls) {
+  if (max_calls <= 0) return nullptr;
+  hull_timer* t = new hull_timer();
+  t->cap = max_calls;
+  t->ev.resize((size_t)max_calls * (HULL_STAGES + 1));
+  for (auto& e : t->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+      hull_timer_destroy(t);
+      return nullptr;
+    }
+  }
+  return t;
+}
+
+void hull_timer_destroy(hull_timer* t) {
+  if (!t) return;
+  if (g_timer == t) g_timer = nullptr;
+  for (auto e : t->ev) if (e) cudaEventDestroy(e);
+  delete t;
+}
+
+void hull_timer_attach(hull_timer* t) { g_timer = t; }
+
+hull_status hull_timer_read(hull_timer* t, float* h_ms, int32_t* h_calls) {
+  if (!t || !h_ms) return HULL_ERR_INVALID_ARG;
+  for (int s = 0; s < HULL_STAGES; ++s) h_ms[s] = 0.0f;
+  for (int c = 0; c < t->calls; ++c) {
+    cudaEvent_t* e = &t->ev[(size_t)c * (HULL_STAGES + 1)];
+    HULL_TRY(cudaEventSynchronize(e[HULL_STAGES]));
+    for (int s = 0; s < HULL_STAGES; ++s) {
+      float ms = 0.0f;
+      HULL_TRY(cudaEventElapsedTime(&ms, e[s], e[s + 1]));
+      h_ms[s] += ms;
+    }
+  }
+  if (h_calls) *h_calls = t->calls;
+  t->calls = 0;
+  return HULL_OK;
+}
+
+int64_t hull_launch_count(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"

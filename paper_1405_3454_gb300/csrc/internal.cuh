@@ -1,0 +1,134 @@
+// internal.cuh -- device-side layout, constants and helpers shared by the
+// kernels of the CudaPre implementation (arXiv 1405.3454).  Not part of the
+// public ABI (include/cudapre.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cudapre.h"
+
+namespace cudapre {
+
+// ----------------------------------------------------------------------------
+// Projection constants: correctly rounded closed forms (section 2, Step 1).
+//   K_S3 = sqrt(3)/2, K_C75 = (sqrt(6)-sqrt(2))/4, K_S75 = (sqrt(6)+sqrt(2))/4,
+//   K_H = sqrt(2)/2.  cos(radians(t)) would be off by one ulp for 30 degrees.
+constexpr double K_S3 = 0x1.bb67ae8584caap-1;
+constexpr double K_C75 = 0x1.0907dc1930690p-2;
+constexpr double K_S75 = 0x1.ee8dd4748bf15p-1;
+constexpr double K_H = 0x1.6a09e667f3bcdp-1;
+constexpr float F_S3 = (float)K_S3;
+constexpr float F_C75 = (float)K_C75;
+constexpr float F_S75 = (float)K_S75;
+constexpr float F_H = (float)K_H;
+
+// Error bound of the float32 projections against the binary64 definition.
+// For |x|, |y| <= 2^24 every float32 form used below is within 2.5 of the
+// binary64 value (coefficient rounding <= 0.5 + 0.5, product rounding <= 0.5,
+// final rounding <= 1); E_PROJ = 8 leaves a factor of three.  Two candidates
+// whose float32 scores differ by more than BAND = 2 * E_PROJ are ordered by
+// their float32 scores; otherwise the binary64 definition decides.
+constexpr float E_PROJ = 8.0f;
+constexpr float BAND = 2.0f * E_PROJ;
+
+constexpr int MAXV = 16;          // polygon vertices (16 extremes at most)
+constexpr int NSLOT = 16;         // extreme slots
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr int32_t COORD_MAX = 1 << 24;
+
+// ----------------------------------------------------------------------------
+// Step-2 polygon as the inside test consumes it.
+struct Edge {
+  float A, B, C, E;     // float32 s = fma(A, px, fma(B, py, C)), |s - orient| <= E
+  int32_t ax, ay;       // exact tail vertex
+  int32_t dx, dy;       // exact edge vector
+};
+
+struct Poly {
+  int32_t m;            // vertex count (0..16); < 3 discards nothing
+  int32_t pad_[3];
+  float box[4];         // closed inner box x0, x1, y0, y1 (integer-valued);
+                        // every point of it is strictly inside; x0 > x1 if empty
+  int32_t vx[MAXV], vy[MAXV];
+  uint32_t vidx[MAXV];  // point index of each vertex
+  uint32_t ext[NSLOT];  // the 16 extreme indices (slot order of the ABI)
+  Edge e[MAXV];
+};
+
+// Per-block partial result of the extreme search: binary64 score (sign
+// applied so that larger is better) and point index.
+struct BlockBest {
+  double s;
+  uint32_t idx;
+  uint32_t pad_;
+};
+
+// Workspace header (offset 0 of every workspace); zeroed by each call.
+struct WsHeader {
+  uint32_t status;        // HULL_DEVICE_* bits
+  uint32_t done_blocks;   // last-block-done counter of the extreme search
+  unsigned long long n_surv;      // survivors written by the inside test
+  unsigned long long n_escalated; // float32 decisions escalated to int64
+  unsigned long long pad0_;
+  uint32_t hist[8][256];  // radix-sort digit histograms (all passes)
+  Poly poly;
+};
+
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t HEADER_BYTES = align_up(sizeof(WsHeader), 256);
+
+// ----------------------------------------------------------------------------
+// Exact helpers.
+
+__host__ __device__ inline long long orient64(long long ax, long long ay, long long bx,
+                                              long long by, long long px, long long py) {
+  return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+// Sort key of an integer point: x and y shifted to [0, 2^25] and packed
+// (x in bits 26..51, y in bits 0..25), so key order is (x, y) order.
+__host__ __device__ inline unsigned long long point_key(int32_t ix, int32_t iy) {
+  return ((unsigned long long)(uint32_t)(ix + COORD_MAX) << 26) |
+         (unsigned long long)(uint32_t)(iy + COORD_MAX);
+}
+__host__ __device__ inline int32_t key_x(unsigned long long k) {
+  return (int32_t)(k >> 26) - COORD_MAX;
+}
+__host__ __device__ inline int32_t key_y(unsigned long long k) {
+  return (int32_t)(k & ((1ull << 26) - 1)) - COORD_MAX;
+}
+
+// ----------------------------------------------------------------------------
+// Launch shapes and per-device facts.
+int device_sm_count();
+
+// Process-wide count of kernels enqueued by this library (instrumentation).
+void count_launches(int k);
+
+// Launchers (one per translation unit); all enqueue on `st`.
+cudaError_t launch_validate(const float* xy, int64_t n, WsHeader* h, cudaStream_t st);
+cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, WsHeader* h,
+                            BlockBest* blockres, int grid, int block, uint32_t* ext_out,
+                            cudaStream_t st);
+cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, uint32_t* surv_idx,
+                          unsigned long long* surv_key, int grid, int block, cudaStream_t st);
+cudaError_t launch_sort(int64_t cap, WsHeader* h, unsigned long long* keys_a, uint32_t* vals_a,
+                        unsigned long long* keys_b, uint32_t* vals_b, uint32_t* tilecnt,
+                        cudaStream_t st);
+cudaError_t launch_chain(int64_t cap, WsHeader* h, unsigned long long* keys_s, uint32_t* vals_s,
+                         unsigned long long* keys_u, uint32_t* vals_u, uint32_t* cnt,
+                         uint32_t* out_idx, int64_t* out_n, cudaStream_t st);
+cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st);
+
+// Sizes used by the sort and chain stages.
+constexpr int SORT_TILE = 4096;           // elements per sort tile
+constexpr int SORT_PASSES = 7;            // 8-bit digits over the 52-bit key
+constexpr int CHAIN_C0 = 1024;            // sorted elements per level-0 chunk
+constexpr int CHAIN_FAN = 32;             // chunks merged per later-level group
+
+inline int64_t sort_tiles(int64_t cap) { return (cap + SORT_TILE - 1) / SORT_TILE; }
+int chain_levels(int64_t cap);
+
+}  // namespace cudapre

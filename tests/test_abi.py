@@ -1,0 +1,84 @@
+"""The C-ABI library loads and exports every symbol the header declares.
+
+No compute call here (no GPU needed): only loading, symbol lookup, option
+defaults, error strings, workspace sizing and the projection constants.
+"""
+import ctypes
+import os
+import re
+from decimal import Decimal, getcontext
+
+import pytest
+
+import paper_1405_3454_gb300 as cp
+from paper_1405_3454_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return cp.load()
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(cp.ABI_SYMBOLS) <= set(names)
+
+
+def test_defaults_and_strings(lib):
+    o = cp.HullOptions()
+    lib.hull_default_options(ctypes.byref(o))
+    assert o.angles == cp.HULL_ANGLES_CUMULATIVE and o.filter == cp.HULL_FILTER_FP32 and o.validate == 0
+    for code in range(8):
+        assert lib.hull_strerror(code).decode().startswith("HULL_")
+    assert lib.hull_abi_version() == 1
+
+
+def test_workspace_sizes_monotone(lib):
+    a = cp.hull_workspace_bytes(1000)
+    b = cp.hull_workspace_bytes(1 << 20)
+    assert 0 < a < b
+    assert cp.hull_prefilter_workspace_bytes(1 << 28) < cp.hull_workspace_bytes(1 << 28)
+    # the full pipeline keeps two (u64 key, u32 index) buffers of n entries
+    assert cp.hull_workspace_bytes(1 << 28) >= 24 * (1 << 28)
+
+
+def test_library_constants_are_correctly_rounded(lib):
+    getcontext().prec = 60
+    s3 = Decimal(3).sqrt() / 2
+    s6, s2 = Decimal(6).sqrt(), Decimal(2).sqrt()
+    c = cp.constants()
+    assert c["s3"] == float(s3)
+    assert c["c75"] == float((s6 - s2) / 4)
+    assert c["s75"] == float((s6 + s2) / 4)
+    assert c["h"] == float(s2 / 2)
+
+
+def test_argument_errors_without_gpu(lib):
+    # invalid arguments are rejected before any CUDA call
+    P = 256 * 1024
+    assert cp.hull_prefilter(0, 10, P, 1 << 30, P, P, 0, None, 0) == 1      # null xy
+    assert cp.hull_prefilter(P + 4, 10, P, 1 << 30, P, P, 0, None, 0) == 1  # misaligned xy
+    assert cp.hull_prefilter(P, -1, P, 1 << 30, P, P, 0, None, 0) == 1      # negative n
+    assert cp.hull_prefilter(P, 1 << 32, P, 1 << 30, P, P, 0, None, 0) == 1 # n too large
+    assert cp.hull_compute(P, 10, P + 8, 1 << 30, P, P, None, 0) == 1       # misaligned workspace
+    assert cp.hull_compute(P, 1000, P, 16, P, P, None, 0) == 3               # workspace too small
+    o = cp.Options(angles=7)
+    assert cp.hull_compute(P, 10, P, 1 << 30, P, P, o, 0) == 7               # unsupported option

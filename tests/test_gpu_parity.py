@@ -1,0 +1,200 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact comparisons: the 16 extreme indices, the Step-2 polygon, the
+survivor set (sorted indices; compaction order is unspecified) and the hull
+index list (order included).  Sizes span several tiles and ragged tails;
+edge cases cover empty input, tiny inputs, duplicates, collinear sets,
+-0.0 and coordinates at +-2^24, and an 8-byte (not 16-byte) aligned input.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+MODES = [(a, f) for a in (0, 1) for f in (0, 1)]  # (angles, filter)
+
+
+def to_dev(xy, offset=False):
+    import torch
+    a = np.ascontiguousarray(xy, dtype=np.float32).reshape(-1, 2)
+    if not offset:
+        return torch.from_numpy(a).cuda()
+    # 8-byte but not 16-byte aligned view: one leading dummy point
+    buf = torch.empty(a.shape[0] + 1, 2, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(a).cuda()
+    v = buf[1:]
+    assert v.data_ptr() % 16 == 8
+    return v
+
+
+def run_prefilter(cp, xy, angles, filt, offset=False):
+    d = to_dev(xy, offset)
+    surv, cnt, ext, ws = cp.prefilter(d, cp.Options(angles=angles, filter=filt))
+    import torch
+    torch.cuda.synchronize()
+    n_s = int(cnt.item())
+    s = np.sort(cp.as_index(surv, n_s))
+    e = cp.as_index(ext)
+    m, pxy, _ = cp.read_polygon(ws)
+    return e, np.array(pxy, dtype=np.int64).reshape(-1, 2), s, ws
+
+
+def oracle_ext(xy, angles):
+    e = oracle.extremes(xy, angles)
+    return np.where(e < 0, 0xFFFFFFFF, e)
+
+
+def check_prefilter(cp, xy, angles, filt, offset=False):
+    e, poly, surv, ws = run_prefilter(cp, xy, angles, filt, offset)
+    oe = oracle_ext(xy, angles)
+    assert e.tolist() == oe.tolist(), "extremes"
+    if xy.shape[0]:
+        _, opoly = oracle.hull16(xy, oracle.extremes(xy, angles))
+    else:
+        opoly = np.zeros((0, 2), dtype=np.int32)
+    assert poly.tolist() == opoly.tolist(), "polygon"
+    osurv = oracle.prefilter(xy, opoly)
+    assert surv.tolist() == osurv.tolist(), "survivors"
+    return ws
+
+
+def check_compute(cp, xy, angles, filt, offset=False):
+    import torch
+    d = to_dev(xy, offset)
+    out, cnt, ws = cp.compute(d, cp.Options(angles=angles, filter=filt))
+    torch.cuda.synchronize()
+    h = cp.as_index(out, int(cnt.item()))
+    want = oracle.hull(xy)
+    assert h.tolist() == want.tolist(), "hull"
+    return ws
+
+
+SIZES = [0, 1, 2, 3, 4, 5, 7, 17, 255, 1000, 2047, 2048, 4097, 65537, 300001]
+
+
+@pytest.mark.parametrize("angles,filt", MODES)
+@pytest.mark.parametrize("n", SIZES)
+def test_prefilter_sizes(gpu_lib, n, angles, filt):
+    for kind in (0, 1, 2):
+        xy = synth.shape(kind, n, 7 + n, 50 + kind)
+        check_prefilter(gpu_lib, xy, angles, filt)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 1001, 65537])
+def test_prefilter_unaligned_input(gpu_lib, n):
+    for kind in (0, 1, 2):
+        xy = synth.shape(kind, n, 9 + n, 60 + kind)
+        for filt in (0, 1):
+            check_prefilter(gpu_lib, xy, 0, filt, offset=True)
+            check_compute(gpu_lib, xy, 0, filt, offset=True)
+
+
+@pytest.mark.parametrize("angles,filt", MODES)
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 17, 1000, 4097, 65537, 300001])
+def test_compute_sizes(gpu_lib, n, angles, filt):
+    for kind in (0, 1, 2):
+        xy = synth.shape(kind, n, 11 + n, 70 + kind)
+        check_compute(gpu_lib, xy, angles, filt)
+
+
+def degenerate_sets():
+    r = np.random.default_rng(5)
+    yield "all_equal", np.tile(np.array([[3.0, -4.0]], np.float32), (5000, 1))
+    yield "two_points", np.array([[0, 0], [5, 5]] * 3000, np.float32)
+    k = r.integers(-1000, 1000, 20000)
+    yield "collinear", np.stack([k * 7, k * -3], 1).astype(np.float32)
+    sq = synth.square(40000, 3, 50)  # heavy duplication, many ties
+    yield "small_lattice", sq
+    z = sq.copy()
+    z[z == 0] = -0.0
+    yield "negative_zero", z
+    big = r.choice(np.array([-(1 << 24), 1 << 24, 0, 1, -1], np.float32), size=(30000, 2))
+    yield "domain_corners", big.astype(np.float32)
+    tri = np.array([[0, 0], [6, 0], [0, 6], [1, 1], [3, 3], [0, 3], [3, 0]] * 1000, np.float32)
+    yield "triangle_repeated", tri
+    circ = []
+    for t in range(4096):  # points in convex position: nothing can be discarded twice
+        a = 2 * np.pi * t / 4096
+        circ.append((round(8e6 * np.cos(a)), round(8e6 * np.sin(a))))
+    yield "convex_position", np.array(circ, np.float32)
+
+
+@pytest.mark.parametrize("name,xy", list(degenerate_sets()), ids=lambda v: v if isinstance(v, str) else "")
+def test_degenerate(gpu_lib, name, xy):
+    for angles, filt in MODES:
+        check_prefilter(gpu_lib, xy, angles, filt)
+        check_compute(gpu_lib, xy, angles, filt)
+
+
+def test_config1_square_1m(gpu_lib):
+    # 1,000,000 points uniform in [-2^20, 2^20]^2, plain exact and FP32-filtered
+    xy = synth.square(1_000_000, synth.BASE_SEED, 1 << 20)
+    for filt in (0, 1):
+        check_prefilter(gpu_lib, xy, 0, filt)
+        check_compute(gpu_lib, xy, 0, filt)
+
+
+def test_filter_modes_identical_near_edges(gpu_lib):
+    # Half Gaussian, half on/within one unit inside the polygon's edges: the
+    # FP32 filter must escalate, and both modes must agree with the oracle.
+    import torch
+    n = 1 << 20
+    g = synth.gaussian(n // 2, 17)
+    _, poly = oracle.hull16(g, oracle.extremes(g))
+    ne = synth.near_edge(n - n // 2, poly, 18)
+    xy = synth.permute(np.concatenate([g, ne]), 19)
+    _, poly_all = oracle.hull16(xy, oracle.extremes(xy))
+    assert poly_all.tolist() == poly.tolist()
+    ws = check_prefilter(gpu_lib, xy, 0, 1)
+    ns, nesc = gpu_lib.read_counters(ws)
+    assert nesc > n // 8, nesc  # many near-boundary decisions escalated
+    check_prefilter(gpu_lib, xy, 0, 0)
+    check_compute(gpu_lib, xy, 0, 1)
+
+
+def test_launch_shapes_do_not_change_results(gpu_lib):
+    import torch
+    xy = synth.disk(500_000, 23)
+    ref = None
+    for grid in (1, 3, 64, 1000):
+        d = to_dev(xy)
+        surv, cnt, ext, ws = gpu_lib.prefilter(d, gpu_lib.Options(grid=grid))
+        out, hcnt, _ = gpu_lib.compute(d, gpu_lib.Options(grid=grid))
+        torch.cuda.synchronize()
+        got = (gpu_lib.as_index(ext).tolist(), np.sort(gpu_lib.as_index(surv, int(cnt.item()))).tolist(),
+               gpu_lib.as_index(out, int(hcnt.item())).tolist())
+        if ref is None:
+            ref = got
+        assert got == ref, grid
+
+
+def test_validate_flags_out_of_domain(gpu_lib):
+    import torch
+    for bad in (np.float32(0.5), np.float32(np.nan), np.float32(np.inf), np.float32(2 ** 24 + 2)):
+        xy = synth.square(10000, 1, 100)
+        xy[1234, 1] = bad
+        d = to_dev(xy)
+        out, cnt, ws = gpu_lib.compute(d, gpu_lib.Options(validate=True))
+        torch.cuda.synchronize()
+        code, bits = gpu_lib.device_status(ws)
+        assert bits & gpu_lib.HULL_DEVICE_DOMAIN and code == 2
+        assert int(cnt.item()) == 0
+    # in-domain input passes validation
+    xy = synth.square(10000, 1, 100)
+    out, cnt, ws = gpu_lib.compute(to_dev(xy), gpu_lib.Options(validate=True))
+    assert gpu_lib.device_status(ws) == (0, 0)
+    assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()
+
+
+def test_workspace_reuse_back_to_back(gpu_lib):
+    import torch
+    a = synth.disk(200_000, 31)
+    b = synth.gaussian(150_000, 32)
+    ws = gpu_lib.workspace(gpu_lib.hull_workspace_bytes(200_000))
+    for xy in (a, b, a):
+        out, cnt, _ = gpu_lib.compute(to_dev(xy), ws=ws)
+        torch.cuda.synchronize()
+        assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()
