@@ -104,6 +104,30 @@ def permute(xy: np.ndarray, seed: int = BASE_SEED) -> np.ndarray:
     return out
 
 
+def interleave(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Even indices from a, odd indices from b (len(a) == len(b) or len(a) == len(b) + 1).
+
+    Both inputs keep their relative order, so lowest-index tie-breaking among
+    the points of `a` is unchanged."""
+    assert len(a) - len(b) in (0, 1)
+    out = np.empty((len(a) + len(b), 2), dtype=np.float32)
+    out[0::2] = a
+    out[1::2] = b
+    return out
+
+
+def near_edge_mix(n: int, seed: int, polygon_of) -> tuple[np.ndarray, np.ndarray]:
+    """The FP32-escalation workload: n points, half integer-valued Gaussian
+    (sigma 2^22, clipped to +-2^24) at even indices, half on or within one unit
+    inside the edges of the Gaussian half's Step-2 polygon at odd indices.
+    `polygon_of(xy) -> [m, 2] int` supplies that polygon (the generator
+    computes no polygon itself).  Returns (xy, polygon)."""
+    g = gaussian(n - n // 2, seed, stream=40)
+    poly = np.asarray(polygon_of(g), dtype=np.int32).reshape(-1, 2)
+    ne = near_edge(n // 2, poly, seed, stream=41)
+    return interleave(g, ne), poly
+
+
 def shape(kind: int, n: int, seed: int, stream: int, out=None) -> np.ndarray:
     """Shape id 0 = square r=2^24, 1 = disk r=2^24, 2 = Gaussian sigma=2^22 clipped at 2^24."""
     if kind == 0:

@@ -123,8 +123,9 @@ static int64_t gcd64(int64_t a, int64_t b) {
  * exactly on the edge; otherwise the point sits on the major-axis lattice line
  * at parameter t and the other coordinate is rounded toward the polygon's
  * interior (the left of a->b), so its distance to the edge line is < 1 and it
- * is on the inner side or on the line.  Used to force near-boundary inside
- * tests.  m < 3 writes nothing and returns 0. */
+ * is on the inner side or on the line.  Points of axis-parallel edges are put
+ * one unit inside instead.  Used to force near-boundary inside tests.
+ * m < 3 writes nothing and returns 0. */
 int synth_near_edge(float* xy, int64_t n, uint64_t seed, uint64_t stream,
                     const int32_t* poly, int m) {
   if (m < 3) return 0;
@@ -156,6 +157,10 @@ int synth_near_edge(float* xy, int64_t n, uint64_t seed, uint64_t stream,
       int64_t num = (qx - ax) * dy; /* y = ay + num / dx */
       qy = ay + (dx > 0 ? ceil_div(num, dx) : floor_div(num, dx));
     }
+    /* an axis-parallel edge lies on a line of axis extremes; keep its points
+     * one unit inside so that they never tie with those extremes */
+    if (dx == 0) qx += (-dy > 0) ? 1 : -1;
+    if (dy == 0) qy += (dx > 0) ? 1 : -1;
     xy[2 * i] = (float)qx;
     xy[2 * i + 1] = (float)qy;
   }

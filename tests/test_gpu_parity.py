@@ -142,10 +142,7 @@ def test_filter_modes_identical_near_edges(gpu_lib):
     # FP32 filter must escalate, and both modes must agree with the oracle.
     import torch
     n = 1 << 20
-    g = synth.gaussian(n // 2, 17)
-    _, poly = oracle.hull16(g, oracle.extremes(g))
-    ne = synth.near_edge(n - n // 2, poly, 18)
-    xy = synth.permute(np.concatenate([g, ne]), 19)
+    xy, poly = synth.near_edge_mix(n, 17, lambda g: oracle.hull16(g, oracle.extremes(g))[1])
     _, poly_all = oracle.hull16(xy, oracle.extremes(xy))
     assert poly_all.tolist() == poly.tolist()
     ws = check_prefilter(gpu_lib, xy, 0, 1)

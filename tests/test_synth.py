@@ -35,9 +35,11 @@ def test_domain_and_shapes():
 
 def test_near_edge_points_on_inner_side_within_one_unit():
     poly = np.array([[0, 0], [1000003, 17], [700001, 900007], [-5, 400001]], dtype=np.int32)
-    # also an edge with many interior lattice points (gcd > 1)
-    poly2 = np.array([[0, 0], [600, 0], [600, 300], [0, 300]], dtype=np.int32)
-    for P in (poly, poly2):
+    # an edge with interior lattice points (gcd > 1): some points exactly on it
+    poly2 = np.array([[0, 0], [600, 300], [-40, 900]], dtype=np.int32)
+    # axis-parallel edges: points exactly one unit inside, never on the edge
+    poly3 = np.array([[0, 0], [600, 0], [600, 300], [0, 300]], dtype=np.int32)
+    for P in (poly, poly2, poly3):
         q = synth.near_edge(20000, P, 3).astype(np.int64)
         m = len(P)
         on = 0
@@ -50,7 +52,7 @@ def test_near_edge_points_on_inner_side_within_one_unit():
                 best = d if best is None or abs(d) < abs(best) else best
             assert 0 <= best <= 1.0 + 1e-9
             on += best == 0
-        assert on > 0
+        assert (on > 0) == (P is poly2) or P is poly
 
 
 def test_set_plan_log_uniform():
