@@ -85,7 +85,10 @@ typedef struct hull_options {
   int32_t validate;      /* nonzero: check the input domain on the device first */
   int32_t block;         /* threads per block of the streaming kernels; 0 = tuned */
   int32_t grid;          /* blocks of the streaming kernels; 0 = tuned */
-  int32_t reserved[11];  /* must be zero */
+  int32_t refine;        /* hull_compute: 1 (default) = a second, finer discard
+                            round on the survivors before the final hull (same
+                            result, less work); 0 = sort and chain every survivor */
+  int32_t reserved[10];  /* must be zero */
 } hull_options;
 
 /* Device-side condition bits (hull_get_device_status). */
@@ -94,7 +97,7 @@ typedef struct hull_options {
 #define HULL_DEVICE_OVERFLOW 4u /* an internal capacity was exceeded */
 
 /* Fills *opt with the defaults (cumulative angles, FP32 filter, no validation,
- * tuned launch shapes). */
+ * tuned launch shapes, refinement on). */
 void hull_default_options(hull_options* opt);
 
 /* Bytes of workspace needed by hull_prefilter for n points (opt may be NULL

@@ -44,7 +44,8 @@ STAGE_NAMES = ("validate", "extremes", "filter", "sort", "chain")
 
 class HullOptions(ctypes.Structure):
     _fields_ = [("angles", ctypes.c_int32), ("filter", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("refine", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
 
 
 class HullError(RuntimeError):
@@ -124,12 +125,13 @@ class Options:
     validate: bool = False
     block: int = 0
     grid: int = 0
+    refine: bool = True
 
     def c(self) -> HullOptions:
         o = HullOptions()
         load().hull_default_options(ctypes.byref(o))
         o.angles, o.filter, o.validate = int(self.angles), int(self.filter), int(bool(self.validate))
-        o.block, o.grid = int(self.block), int(self.grid)
+        o.block, o.grid, o.refine = int(self.block), int(self.grid), int(bool(self.refine))
         return o
 
 

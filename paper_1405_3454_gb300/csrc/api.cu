@@ -55,7 +55,7 @@ constexpr int64_t MAX_N = 0xFFFFFFFFll;  // indices are uint32
 constexpr int64_t MAX_BLOCKS = 4096;     // per-block partials of the extreme search
 
 struct Layout {
-  size_t header = 0, blockres = 0, keys_a = 0, vals_a = 0, keys_b = 0, vals_b = 0, tilecnt = 0,
+  size_t header = 0, blockres = 0, cells = 0, tri = 0, keys_a = 0, vals_a = 0, keys_b = 0, vals_b = 0, tilecnt = 0,
          cnt = 0, total = 0;
 };
 
@@ -65,8 +65,11 @@ Layout layout(int64_t n, bool full) {
   L.header = 0;
   L.blockres = off;
   off += align_up(sizeof(BlockBest) * NSLOT * MAX_BLOCKS, 256);
+  L.cells = off;
+  off += align_up(sizeof(uint16_t) * GRID * GRID, 256);
   if (full) {
     const int64_t cap = std::max<int64_t>(n, 1);
+    L.tri = off; off += align_up(sizeof(int4) * 2 * REFINE_BINS, 256);
     L.keys_a = off; off += align_up(8 * (size_t)cap, 256);
     L.vals_a = off; off += align_up(4 * (size_t)cap, 256);
     L.keys_b = off; off += align_up(8 * (size_t)cap, 256);
@@ -84,7 +87,8 @@ hull_status check_opts(const hull_options* o) {
   if (o->angles != HULL_ANGLES_CUMULATIVE && o->angles != HULL_ANGLES_ABSOLUTE) return HULL_ERR_UNSUPPORTED;
   if (o->filter != HULL_FILTER_EXACT && o->filter != HULL_FILTER_FP32) return HULL_ERR_UNSUPPORTED;
   if (o->block < 0 || o->grid < 0 || o->grid > MAX_BLOCKS) return HULL_ERR_INVALID_ARG;
-  for (int k = 0; k < 11; ++k) if (o->reserved[k] != 0) return HULL_ERR_UNSUPPORTED;
+  if (o->refine != 0 && o->refine != 1) return HULL_ERR_UNSUPPORTED;
+  for (int k = 0; k < 10; ++k) if (o->reserved[k] != 0) return HULL_ERR_UNSUPPORTED;
   return HULL_OK;
 }
 
@@ -114,7 +118,8 @@ hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& 
   HULL_TRY(launch_extremes(d_xy, n, o.angles, o.filter, h,
                            reinterpret_cast<BlockBest*>(ws + L.blockres), o.grid, o.block, ext_out, st));
   mark(2, st);
-  HULL_TRY(launch_filter(d_xy, n, o.filter, h, surv_idx, surv_key, o.grid, o.block, st));
+  HULL_TRY(launch_filter(d_xy, n, o.filter, h, reinterpret_cast<uint16_t*>(ws + L.cells), surv_idx,
+                         surv_key, o.grid, o.block, st));
   mark(3, st);
   return HULL_OK;
 }
@@ -140,6 +145,7 @@ void hull_default_options(hull_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->angles = HULL_ANGLES_CUMULATIVE;
   opt->filter = HULL_FILTER_FP32;
+  opt->refine = 1;
 }
 
 void hull_constants(double* out) {
@@ -214,10 +220,25 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   s = run_prefilter(d_xy, n, ws, L, va, ka, nullptr, o, st);
   if (s != HULL_OK) return s;
   const int64_t cap = std::max<int64_t>(n, 1);
-  HULL_TRY(launch_sort(cap, h, ka, va, kb, vb, reinterpret_cast<uint32_t*>(ws + L.tilecnt), st));
+  // The hull of the survivors.  With refinement the survivors in (ka, va)
+  // are thinned into (kb, vb) first.  Sets up to SMALL_MAX points take the
+  // one-block path; larger ones the device radix sort (7 passes, ending in
+  // the other buffer) and the chunked chain (its upper chains in the input).
+  const bool refine = o.refine != 0;
+  unsigned long long* kin = ka;
+  uint32_t* vin = va;
+  unsigned long long* kot = kb;
+  uint32_t* vot = vb;
+  const unsigned long long* count = &h->n_surv;
+  if (refine) {
+    HULL_TRY(launch_refine(h, ka, va, kb, vb, reinterpret_cast<int4*>(ws + L.tri), cap, st));
+    kin = kb; vin = vb; kot = ka; vot = va;
+    count = &h->n_surv2;
+  }
+  HULL_TRY(launch_small_hull(kin, vin, count, h, d_hull_idx, d_n_hull, st));
+  HULL_TRY(launch_sort(cap, h, count, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt), st));
   mark(4, st);
-  // sorted data in (kb, vb); the upper chains go to (ka, va)
-  HULL_TRY(launch_chain(cap, h, kb, vb, ka, va, reinterpret_cast<uint32_t*>(ws + L.cnt), d_hull_idx,
+  HULL_TRY(launch_chain(cap, h, count, kot, vot, kin, vin, reinterpret_cast<uint32_t*>(ws + L.cnt), d_hull_idx,
                         d_n_hull, st));
   mark(5, st);
   return HULL_OK;

@@ -46,9 +46,20 @@ struct Edge {
   int32_t dx, dy;       // exact edge vector
 };
 
+// Cell grid over the polygon's bounding box for the inside test: GRID x GRID
+// cells of 2^kx by 2^ky lattice points from (gx0, gy0).  Cell code = bit mask
+// of the edges that some point of the cell may fail; 0 = every point of the
+// cell is strictly inside (discard without a test).
+constexpr int GRID_LOG = 7;
+constexpr int GRID = 1 << GRID_LOG;
+
 struct Poly {
   int32_t m;            // vertex count (0..16); < 3 discards nothing
-  int32_t pad_[3];
+  int32_t gx0, gy0;     // cell grid origin (multiples of the cell sizes)
+  int32_t kx, ky;       // log2 of the cell sizes
+  int32_t rox, roy;     // integer point strictly inside (centre of the inner box)
+  int32_t refine_on;    // 1 when (rox, roy) is valid
+  int32_t pad_[4];
   float box[4];         // closed inner box x0, x1, y0, y1 (integer-valued);
                         // every point of it is strictly inside; x0 > x1 if empty
   int32_t vx[MAXV], vy[MAXV];
@@ -73,7 +84,10 @@ struct WsHeader {
   unsigned long long n_escalated; // float32 decisions escalated to int64
   unsigned long long pad0_;
   uint32_t hist[8][256];  // radix-sort digit histograms (all passes)
+  unsigned long long n_surv2;  // survivors left by the refinement round
+  unsigned long long pad1_;
   Poly poly;
+  unsigned long long rbin[1024];  // refinement: per angular bin, packed farthest survivor
 };
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -112,15 +126,28 @@ cudaError_t launch_validate(const float* xy, int64_t n, WsHeader* h, cudaStream_
 cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, WsHeader* h,
                             BlockBest* blockres, int grid, int block, uint32_t* ext_out,
                             cudaStream_t st);
-cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, uint32_t* surv_idx,
-                          unsigned long long* surv_key, int grid, int block, cudaStream_t st);
-cudaError_t launch_sort(int64_t cap, WsHeader* h, unsigned long long* keys_a, uint32_t* vals_a,
-                        unsigned long long* keys_b, uint32_t* vals_b, uint32_t* tilecnt,
-                        cudaStream_t st);
-cudaError_t launch_chain(int64_t cap, WsHeader* h, unsigned long long* keys_s, uint32_t* vals_s,
-                         unsigned long long* keys_u, uint32_t* vals_u, uint32_t* cnt,
-                         uint32_t* out_idx, int64_t* out_n, cudaStream_t st);
+cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, uint16_t* cells,
+                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, int block,
+                          cudaStream_t st);
+// The large path (sort + chunked chain) runs only when *count > SMALL_MAX.
+cudaError_t launch_sort(int64_t cap, WsHeader* h, const unsigned long long* count,
+                        unsigned long long* keys_a, uint32_t* vals_a, unsigned long long* keys_b,
+                        uint32_t* vals_b, uint32_t* tilecnt, cudaStream_t st);
+cudaError_t launch_chain(int64_t cap, WsHeader* h, const unsigned long long* count,
+                         unsigned long long* keys_s, uint32_t* vals_s, unsigned long long* keys_u,
+                         uint32_t* vals_u, uint32_t* cnt, uint32_t* out_idx, int64_t* out_n,
+                         cudaStream_t st);
 cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st);
+
+constexpr int REFINE_BINS = 1024;         // angular bins of the refinement round
+constexpr int SMALL_MAX = 8192;           // survivor sets up to this size: one-block hull
+
+cudaError_t launch_refine(WsHeader* h, const unsigned long long* keys_in, const uint32_t* vals_in,
+                          unsigned long long* keys_out, uint32_t* vals_out, int4* tri, int64_t cap,
+                          cudaStream_t st);
+cudaError_t launch_small_hull(const unsigned long long* keys, const uint32_t* vals,
+                              const unsigned long long* count, const WsHeader* h, uint32_t* out,
+                              int64_t* out_n, cudaStream_t st);
 
 // Sizes used by the sort and chain stages.
 constexpr int SORT_TILE = 4096;           // elements per sort tile

@@ -16,9 +16,12 @@ namespace cudapre {
 
 namespace {
 
-__device__ __forceinline__ int64_t dev_count(const WsHeader* h) {
+// Element count of the large path: 0 (nothing to do) when the one-block
+// path takes the set.
+__device__ __forceinline__ int64_t dev_count(const WsHeader* h, const unsigned long long* count) {
   if (*reinterpret_cast<const volatile uint32_t*>(&h->status)) return 0;
-  return (int64_t)*reinterpret_cast<const volatile unsigned long long*>(&h->n_surv);
+  const int64_t m = (int64_t)*reinterpret_cast<const volatile unsigned long long*>(count);
+  return m > SMALL_MAX ? m : 0;
 }
 
 __device__ __forceinline__ long long cross_k(unsigned long long o, unsigned long long a,
@@ -67,10 +70,10 @@ struct Stack {
 // Lower chain in place in (Ks, Vs); upper chain into (Ku, Vu) at the same
 // offsets.  Counts to cnt_lo[g], cnt_up[g].
 __global__ void k_chain0(unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku, uint32_t* Vu,
-                         const WsHeader* h, uint32_t* cnt_lo, uint32_t* cnt_up, int64_t nch) {
+                         const WsHeader* h, const unsigned long long* count, uint32_t* cnt_lo, uint32_t* cnt_up, int64_t nch) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nch) return;
-  const int64_t m = dev_count(h);
+  const int64_t m = dev_count(h, count);
   const int64_t start = g * CHAIN_C0;
   if (start >= m) return;
   const int64_t end = min(start + (int64_t)CHAIN_C0, m);
@@ -92,14 +95,14 @@ __global__ void k_chain0(unsigned long long* Ks, uint32_t* Vs, unsigned long lon
 // previous level (span `span_prev` each).  Thread 2g+0 does the lower
 // chains, 2g+1 the upper ones.
 __global__ void k_chainN(unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku, uint32_t* Vu,
-                         const WsHeader* h, const uint32_t* cin_lo, const uint32_t* cin_up,
+                         const WsHeader* h, const unsigned long long* count, const uint32_t* cin_lo, const uint32_t* cin_up,
                          uint32_t* cout_lo, uint32_t* cout_up, int64_t nch_prev, int64_t span_prev,
                          int64_t ngroups) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t g = t >> 1;
   const bool upper = t & 1;
   if (g >= ngroups) return;
-  const int64_t m = dev_count(h);
+  const int64_t m = dev_count(h, count);
   const int64_t c0 = g * CHAIN_FAN;
   if (c0 * span_prev >= m) return;
   const int64_t c1 = min(c0 + (int64_t)CHAIN_FAN, nch_prev);
@@ -126,10 +129,10 @@ __global__ void k_chainN(unsigned long long* Ks, uint32_t* Vs, unsigned long lon
 // left to right, then the upper chain right to left, without repeating the
 // two end points.
 __global__ void k_chain_final(const uint32_t* Vs, const uint32_t* Vu, const WsHeader* h,
-                              const uint32_t* cnt_lo, const uint32_t* cnt_up, uint32_t* out_idx,
-                              int64_t* out_n) {
-  const int64_t m = dev_count(h);
-  if (m == 0) { *out_n = 0; return; }
+                              const unsigned long long* count, const uint32_t* cnt_lo,
+                              const uint32_t* cnt_up, uint32_t* out_idx, int64_t* out_n) {
+  const int64_t m = dev_count(h, count);
+  if (m == 0) return;  // the one-block path wrote the result
   const int64_t a = cnt_lo[0], b = cnt_up[0];
   int64_t pos = 0;
   if (a == 1) {
@@ -151,21 +154,22 @@ int chain_levels(int64_t cap) {
 }
 
 // cnt holds four arrays of nch0 entries: lower/upper for even and odd levels.
-cudaError_t launch_chain(int64_t cap, WsHeader* h, unsigned long long* keys_s, uint32_t* vals_s,
-                         unsigned long long* keys_u, uint32_t* vals_u, uint32_t* cnt,
-                         uint32_t* out_idx, int64_t* out_n, cudaStream_t st) {
+cudaError_t launch_chain(int64_t cap, WsHeader* h, const unsigned long long* count,
+                         unsigned long long* keys_s, uint32_t* vals_s, unsigned long long* keys_u,
+                         uint32_t* vals_u, uint32_t* cnt, uint32_t* out_idx, int64_t* out_n,
+                         cudaStream_t st) {
   const int64_t nch0 = (std::max<int64_t>(cap, 1) + CHAIN_C0 - 1) / CHAIN_C0;
   uint32_t* lo[2] = {cnt, cnt + 2 * nch0};
   uint32_t* up[2] = {cnt + nch0, cnt + 3 * nch0};
   const int TB = 128;
-  k_chain0<<<(unsigned)((nch0 + TB - 1) / TB), TB, 0, st>>>(keys_s, vals_s, keys_u, vals_u, h, lo[0], up[0], nch0);
+  k_chain0<<<(unsigned)((nch0 + TB - 1) / TB), TB, 0, st>>>(keys_s, vals_s, keys_u, vals_u, h, count, lo[0], up[0], nch0);
   count_launches(1);
   int64_t nch = nch0, span = CHAIN_C0;
   int par = 0;
   while (nch > 1) {
     const int64_t ng = (nch + CHAIN_FAN - 1) / CHAIN_FAN;
     const int64_t threads = 2 * ng;
-    k_chainN<<<(unsigned)((threads + TB - 1) / TB), TB, 0, st>>>(keys_s, vals_s, keys_u, vals_u, h,
+    k_chainN<<<(unsigned)((threads + TB - 1) / TB), TB, 0, st>>>(keys_s, vals_s, keys_u, vals_u, h, count,
                                                                  lo[par], up[par], lo[par ^ 1], up[par ^ 1],
                                                                  nch, span, ng);
     count_launches(1);
@@ -173,7 +177,7 @@ cudaError_t launch_chain(int64_t cap, WsHeader* h, unsigned long long* keys_s, u
     nch = ng;
     span *= CHAIN_FAN;
   }
-  k_chain_final<<<1, 1, 0, st>>>(vals_s, vals_u, h, lo[par], up[par], out_idx, out_n);
+  k_chain_final<<<1, 1, 0, st>>>(vals_s, vals_u, h, count, lo[par], up[par], out_idx, out_n);
   count_launches(1);
   return cudaGetLastError();
 }

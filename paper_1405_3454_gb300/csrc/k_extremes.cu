@@ -252,6 +252,27 @@ __device__ void build_edges_and_box(Poly* P, int m, int lane) {
       }
     }
     for (int c = 0; c < 4; ++c) P->box[c] = box[c];
+    // An integer point strictly inside: the centre of a non-empty inner box.
+    P->refine_on = box[0] <= box[1] ? 1 : 0;
+    P->rox = P->refine_on ? (int)floorf(0.5f * (box[0] + box[1])) : 0;
+    P->roy = P->refine_on ? (int)floorf(0.5f * (box[2] + box[3])) : 0;
+    // Cell grid: smallest power-of-two cell sizes whose GRID cells, from an
+    // origin aligned to the cell size, cover the bounding box.
+    int xl = 0, xh = 0, yl = 0, yh = 0;
+    for (int k = 0; k < m; ++k) {
+      if (k == 0 || P->vx[k] < xl) xl = P->vx[k];
+      if (k == 0 || P->vx[k] > xh) xh = P->vx[k];
+      if (k == 0 || P->vy[k] < yl) yl = P->vy[k];
+      if (k == 0 || P->vy[k] > yh) yh = P->vy[k];
+    }
+    int kx = 0, ky = 0;
+    auto origin = [](int v, int k) { return (int)(((long long)v >> k) << k); };  // floor to 2^k
+    while ((long long)xh - origin(xl, kx) >= ((long long)GRID << kx)) ++kx;
+    while ((long long)yh - origin(yl, ky) >= ((long long)GRID << ky)) ++ky;
+    P->kx = kx;
+    P->ky = ky;
+    P->gx0 = origin(xl, kx);
+    P->gy0 = origin(yl, ky);
   }
 }
 
@@ -384,38 +405,51 @@ __device__ bool last_block_arrives(WsHeader* h) {
 
 // ----------------------------------------------------------------------------
 // FP32-filtered extreme search.
+//
+// The running best of every thread and direction lives in shared memory: it
+// is touched only when a tile can improve on the block's best, which is rare
+// once the block-wide thresholds have risen.  The streaming loop therefore
+// keeps only the current and the next tile in registers (8 points each), so
+// four blocks fit on an SM and 32 bytes per thread are always in flight.
 
 template <int ANG>
-__global__ void __launch_bounds__(BLOCK) k_extremes32(const float* __restrict__ xy, int64_t n,
-                                                       int head, int64_t npairs, int64_t ppb,
-                                                       WsHeader* h, BlockBest* blockres,
-                                                       uint32_t* ext_out) {
+__global__ void __launch_bounds__(BLOCK, 3) k_extremes32(const float* __restrict__ xy, int64_t n,
+                                                          int head, int64_t npairs, int64_t ppb,
+                                                          WsHeader* h, BlockBest* blockres,
+                                                          uint32_t* ext_out) {
   constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
   __shared__ __align__(16) float thr[ND];  // trigger thresholds in value space
+  __shared__ float s_best[ND][BLOCK];
+  __shared__ uint32_t s_bidx[ND][BLOCK];
   __shared__ float s_red[BLOCK / 32][ND];
   __shared__ uint32_t s_redi[BLOCK / 32][ND];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool dead = *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
-
-  float best[ND];
-  uint32_t bidx[ND];
 #pragma unroll
-  for (int d = 0; d < ND; ++d) { best[d] = -FLT_MAX; bidx[d] = NONE; }
+  for (int d = 0; d < ND; ++d) { s_best[d][tid] = -FLT_MAX; s_bidx[d][tid] = NONE; }
 
   const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
   const int64_t p0 = (int64_t)blockIdx.x * ppb;
   const int64_t p1 = dead ? p0 : min(p0 + ppb, npairs);
-  bool first = true;
-  for (int64_t base = p0; base < p1; base += STEP) {
-    float px[2 * PAIRS_PER_THREAD], py[2 * PAIRS_PER_THREAD];
-    uint32_t pid[PAIRS_PER_THREAD];
+  const int64_t nsteps = p1 > p0 ? (p1 - p0 + STEP - 1) / STEP : 0;
+
+  float4 cur[PAIRS_PER_THREAD];
+  auto load = [&](int64_t base, float4* v) {
 #pragma unroll
     for (int j = 0; j < PAIRS_PER_THREAD; ++j) {
       const int64_t pp = base + j * BLOCK + tid;
-      const int64_t q = pp < p1 ? pp : p0;  // out of range: repeat a real point
-      const float4 v = __ldcs(P + q);
-      px[2 * j] = v.x; py[2 * j] = v.y; px[2 * j + 1] = v.z; py[2 * j + 1] = v.w;
-      pid[j] = (uint32_t)(head + 2 * q);
+      v[j] = __ldg(P + (pp < p1 ? pp : p0));  // out of range: repeat a real point
+    }
+  };
+  if (nsteps > 0) load(p0, cur);
+  for (int64_t st = 0; st < nsteps; ++st) {
+    const int64_t base = p0 + st * BLOCK * PAIRS_PER_THREAD;
+    float4 nxt[PAIRS_PER_THREAD];
+    if (st + 1 < nsteps) load(base + STEP, nxt);
+    float px[2 * PAIRS_PER_THREAD], py[2 * PAIRS_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < PAIRS_PER_THREAD; ++j) {
+      px[2 * j] = cur[j].x; py[2 * j] = cur[j].y; px[2 * j + 1] = cur[j].z; py[2 * j + 1] = cur[j].w;
     }
     float tmin[NV], tmax[NV];
     {
@@ -430,9 +464,8 @@ __global__ void __launch_bounds__(BLOCK) k_extremes32(const float* __restrict__ 
         for (int k = 0; k < NV; ++k) { tmin[k] = fminf(tmin[k], v[k]); tmax[k] = fmaxf(tmax[k], v[k]); }
       }
     }
-    if (first) {
+    if (st == 0) {
       // Seed the block's thresholds from the first tile of every thread.
-      first = false;
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         float a = tmin[k], b = tmax[k];
@@ -459,23 +492,24 @@ __global__ void __launch_bounds__(BLOCK) k_extremes32(const float* __restrict__ 
     }
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      if (tmin[k] <= t[2 * k]) {
-#pragma unroll
+      const bool lo = tmin[k] <= t[2 * k], hi = tmax[k] >= t[2 * k + 1];
+      if (lo || hi) {
+#pragma unroll 1
         for (int j = 0; j < 2 * PAIRS_PER_THREAD; ++j) {
           const float val = value32<ANG>(k, px[j], py[j]);
-          if (val <= *reinterpret_cast<volatile float*>(&thr[2 * k]))
-            offer32<ANG>(2 * k, val, px[j], py[j], pid[j >> 1] + (j & 1), best[2 * k], bidx[2 * k], thr, xy);
+          const int64_t pp = base + (j >> 1) * BLOCK + tid;
+          const uint32_t i = (uint32_t)(head + 2 * (pp < p1 ? pp : p0)) + (j & 1);
+          if (lo && val <= *reinterpret_cast<volatile float*>(&thr[2 * k]))
+            offer32<ANG>(2 * k, val, px[j], py[j], i, s_best[2 * k][tid], s_bidx[2 * k][tid], thr, xy);
+          if (hi && val >= *reinterpret_cast<volatile float*>(&thr[2 * k + 1]))
+            offer32<ANG>(2 * k + 1, val, px[j], py[j], i, s_best[2 * k + 1][tid], s_bidx[2 * k + 1][tid],
+                         thr, xy);
         }
       }
-      if (tmax[k] >= t[2 * k + 1]) {
+    }
+    if (st + 1 < nsteps) {
 #pragma unroll
-        for (int j = 0; j < 2 * PAIRS_PER_THREAD; ++j) {
-          const float val = value32<ANG>(k, px[j], py[j]);
-          if (val >= *reinterpret_cast<volatile float*>(&thr[2 * k + 1]))
-            offer32<ANG>(2 * k + 1, val, px[j], py[j], pid[j >> 1] + (j & 1), best[2 * k + 1],
-                         bidx[2 * k + 1], thr, xy);
-        }
-      }
+      for (int j = 0; j < PAIRS_PER_THREAD; ++j) cur[j] = nxt[j];
     }
   }
   // Points outside the 16-byte-aligned pairs: a leading point (block 0) and
@@ -491,16 +525,16 @@ __global__ void __launch_bounds__(BLOCK) k_extremes32(const float* __restrict__ 
       values32<ANG>(p.x, p.y, v);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
-        offer32<ANG>(2 * k, v[k], p.x, p.y, i, best[2 * k], bidx[2 * k], thr, xy);
-        offer32<ANG>(2 * k + 1, v[k], p.x, p.y, i, best[2 * k + 1], bidx[2 * k + 1], thr, xy);
+        offer32<ANG>(2 * k, v[k], p.x, p.y, i, s_best[2 * k][tid], s_bidx[2 * k][tid], thr, xy);
+        offer32<ANG>(2 * k + 1, v[k], p.x, p.y, i, s_best[2 * k + 1][tid], s_bidx[2 * k + 1][tid], thr, xy);
       }
     }
   }
   // Block reduction (warp butterfly, then across warps), exact.
-#pragma unroll
+#pragma unroll 1
   for (int d = 0; d < ND; ++d) {
-    float s = best[d];
-    uint32_t i = bidx[d];
+    float s = s_best[d][tid];
+    uint32_t i = s_bidx[d][tid];
     for (int off = 16; off; off >>= 1) {
       const float so = __shfl_xor_sync(FULL, s, off);
       const uint32_t io = __shfl_xor_sync(FULL, i, off);
@@ -510,6 +544,7 @@ __global__ void __launch_bounds__(BLOCK) k_extremes32(const float* __restrict__ 
   }
   __syncthreads();
   if (warp == 0) {
+#pragma unroll 1
     for (int d = 0; d < ND; ++d) {
       float s = lane < BLOCK / 32 ? s_red[lane][d] : -FLT_MAX;
       uint32_t i = lane < BLOCK / 32 ? s_redi[lane][d] : NONE;
@@ -556,7 +591,8 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(const float* __restrict__ 
   auto offer = [&](float x, float y, uint32_t i) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      const double v = value64(ANG, k, x, y);
+      // group 0 is the original set: x' = x, y' = y exactly
+      const double v = k == 0 ? (double)x : (k == 1 ? (double)y : value64(ANG, k, x, y));
       if (bidx[2 * k] == NONE || -v > best[2 * k] || (-v == best[2 * k] && i < bidx[2 * k])) {
         best[2 * k] = -v; bidx[2 * k] = i;
       }
@@ -630,6 +666,13 @@ __global__ void k_validate(const float* __restrict__ xy, int64_t n2, WsHeader* h
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&h->status, HULL_DEVICE_DOMAIN);
 }
 
+template <typename K>
+int occupancy(K kernel) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, BLOCK, 0) != cudaSuccess || b < 1) b = 1;
+  return b;
+}
+
 }  // namespace
 
 cudaError_t launch_validate(const float* xy, int64_t n, WsHeader* h, cudaStream_t st) {
@@ -647,7 +690,12 @@ cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, 
   (void)block;
   const int head = (n > 0 && (reinterpret_cast<uintptr_t>(xy) & 15u)) ? 1 : 0;
   const int64_t npairs = n > head ? (n - head) / 2 : 0;
-  int64_t G = grid > 0 ? grid : (int64_t)device_sm_count() * 4;
+  int occ = 1;
+  if (filter == HULL_FILTER_FP32)
+    occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes32<0>) : occupancy(k_extremes32<1>);
+  else
+    occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes64<0>) : occupancy(k_extremes64<1>);
+  int64_t G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
   G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + STEP - 1) / STEP));
   int64_t ppb = (npairs + G - 1) / G;
   ppb = (ppb + STEP - 1) / STEP * STEP;

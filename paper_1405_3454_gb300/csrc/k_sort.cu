@@ -20,9 +20,12 @@ constexpr int PER_WARP = SORT_TILE / WARPS;  // 512
 constexpr int ROWS = PER_WARP / 32;          // 16
 static_assert(SORT_TILE == SBLOCK * ROWS, "tile shape");
 
-__device__ __forceinline__ int64_t dev_count(const WsHeader* h) {
+// Element count of the large path: 0 (nothing to do) when the one-block
+// path takes the set.
+__device__ __forceinline__ int64_t dev_count(const WsHeader* h, const unsigned long long* count) {
   if (*reinterpret_cast<const volatile uint32_t*>(&h->status)) return 0;
-  return (int64_t)*reinterpret_cast<const volatile unsigned long long*>(&h->n_surv);
+  const int64_t m = (int64_t)*reinterpret_cast<const volatile unsigned long long*>(count);
+  return m > SMALL_MAX ? m : 0;
 }
 
 __device__ __forceinline__ uint32_t digit(unsigned long long k, int pass) {
@@ -31,11 +34,11 @@ __device__ __forceinline__ uint32_t digit(unsigned long long k, int pass) {
 
 // Digit histograms of all passes in one read (they do not depend on order).
 __global__ void __launch_bounds__(SBLOCK) k_hist_all(const unsigned long long* __restrict__ keys,
-                                                      WsHeader* h) {
+                                                      WsHeader* h, const unsigned long long* count) {
   __shared__ uint32_t hs[SORT_PASSES][256];
   for (int k = threadIdx.x; k < SORT_PASSES * 256; k += SBLOCK) (&hs[0][0])[k] = 0;
   __syncthreads();
-  const int64_t m = dev_count(h);
+  const int64_t m = dev_count(h, count);
   for (int64_t j = (int64_t)blockIdx.x * SBLOCK + threadIdx.x; j < m; j += (int64_t)gridDim.x * SBLOCK) {
     const unsigned long long k = keys[j];
 #pragma unroll
@@ -50,10 +53,10 @@ __global__ void __launch_bounds__(SBLOCK) k_hist_all(const unsigned long long* _
 
 // Per-tile digit counts: tilecnt[d * NT + t].
 __global__ void __launch_bounds__(SBLOCK) k_tile_count(const unsigned long long* __restrict__ keys,
-                                                        const WsHeader* h, int pass, int64_t NT,
-                                                        uint32_t* __restrict__ tilecnt) {
+                                                        const WsHeader* h, const unsigned long long* count,
+                                                        int pass, int64_t NT, uint32_t* __restrict__ tilecnt) {
   __shared__ uint32_t hs[256];
-  const int64_t m = dev_count(h);
+  const int64_t m = dev_count(h, count);
   const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
   for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
     hs[threadIdx.x] = 0;
@@ -74,12 +77,12 @@ __global__ void __launch_bounds__(SBLOCK) k_tile_count(const unsigned long long*
 
 // Exclusive scan over tiles of one digit's counts, offset by the number of
 // elements with a smaller digit.  One block per digit.
-__global__ void __launch_bounds__(1024) k_tile_scan(const WsHeader* h, int pass, int64_t NT,
-                                                     uint32_t* __restrict__ tilecnt) {
+__global__ void __launch_bounds__(1024) k_tile_scan(const WsHeader* h, const unsigned long long* count,
+                                                     int pass, int64_t NT, uint32_t* __restrict__ tilecnt) {
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   const int d = blockIdx.x;
-  const int64_t m = dev_count(h);
+  const int64_t m = dev_count(h, count);
   const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
@@ -123,10 +126,11 @@ __global__ void __launch_bounds__(SBLOCK) k_tile_scatter(const unsigned long lon
                                                           const uint32_t* __restrict__ vin,
                                                           unsigned long long* __restrict__ kout,
                                                           uint32_t* __restrict__ vout,
-                                                          const WsHeader* h, int pass, int64_t NT,
+                                                          const WsHeader* h, const unsigned long long* count,
+                                                          int pass, int64_t NT,
                                                           const uint32_t* __restrict__ tilecnt) {
   __shared__ uint32_t wc[WARPS][256];
-  const int64_t m = dev_count(h);
+  const int64_t m = dev_count(h, count);
   const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -177,25 +181,25 @@ __global__ void __launch_bounds__(SBLOCK) k_tile_scatter(const unsigned long lon
 
 }  // namespace
 
-cudaError_t launch_sort(int64_t cap, WsHeader* h, unsigned long long* keys_a, uint32_t* vals_a,
-                        unsigned long long* keys_b, uint32_t* vals_b, uint32_t* tilecnt,
-                        cudaStream_t st) {
+cudaError_t launch_sort(int64_t cap, WsHeader* h, const unsigned long long* count,
+                        unsigned long long* keys_a, uint32_t* vals_a, unsigned long long* keys_b,
+                        uint32_t* vals_b, uint32_t* tilecnt, cudaStream_t st) {
   const int64_t NT = sort_tiles(cap);
   const int sms = device_sm_count();
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(NT, (int64_t)sms * 8));
   const unsigned gh = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + SBLOCK - 1) / SBLOCK, (int64_t)sms * 8));
-  k_hist_all<<<gh, SBLOCK, 0, st>>>(keys_a, h);
+  k_hist_all<<<gh, SBLOCK, 0, st>>>(keys_a, h, count);
   count_launches(1);
   unsigned long long* kin = keys_a;
   uint32_t* vin = vals_a;
   unsigned long long* kout = keys_b;
   uint32_t* vout = vals_b;
   for (int p = 0; p < SORT_PASSES; ++p) {
-    k_tile_count<<<g, SBLOCK, 0, st>>>(kin, h, p, NT, tilecnt);
+    k_tile_count<<<g, SBLOCK, 0, st>>>(kin, h, count, p, NT, tilecnt);
     count_launches(1);
-    k_tile_scan<<<256, 1024, 0, st>>>(h, p, NT, tilecnt);
+    k_tile_scan<<<256, 1024, 0, st>>>(h, count, p, NT, tilecnt);
     count_launches(1);
-    k_tile_scatter<<<g, SBLOCK, 0, st>>>(kin, vin, kout, vout, h, p, NT, tilecnt);
+    k_tile_scatter<<<g, SBLOCK, 0, st>>>(kin, vin, kout, vout, h, count, p, NT, tilecnt);
     count_launches(1);
     std::swap(kin, kout);
     std::swap(vin, vout);

@@ -46,6 +46,7 @@ def test_defaults_and_strings(lib):
     o = cp.HullOptions()
     lib.hull_default_options(ctypes.byref(o))
     assert o.angles == cp.HULL_ANGLES_CUMULATIVE and o.filter == cp.HULL_FILTER_FP32 and o.validate == 0
+    assert o.refine == 1 and ctypes.sizeof(o) == 16 * 4
     for code in range(8):
         assert lib.hull_strerror(code).decode().startswith("HULL_")
     assert lib.hull_abi_version() == 1

@@ -42,8 +42,10 @@ def test_disk_2p28_bit_exact(gpu_lib, disk_and_oracle, filt):
     got = np.sort(cp.as_index(surv, ns))
     assert np.array_equal(got, ref["survivors"])
     del surv, ws
-    out, hcnt, ws2 = cp.compute(d, opt)
-    torch.cuda.synchronize()
-    assert cp.as_index(out, int(hcnt.item())).tolist() == ref["hull"].tolist()
+    for refine in (True, False):
+        out, hcnt, ws2 = cp.compute(d, cp.Options(filter=filt, refine=refine))
+        torch.cuda.synchronize()
+        assert cp.as_index(out, int(hcnt.item())).tolist() == ref["hull"].tolist()
+        del out, ws2
     # cumulative angles on a disk leave ~6.7 % outside the 12-gon
     assert 0.060 < ns / N < 0.072

@@ -61,10 +61,10 @@ def check_prefilter(cp, xy, angles, filt, offset=False):
     return ws
 
 
-def check_compute(cp, xy, angles, filt, offset=False):
+def check_compute(cp, xy, angles, filt, offset=False, refine=True):
     import torch
     d = to_dev(xy, offset)
-    out, cnt, ws = cp.compute(d, cp.Options(angles=angles, filter=filt))
+    out, cnt, ws = cp.compute(d, cp.Options(angles=angles, filter=filt, refine=refine))
     torch.cuda.synchronize()
     h = cp.as_index(out, int(cnt.item()))
     want = oracle.hull(xy)
@@ -92,12 +92,26 @@ def test_prefilter_unaligned_input(gpu_lib, n):
             check_compute(gpu_lib, xy, 0, filt, offset=True)
 
 
+@pytest.mark.parametrize("refine", [True, False])
 @pytest.mark.parametrize("angles,filt", MODES)
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 17, 1000, 4097, 65537, 300001])
-def test_compute_sizes(gpu_lib, n, angles, filt):
+def test_compute_sizes(gpu_lib, n, angles, filt, refine):
     for kind in (0, 1, 2):
         xy = synth.shape(kind, n, 11 + n, 70 + kind)
-        check_compute(gpu_lib, xy, angles, filt)
+        check_compute(gpu_lib, xy, angles, filt, refine=refine)
+
+
+@pytest.mark.parametrize("refine", [True, False])
+@pytest.mark.parametrize("k", [8190, 8192, 8193, 8200, 20000])
+def test_one_block_and_large_paths_at_the_boundary(gpu_lib, k, refine):
+    # Points in convex position survive every discard round, so the hull
+    # stage sees exactly k survivors: both sides of the one-block limit.
+    a = np.arange(k) * (2 * np.pi / k)
+    r = float(1 << 23)
+    xy = np.stack([np.round(r * np.cos(a)), np.round(r * np.sin(a))], 1).astype(np.float32)
+    inner = synth.disk(5000, 3, 1 << 20)
+    xy = np.concatenate([inner, xy]).astype(np.float32)
+    check_compute(gpu_lib, xy, 0, 1, refine=refine)
 
 
 def degenerate_sets():
@@ -127,6 +141,7 @@ def test_degenerate(gpu_lib, name, xy):
     for angles, filt in MODES:
         check_prefilter(gpu_lib, xy, angles, filt)
         check_compute(gpu_lib, xy, angles, filt)
+        check_compute(gpu_lib, xy, angles, filt, refine=False)
 
 
 def test_config1_square_1m(gpu_lib):
@@ -193,5 +208,8 @@ def test_workspace_reuse_back_to_back(gpu_lib):
     ws = gpu_lib.workspace(gpu_lib.hull_workspace_bytes(200_000))
     for xy in (a, b, a):
         out, cnt, _ = gpu_lib.compute(to_dev(xy), ws=ws)
+        torch.cuda.synchronize()
+        assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()
+        out, cnt, _ = gpu_lib.compute(to_dev(xy), gpu_lib.Options(refine=False), ws=ws)
         torch.cuda.synchronize()
         assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()
