@@ -252,7 +252,8 @@ def run_ours(args):
     clk = clocks.stop()
     stage_ms, calls = timer.read()
     per_call = {k: v / max(calls, 1) for k, v in stage_ms.items()}
-    n_surv, n_esc = cp.read_counters(ws)
+    stats = cp.read_stats(ws)
+    n_surv, n_esc, n_ref = stats["n_survivors"], stats["n_escalated"], stats["n_refined"]
     n_hull = int(cnt.item())
     value = world * n / (ms * 1e-3) / 1e9
 
@@ -333,7 +334,7 @@ def run_ours(args):
                          "fp32_filtered": {"value": value, "ms_per_step": ms},
                          "prefilter_only": prefilter},
             "stages_ms_per_step": stages_out,
-            "survivors": n_surv, "escalations": n_esc, "hull_vertices": n_hull,
+            "survivors": n_surv, "escalations": n_esc, "refined_survivors": n_ref, "hull_vertices": n_hull,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -137,6 +137,19 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
 hull_status hull_read_counters(const void* d_ws, int64_t* h_n_survivors,
                                int64_t* h_n_escalated, void* stream);
 
+/* Counters of the last hull_prefilter / hull_compute on a workspace. */
+typedef struct hull_stats {
+  int64_t n_survivors;      /* points not strictly inside the Step-2 polygon */
+  int64_t n_escalated;      /* float32 decisions escalated to exact arithmetic */
+  int64_t n_refined;        /* survivors left by the refinement round (hull_compute) */
+  int32_t polygon_vertices; /* vertices of the Step-2 polygon */
+  uint32_t device_status;   /* HULL_DEVICE_* bits */
+} hull_stats;
+
+/* Reads the counters of the last call on this workspace (host memory);
+ * synchronises the stream. */
+hull_status hull_read_stats(const void* d_ws, hull_stats* h_out, void* stream);
+
 /* The Step-2 polygon of the last call on this workspace: *h_m vertices,
  * h_xy[2k], h_xy[2k+1] their integer coordinates counter-clockwise from the
  * lexicographic minimum (room for 32 int32), h_idx[k] their point indices

@@ -35,7 +35,7 @@ NONE_IDX = 0xFFFFFFFF
 ABI_SYMBOLS = (
     "hull_default_options", "hull_prefilter_workspace_bytes", "hull_workspace_bytes",
     "hull_prefilter", "hull_compute", "hull_read_counters", "hull_read_polygon",
-    "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version",
+    "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version", "hull_read_stats",
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
 )
 HULL_STAGES = 5
@@ -46,6 +46,11 @@ class HullOptions(ctypes.Structure):
     _fields_ = [("angles", ctypes.c_int32), ("filter", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("refine", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 10)]
+
+
+class HullStats(ctypes.Structure):
+    _fields_ = [("n_survivors", ctypes.c_int64), ("n_escalated", ctypes.c_int64), ("n_refined", ctypes.c_int64),
+                ("polygon_vertices", ctypes.c_int32), ("device_status", ctypes.c_uint32)]
 
 
 class HullError(RuntimeError):
@@ -92,6 +97,8 @@ def load(path: str | None = None):
     lib.hull_constants.restype = None
     lib.hull_abi_version.argtypes = []
     lib.hull_abi_version.restype = ctypes.c_int32
+    lib.hull_read_stats.argtypes = [P, ctypes.POINTER(HullStats), P]
+    lib.hull_read_stats.restype = st
     lib.hull_timer_create.argtypes = [ctypes.c_int32]
     lib.hull_timer_create.restype = P
     lib.hull_timer_destroy.argtypes = [P]
@@ -225,6 +232,13 @@ def read_counters(ws, stream=None):
     _check(load().hull_read_counters(_ptr(ws), ctypes.byref(ns), ctypes.byref(ne), _stream_handle(stream)),
            "hull_read_counters")
     return int(ns.value), int(ne.value)
+
+
+def read_stats(ws, stream=None) -> dict:
+    """Counters of the last call on this workspace."""
+    o = HullStats()
+    _check(load().hull_read_stats(_ptr(ws), ctypes.byref(o), _stream_handle(stream)), "hull_read_stats")
+    return {k: int(getattr(o, k)) for k, _ in HullStats._fields_}
 
 
 def read_polygon(ws, stream=None):

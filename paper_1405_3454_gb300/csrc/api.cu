@@ -55,7 +55,7 @@ constexpr int64_t MAX_N = 0xFFFFFFFFll;  // indices are uint32
 constexpr int64_t MAX_BLOCKS = 4096;     // per-block partials of the extreme search
 
 struct Layout {
-  size_t header = 0, blockres = 0, cells = 0, tri = 0, keys_a = 0, vals_a = 0, keys_b = 0, vals_b = 0, tilecnt = 0,
+  size_t header = 0, blockres = 0, cells = 0, tri = 0, small = 0, keys_a = 0, vals_a = 0, keys_b = 0, vals_b = 0, tilecnt = 0,
          cnt = 0, total = 0;
 };
 
@@ -66,10 +66,11 @@ Layout layout(int64_t n, bool full) {
   L.blockres = off;
   off += align_up(sizeof(BlockBest) * NSLOT * MAX_BLOCKS, 256);
   L.cells = off;
-  off += align_up(sizeof(uint16_t) * GRID * GRID, 256);
+  off += align_up(CELL_BYTES, 256);
   if (full) {
     const int64_t cap = std::max<int64_t>(n, 1);
     L.tri = off; off += align_up(sizeof(int4) * 2 * REFINE_BINS, 256);
+    L.small = off; off += align_up(sizeof(SmallWs), 256);
     L.keys_a = off; off += align_up(8 * (size_t)cap, 256);
     L.vals_a = off; off += align_up(4 * (size_t)cap, 256);
     L.keys_b = off; off += align_up(8 * (size_t)cap, 256);
@@ -115,8 +116,8 @@ hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& 
   HULL_TRY(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
   if (o.validate) HULL_TRY(launch_validate(d_xy, n, h, st));
   mark(1, st);
-  HULL_TRY(launch_extremes(d_xy, n, o.angles, o.filter, h,
-                           reinterpret_cast<BlockBest*>(ws + L.blockres), o.grid, o.block, ext_out, st));
+  HULL_TRY(launch_extremes(d_xy, n, o.angles, o.filter, h, ws + L.blockres,
+                           reinterpret_cast<uint16_t*>(ws + L.cells), o.grid, o.block, ext_out, st));
   mark(2, st);
   HULL_TRY(launch_filter(d_xy, n, o.filter, h, reinterpret_cast<uint16_t*>(ws + L.cells), surv_idx,
                          surv_key, o.grid, o.block, st));
@@ -235,7 +236,8 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
     kin = kb; vin = vb; kot = ka; vot = va;
     count = &h->n_surv2;
   }
-  HULL_TRY(launch_small_hull(kin, vin, count, h, d_hull_idx, d_n_hull, st));
+  HULL_TRY(launch_small_hull(kin, vin, count, h, reinterpret_cast<SmallWs*>(ws + L.small), d_hull_idx, d_n_hull,
+                             st));
   HULL_TRY(launch_sort(cap, h, count, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt), st));
   mark(4, st);
   HULL_TRY(launch_chain(cap, h, count, kot, vot, kin, vin, reinterpret_cast<uint32_t*>(ws + L.cnt), d_hull_idx,
@@ -253,6 +255,20 @@ hull_status hull_read_counters(const void* d_ws, int64_t* h_n_survivors, int64_t
   HULL_TRY(cudaStreamSynchronize(st));
   if (h_n_survivors) *h_n_survivors = (int64_t)hh.n_surv;
   if (h_n_escalated) *h_n_escalated = (int64_t)hh.n_escalated;
+  return HULL_OK;
+}
+
+hull_status hull_read_stats(const void* d_ws, hull_stats* h_out, void* stream) {
+  if (!d_ws || !h_out) return HULL_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader hh;
+  HULL_TRY(cudaMemcpyAsync(&hh, d_ws, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
+  HULL_TRY(cudaStreamSynchronize(st));
+  h_out->n_survivors = (int64_t)hh.n_surv;
+  h_out->n_escalated = (int64_t)hh.n_escalated;
+  h_out->n_refined = (int64_t)hh.n_surv2;
+  h_out->polygon_vertices = hh.poly.m;
+  h_out->device_status = hh.status;
   return HULL_OK;
 }
 

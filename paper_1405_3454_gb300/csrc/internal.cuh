@@ -24,14 +24,24 @@ constexpr float F_C75 = (float)K_C75;
 constexpr float F_S75 = (float)K_S75;
 constexpr float F_H = (float)K_H;
 
-// Error bound of the float32 projections against the binary64 definition.
-// For |x|, |y| <= 2^24 every float32 form used below is within 2.5 of the
-// binary64 value (coefficient rounding <= 0.5 + 0.5, product rounding <= 0.5,
-// final rounding <= 1); E_PROJ = 8 leaves a factor of three.  Two candidates
-// whose float32 scores differ by more than BAND = 2 * E_PROJ are ordered by
-// their float32 scores; otherwise the binary64 definition decides.
-constexpr float E_PROJ = 8.0f;
-constexpr float BAND = 2.0f * E_PROJ;
+// Float32 values of the extreme search.  Each tracked value is a positive
+// multiple k of a rotated coordinate (the order of the points is unchanged),
+// chosen so that one fused multiply-add computes it:
+//   30 and 60 degrees: k = 2, e.g. 2 x'(30) = fma(x, 2 s3, -y);
+//   75 degrees:        k = 1/c75, x'(75)/c75 = fma(y, -tan75, x);
+//   45 degrees:        k = 1/h,   x'(45)/h = x - y.
+// For |x|, |y| <= 2^24 the float32 value is within 3 (30, 45 and 60 degrees)
+// or 6 (75 degrees) of k times the binary64 definition: coefficient rounding
+// (|y| * half an ulp of the coefficient) plus the final rounding (half an ulp
+// of a result below 2^26 resp. 2^27).  Two candidates whose float32 values
+// differ by more than BAND_LO = 16 resp. BAND_HI = 32 -- over twice the sum of
+// their errors -- are ordered by the float32 values; otherwise the binary64
+// definition decides.
+constexpr float BAND_LO = 16.0f;
+constexpr float BAND_HI = 32.0f;
+constexpr float F_2S3 = (float)(2.0 * K_S3);
+// tan(75 degrees) = 2 + sqrt(3), correctly rounded to float
+constexpr float F_T75 = 0x1.ddb3d8p+1f;
 
 constexpr int MAXV = 16;          // polygon vertices (16 extremes at most)
 constexpr int NSLOT = 16;         // extreme slots
@@ -52,6 +62,10 @@ struct Edge {
 // cell is strictly inside (discard without a test).
 constexpr int GRID_LOG = 7;
 constexpr int GRID = 1 << GRID_LOG;
+// Cell storage in the workspace: GRID*GRID uint16 edge masks, then GRID*GRID
+// byte codes (0: inside, k + 1: only edge k, CELL_MULTI: see the mask).
+constexpr int CELL_MULTI = 255;
+constexpr size_t CELL_BYTES = (size_t)GRID * GRID * 3;
 
 struct Poly {
   int32_t m;            // vertex count (0..16); < 3 discards nothing
@@ -123,8 +137,10 @@ void count_launches(int k);
 
 // Launchers (one per translation unit); all enqueue on `st`.
 cudaError_t launch_validate(const float* xy, int64_t n, WsHeader* h, cudaStream_t st);
+// Steps 1-2 and the cell grid: the streaming search, then one finishing block.
+// `partials` holds the per-warp (float32) or per-block (binary64) candidates.
 cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, WsHeader* h,
-                            BlockBest* blockres, int grid, int block, uint32_t* ext_out,
+                            void* partials, uint16_t* cells, int grid, int block, uint32_t* ext_out,
                             cudaStream_t st);
 cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, uint16_t* cells,
                           uint32_t* surv_idx, unsigned long long* surv_key, int grid, int block,
@@ -145,8 +161,23 @@ constexpr int SMALL_MAX = 8192;           // survivor sets up to this size: one-
 cudaError_t launch_refine(WsHeader* h, const unsigned long long* keys_in, const uint32_t* vals_in,
                           unsigned long long* keys_out, uint32_t* vals_out, int4* tri, int64_t cap,
                           cudaStream_t st);
+// State of the small-set hull between its launches (in the workspace).
+constexpr int SMALL_NCH = 32;
+struct SmallWs {
+  int active;  // 1 when prune/emit have work
+  int u;       // distinct points
+  int C;       // chunk capacity
+  int pad_;
+  int cnt[2][SMALL_NCH];
+  int base[2][SMALL_NCH + 1];
+  int2 pts[SMALL_MAX];
+  uint32_t uid[SMALL_MAX];
+  uint16_t chain[2][SMALL_MAX];
+  uint8_t keep[2][SMALL_MAX];
+};
+
 cudaError_t launch_small_hull(const unsigned long long* keys, const uint32_t* vals,
-                              const unsigned long long* count, const WsHeader* h, uint32_t* out,
+                              const unsigned long long* count, const WsHeader* h, SmallWs* sw, uint32_t* out,
                               int64_t* out_n, cudaStream_t st);
 
 // Sizes used by the sort and chain stages.

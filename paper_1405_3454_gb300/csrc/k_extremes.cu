@@ -8,15 +8,18 @@
 // rotation kernels and per-direction reductions (section 4.2) become one
 // fused projection + argreduction; no rotated copy is ever written.
 //
-// FP32 mode: projections are float32 (<= 2.5 from the binary64 definition);
-// a tile of 8 points per thread is skipped for a direction when its float32
-// maximum cannot reach the block's best so far, and float32 scores closer
-// than BAND are ordered by the binary64 definition, so the chosen indices are
-// exactly those of the definition.  EXACT mode evaluates the binary64
-// definition for every point.
+// FP32 mode: each direction tracks a float32 value, an order-preserving
+// multiple of the rotated coordinate that one fused multiply-add computes,
+// with a proven error bound (internal.cuh); a tile of 8 points per thread is
+// skipped for a direction when its float32 maximum cannot reach the block's
+// best so far, and float32 values closer than the direction's band are
+// ordered by the binary64 definition, so the chosen indices are exactly those
+// of the definition.  EXACT mode evaluates the binary64 definition for every
+// point.
 #include <cfloat>
 
 #include "internal.cuh"
+#include "stream.cuh"
 
 namespace cudapre {
 
@@ -61,25 +64,36 @@ __device__ __forceinline__ double score64(int ang, int d, float x, float y) {
   return (d & 1) ? v : -v;
 }
 
-// Float32 values of one point (error <= 2.5 against value64, see E_PROJ).
+// Order-preserving unsigned key of a (non-NaN) double: integer comparisons
+// of keys order the doubles (FP64 compares are slow on this part).
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// Float32 values of one point: order-preserving multiples of the rotated
+// coordinates (see BAND_LO / BAND_HI for the scales and error bounds).
 template <int ANG>
 __device__ __forceinline__ void values32(float x, float y, float* v) {
   v[0] = x;
   v[1] = y;
-  const float hx = 0.5f * x, hy = 0.5f * y;
-  v[2] = fmaf(x, F_S3, -hy);  // x s3 - y/2
-  v[3] = fmaf(y, F_S3, hx);   // x/2 + y s3
+  v[2] = fmaf(x, F_2S3, -y);  // 2 x'(30) = 2 s3 x - y
+  v[3] = fmaf(y, F_2S3, x);   // 2 y'(30) = x + 2 s3 y
   if (ANG == 0) {
-    const float p = y * F_S75, q = y * F_C75;
-    v[4] = fmaf(x, F_C75, -p);  // x c75 - y s75
-    v[5] = fmaf(x, F_S75, q);   // x s75 + y c75
+    v[4] = fmaf(y, -F_T75, x);  // x'(75) / c75 = x - tan75 y
+    v[5] = fmaf(x, F_T75, y);   // y'(75) / c75 = tan75 x + y
   } else {
-    const float a = x * F_H, b = y * F_H;
-    v[4] = a - b;               // (x - y) h
-    v[5] = a + b;               // (x + y) h
-    v[6] = fmaf(-y, F_S3, hx);  // x/2 - y s3
-    v[7] = fmaf(x, F_S3, hy);   // x s3 + y/2
+    v[4] = x - y;               // x'(45) / h
+    v[5] = x + y;               // y'(45) / h
+    v[6] = fmaf(-y, F_2S3, x);  // 2 x'(60) = x - 2 s3 y
+    v[7] = fmaf(x, F_2S3, y);   // 2 y'(60) = 2 s3 x + y
   }
+}
+
+// Band of value v (exact group 0: no band).
+template <int ANG>
+__device__ __forceinline__ float band_of(int v) {
+  return v < 2 ? 0.0f : ((ANG == 0 && v >= 4) ? BAND_HI : BAND_LO);
 }
 
 template <int ANG>
@@ -87,6 +101,17 @@ __device__ __forceinline__ float value32(int v, float x, float y) {
   float t[Dirs<ANG>::NV];
   values32<ANG>(x, y, t);
   return t[v];
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
 }
 
 __device__ __forceinline__ float2 load_point(const float* xy, uint32_t i) {
@@ -105,9 +130,9 @@ __device__ __forceinline__ bool better32(int d, float sa, uint32_t ia, float sb,
   if (ib == NONE) return true;
   if (ia == ib) return false;
   if (d < 4) return sa > sb || (sa == sb && ia < ib);
-  const float diff = sa - sb;
-  if (diff > BAND) return true;
-  if (diff < -BAND) return false;
+  const float diff = sa - sb, band = band_of<ANG>(d >> 1);
+  if (diff > band) return true;
+  if (diff < -band) return false;
   const float2 pa = load_point(xy, ia), pb = load_point(xy, ib);
   const double ea = score64(ANG, d, pa.x, pa.y), eb = score64(ANG, d, pb.x, pb.y);
   return ea > eb || (ea == eb && ia < ib);
@@ -141,39 +166,6 @@ __device__ __forceinline__ float4 lds_vol4(const float* p) {
   return r;
 }
 
-// Offer point (x, y, i) with float32 value `val` to direction d's running
-// best of this thread; on a win, lower the block's trigger threshold.
-template <int ANG>
-__device__ __forceinline__ void offer32(int d, float val, float x, float y, uint32_t i,
-                                        float& best, uint32_t& bidx, float* thr,
-                                        const float* xy) {
-  const float s = (d & 1) ? val : -val;
-  bool take;
-  if (bidx == NONE) {
-    take = true;
-  } else if (d < 4) {
-    take = s > best || (s == best && i < bidx);
-  } else {
-    const float diff = s - best;
-    if (diff > BAND) {
-      take = true;
-    } else if (diff < -BAND) {
-      take = false;
-    } else {
-      const float2 pb = load_point(xy, bidx);
-      const double e = score64(ANG, d, x, y), eb = score64(ANG, d, pb.x, pb.y);
-      take = e > eb || (e == eb && i < bidx);
-    }
-  }
-  if (take) {
-    best = s;
-    bidx = i;
-    const float band = d < 4 ? 0.0f : BAND;
-    if (d & 1) atomic_max_f(&thr[d], val - band);
-    else atomic_min_f(&thr[d], val + band);
-  }
-}
-
 // ----------------------------------------------------------------------------
 // Step 2: the convex polygon of the extremes (Andrew's monotone chain, one
 // warp), plus the per-edge records and the inner box used by Step 3.
@@ -192,65 +184,71 @@ __device__ void build_edges_and_box(Poly* P, int m, int lane) {
     // orientation for |px|, |py| <= M (primes: float32-rounded coefficients):
     //   |s - S'| <= u|A'|M + (2u + u^2)(|B'|M + |C'|)   (two fma roundings)
     //   |S' - S| <= u(|A| + |B|)M + u|C|               (coefficient roundings)
-    // with u = 2^-24, M = 2^24; doubled for safety and rounded up.
-    const double u = 0x1p-24, M = 16777216.0;
-    const double bnd = u * fabs((double)e.A) * M +
-                       (2.0 * u + u * u) * (fabs((double)e.B) * M + fabs((double)e.C)) +
-                       u * (fabs((double)A) + fabs((double)B)) * M + u * fabs((double)C);
-    e.E = __double2float_ru(2.0 * bnd);
+    // with u = 2^-24, M = 2^24, so uM = 1:
+    //   E = |A'| + (2 + u)|B'| + (2 + u) u |C'| + |A| + |B| + u|C|,
+    // evaluated in float32 rounding every step upward (a rigorous upper
+    // bound; 2 + 2^-22 >= 2 + u), then doubled for safety.
+    const float k2 = 2.0000002384185791f;  // 2 + 2^-22
+    const float aA = __ll2float_ru(A < 0 ? -A : A), aB = __ll2float_ru(B < 0 ? -B : B);
+    const float aC = __ll2float_ru(C < 0 ? -C : C);
+    float E = __fadd_ru(fabsf(e.A), __fmul_ru(k2, fabsf(e.B)));
+    E = __fadd_ru(E, __fmul_ru(__fmul_ru(k2, fabsf(e.C)), 0x1p-24f));
+    E = __fadd_ru(E, __fadd_ru(aA, aB));
+    E = __fadd_ru(E, __fmul_ru(aC, 0x1p-24f));
+    e.E = 2.0f * E;
     e.ax = (int32_t)ax;
     e.ay = (int32_t)ay;
     e.dx = (int32_t)dx;
     e.dy = (int32_t)dy;
     P->e[lane] = e;
   }
-  if (lane == 0) {
-    float box[4] = {1.0f, 0.0f, 1.0f, 0.0f};  // empty
-    if (m >= 3) {
-      // Axis-aligned box around the vertex mean with the aspect of the
-      // bounding box, grown until a corner meets an edge (double), rounded
-      // inward to integers and then verified exactly: its 4 corners strictly
-      // inside make every point of the closed box strictly inside.
-      double cx = 0, cy = 0;
-      int xl = P->vx[0], xh = P->vx[0], yl = P->vy[0], yh = P->vy[0];
-      for (int k = 0; k < m; ++k) {
-        cx += P->vx[k];
-        cy += P->vy[k];
-        xl = min(xl, P->vx[k]); xh = max(xh, P->vx[k]);
-        yl = min(yl, P->vy[k]); yh = max(yh, P->vy[k]);
-      }
-      cx /= m;
-      cy /= m;
-      const double wx = 0.5 * ((double)xh - xl), wy = 0.5 * ((double)yh - yl);
-      double t = 1.0;
-      for (int k = 0; k < m; ++k) {
-        const int j = (k + 1) % m;
-        const double A = -((double)P->vy[j] - P->vy[k]), B = (double)P->vx[j] - P->vx[k];
-        const double S = A * (cx - P->vx[k]) + B * (cy - P->vy[k]);
-        for (int c = 0; c < 4; ++c) {
-          const double sl = A * ((c & 1) ? wx : -wx) + B * ((c & 2) ? wy : -wy);
-          if (sl < 0 && S > 0) t = fmin(t, S / -sl);
-        }
-      }
-      t *= 0.98;
-      for (int it = 0; it < 60 && t > 1e-12; ++it, t *= 0.5) {
-        const long long x0 = (long long)ceil(cx - t * wx), x1 = (long long)floor(cx + t * wx);
-        const long long y0 = (long long)ceil(cy - t * wy), y1 = (long long)floor(cy + t * wy);
-        if (x0 > x1 || y0 > y1) break;
-        bool ok = true;
-        for (int c = 0; c < 4 && ok; ++c) {
-          const long long px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
-          for (int k = 0; k < m && ok; ++k) {
-            const int j = (k + 1) % m;
-            ok = orient64(P->vx[k], P->vy[k], P->vx[j], P->vy[j], px, py) > 0;
-          }
-        }
-        if (ok) {
-          box[0] = (float)x0; box[1] = (float)x1; box[2] = (float)y0; box[3] = (float)y1;
-          break;
-        }
+  // Inner box: axis-aligned, around the vertex mean with the aspect of the
+  // bounding box, grown until a corner meets an edge (float estimate),
+  // rounded inward to integers and verified exactly (lane k checks edge k):
+  // its 4 corners strictly inside make every point of the closed box
+  // strictly inside.
+  float box[4] = {1.0f, 0.0f, 1.0f, 0.0f};  // empty
+  if (m >= 3) {
+    float cx = 0, cy = 0;
+    int xl = P->vx[0], xh = P->vx[0], yl = P->vy[0], yh = P->vy[0];
+    for (int k = 0; k < m; ++k) {
+      cx += (float)P->vx[k];
+      cy += (float)P->vy[k];
+      xl = min(xl, P->vx[k]); xh = max(xh, P->vx[k]);
+      yl = min(yl, P->vy[k]); yh = max(yh, P->vy[k]);
+    }
+    cx /= (float)m;
+    cy /= (float)m;
+    const float wx = 0.5f * ((float)xh - (float)xl), wy = 0.5f * ((float)yh - (float)yl);
+    float t = 1.0f;
+    if (lane < m) {
+      const int j = (lane + 1) % m;
+      const float A = -((float)P->vy[j] - (float)P->vy[lane]), B = (float)P->vx[j] - (float)P->vx[lane];
+      const float S = A * (cx - (float)P->vx[lane]) + B * (cy - (float)P->vy[lane]);
+      for (int c = 0; c < 4; ++c) {
+        const float sl = A * ((c & 1) ? wx : -wx) + B * ((c & 2) ? wy : -wy);
+        if (sl < 0 && S > 0) t = fminf(t, S / -sl);
       }
     }
+    for (int off = 16; off; off >>= 1) t = fminf(t, __shfl_xor_sync(FULL, t, off));
+    t *= 0.98f;
+    for (int it = 0; it < 60 && t > 1e-12f; ++it, t *= 0.5f) {
+      const long long x0 = (long long)ceilf(cx - t * wx), x1 = (long long)floorf(cx + t * wx);
+      const long long y0 = (long long)ceilf(cy - t * wy), y1 = (long long)floorf(cy + t * wy);
+      if (x0 > x1 || y0 > y1) break;
+      bool ok = true;
+      if (lane < m) {
+        const int j = (lane + 1) % m;
+        for (int c = 0; c < 4; ++c)
+          ok = ok && orient64(P->vx[lane], P->vy[lane], P->vx[j], P->vy[j], (c & 1) ? x1 : x0, (c & 2) ? y1 : y0) > 0;
+      }
+      if (__all_sync(FULL, ok)) {
+        box[0] = (float)x0; box[1] = (float)x1; box[2] = (float)y0; box[3] = (float)y1;
+        break;
+      }
+    }
+  }
+  if (lane == 0) {
     for (int c = 0; c < 4; ++c) P->box[c] = box[c];
     // An integer point strictly inside: the centre of a non-empty inner box.
     P->refine_on = box[0] <= box[1] ? 1 : 0;
@@ -347,173 +345,179 @@ __device__ void hull16_warp(const float* xy, const uint32_t* ext, Poly* P) {
 }
 
 // ----------------------------------------------------------------------------
-// Grid-level reduction of the per-block bests (binary64 scores, exact), run
-// by the last block; then Step 2.
-
-template <int ANG>
-__device__ void finish_last_block(const float* xy, int64_t n, WsHeader* h,
-                                  const BlockBest* blockres, uint32_t* ext_out) {
-  constexpr int ND = Dirs<ANG>::ND;
-  __shared__ uint32_t s_ext[NSLOT];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const int G = gridDim.x;
-  for (int d = warp; d < ND; d += nwarps) {
-    double bs = -DBL_MAX;
-    uint32_t bi = NONE;
-    for (int k = lane; k < G; k += 32) {
-      const double s = __ldcg(&blockres[(size_t)k * ND + d].s);
-      const uint32_t i = __ldcg(&blockres[(size_t)k * ND + d].idx);
-      if (i != NONE && (bi == NONE || s > bs || (s == bs && i < bi))) { bs = s; bi = i; }
-    }
-    for (int off = 16; off; off >>= 1) {
-      const double so = __shfl_xor_sync(FULL, bs, off);
-      const uint32_t io = __shfl_xor_sync(FULL, bi, off);
-      if (io != NONE && (bi == NONE || so > bs || (so == bs && io < bi))) { bs = so; bi = io; }
-    }
-    if (lane == 0) s_ext[d] = bi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (ANG == 0) {
-      // 120 degrees from 30 degrees: with the correctly rounded constants,
-      // x'(120) = -y'(30) and y'(120) = x'(30) exactly.
-      s_ext[12] = s_ext[7];  // argmin x'120 = argmax y'30
-      s_ext[13] = s_ext[6];  // argmax x'120 = argmin y'30
-      s_ext[14] = s_ext[4];  // argmin y'120 = argmin x'30
-      s_ext[15] = s_ext[5];  // argmax y'120 = argmax x'30
-    }
-    if (h->status) for (int k = 0; k < NSLOT; ++k) s_ext[k] = NONE;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    if (ext_out && lane < NSLOT) ext_out[lane] = s_ext[lane];
-    hull16_warp(xy, s_ext, &h->poly);
-  }
-}
-
-template <int ANG>
-__device__ bool last_block_arrives(WsHeader* h) {
-  __shared__ bool s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&h->done_blocks, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (s_last) __threadfence();
-  return s_last;
-}
-
-// ----------------------------------------------------------------------------
 // FP32-filtered extreme search.
 //
-// The running best of every thread and direction lives in shared memory: it
-// is touched only when a tile can improve on the block's best, which is rare
-// once the block-wide thresholds have risen.  The streaming loop therefore
-// keeps only the current and the next tile in registers (8 points each), so
-// four blocks fit on an SM and 32 bytes per thread are always in flight.
+// The points stream through shared memory (stream.cuh): a producer warp
+// issues bulk copies of 1024 pairs per stage and eight consumer warps take
+// 8 points each per stage.  The running best of every thread and direction
+// lives in shared memory: it is touched only when a tile can improve on the
+// block's best, which is rare once the block-wide thresholds have risen.
+// That rare path re-reads its tile from global memory (an L2 hit), so the
+// streaming loop keeps no indexed arrays.  Each warp seeds the thresholds
+// from its first tile with atomics; the loop has no block-wide barrier.
 
+// Rare path, run by the whole warp when any lane's tile may improve on the
+// block's best for value k (min if lo, max if hi).  Each lane picks its best
+// tile point, a butterfly of exact comparisons picks the warp's, and lane 0
+// merges it into the warp's running best (shared memory) and lowers the
+// block threshold.  The tile is re-read from global memory (an L2 hit);
+// f = first pair of the chunk, cnt = its pairs.
 template <int ANG>
-__global__ void __launch_bounds__(BLOCK, 3) k_extremes32(const float* __restrict__ xy, int64_t n,
-                                                          int head, int64_t npairs, int64_t ppb,
-                                                          WsHeader* h, BlockBest* blockres,
-                                                          uint32_t* ext_out) {
-  constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
-  __shared__ __align__(16) float thr[ND];  // trigger thresholds in value space
-  __shared__ float s_best[ND][BLOCK];
-  __shared__ uint32_t s_bidx[ND][BLOCK];
-  __shared__ float s_red[BLOCK / 32][ND];
-  __shared__ uint32_t s_redi[BLOCK / 32][ND];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool dead = *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
-#pragma unroll
-  for (int d = 0; d < ND; ++d) { s_best[d][tid] = -FLT_MAX; s_bidx[d][tid] = NONE; }
-
-  const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
-  const int64_t p0 = (int64_t)blockIdx.x * ppb;
-  const int64_t p1 = dead ? p0 : min(p0 + ppb, npairs);
-  const int64_t nsteps = p1 > p0 ? (p1 - p0 + STEP - 1) / STEP : 0;
-
-  float4 cur[PAIRS_PER_THREAD];
-  auto load = [&](int64_t base, float4* v) {
-#pragma unroll
-    for (int j = 0; j < PAIRS_PER_THREAD; ++j) {
-      const int64_t pp = base + j * BLOCK + tid;
-      v[j] = __ldg(P + (pp < p1 ? pp : p0));  // out of range: repeat a real point
+__device__ __noinline__ void ext_slow(int k, bool lo, bool hi, int64_t f, int cnt, const float4* P, int head,
+                                      float* thr, float* wbest, uint32_t* widx, const float* xy) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  float s_lo = -FLT_MAX, s_hi = -FLT_MAX;
+  uint32_t i_lo = NONE, i_hi = NONE;
+  const float t_lo = *reinterpret_cast<volatile float*>(&thr[2 * k]);
+  const float t_hi = *reinterpret_cast<volatile float*>(&thr[2 * k + 1]);
+  for (int j = 0; j < 8; ++j) {
+    const int o = (j >> 1) * CONSUMERS + tid;
+    const int64_t q = f + (o < cnt ? o : 0);  // out of range: repeat a real point
+    const float4 v = __ldg(P + q);
+    const float x = (j & 1) ? v.z : v.x, y = (j & 1) ? v.w : v.y;
+    const uint32_t i = (uint32_t)(head + 2 * q) + (j & 1);
+    const float val = value32<ANG>(k, x, y);
+    if (lo && val <= t_lo && better32<ANG>(2 * k, -val, i, s_lo, i_lo, xy)) { s_lo = -val; i_lo = i; }
+    if (hi && val >= t_hi && better32<ANG>(2 * k + 1, val, i, s_hi, i_hi, xy)) { s_hi = val; i_hi = i; }
+  }
+  for (int off = 16; off; off >>= 1) {
+    const float a = __shfl_xor_sync(FULL, s_lo, off), b = __shfl_xor_sync(FULL, s_hi, off);
+    const uint32_t ia = __shfl_xor_sync(FULL, i_lo, off), ib = __shfl_xor_sync(FULL, i_hi, off);
+    if (better32<ANG>(2 * k, a, ia, s_lo, i_lo, xy)) { s_lo = a; i_lo = ia; }
+    if (better32<ANG>(2 * k + 1, b, ib, s_hi, i_hi, xy)) { s_hi = b; i_hi = ib; }
+  }
+  if (lane == 0) {
+    const float band = band_of<ANG>(k);
+    if (better32<ANG>(2 * k, s_lo, i_lo, wbest[2 * k], widx[2 * k], xy)) {
+      wbest[2 * k] = s_lo;
+      widx[2 * k] = i_lo;
+      atomic_min_f(&thr[2 * k], -s_lo + band);
     }
-  };
-  if (nsteps > 0) load(p0, cur);
-  for (int64_t st = 0; st < nsteps; ++st) {
-    const int64_t base = p0 + st * BLOCK * PAIRS_PER_THREAD;
-    float4 nxt[PAIRS_PER_THREAD];
-    if (st + 1 < nsteps) load(base + STEP, nxt);
-    float px[2 * PAIRS_PER_THREAD], py[2 * PAIRS_PER_THREAD];
-#pragma unroll
-    for (int j = 0; j < PAIRS_PER_THREAD; ++j) {
-      px[2 * j] = cur[j].x; py[2 * j] = cur[j].y; px[2 * j + 1] = cur[j].z; py[2 * j + 1] = cur[j].w;
-    }
-    float tmin[NV], tmax[NV];
-    {
-      float v[NV];
-      values32<ANG>(px[0], py[0], v);
-#pragma unroll
-      for (int k = 0; k < NV; ++k) { tmin[k] = v[k]; tmax[k] = v[k]; }
-#pragma unroll
-      for (int j = 1; j < 2 * PAIRS_PER_THREAD; ++j) {
-        values32<ANG>(px[j], py[j], v);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) { tmin[k] = fminf(tmin[k], v[k]); tmax[k] = fmaxf(tmax[k], v[k]); }
-      }
-    }
-    if (st == 0) {
-      // Seed the block's thresholds from the first tile of every thread.
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        float a = tmin[k], b = tmax[k];
-        for (int off = 16; off; off >>= 1) {
-          a = fminf(a, __shfl_xor_sync(FULL, a, off));
-          b = fmaxf(b, __shfl_xor_sync(FULL, b, off));
-        }
-        if (lane == 0) { s_red[warp][2 * k] = a; s_red[warp][2 * k + 1] = b; }
-      }
-      __syncthreads();
-      if (tid < ND) {
-        float r = s_red[0][tid];
-        for (int w = 1; w < BLOCK / 32; ++w) r = (tid & 1) ? fmaxf(r, s_red[w][tid]) : fminf(r, s_red[w][tid]);
-        const float band = tid < 4 ? 0.0f : BAND;
-        thr[tid] = (tid & 1) ? r - band : r + band;
-      }
-      __syncthreads();
-    }
-    float t[ND];
-#pragma unroll
-    for (int q = 0; q < ND / 4; ++q) {
-      const float4 v = lds_vol4(&thr[4 * q]);
-      t[4 * q] = v.x; t[4 * q + 1] = v.y; t[4 * q + 2] = v.z; t[4 * q + 3] = v.w;
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      const bool lo = tmin[k] <= t[2 * k], hi = tmax[k] >= t[2 * k + 1];
-      if (lo || hi) {
-#pragma unroll 1
-        for (int j = 0; j < 2 * PAIRS_PER_THREAD; ++j) {
-          const float val = value32<ANG>(k, px[j], py[j]);
-          const int64_t pp = base + (j >> 1) * BLOCK + tid;
-          const uint32_t i = (uint32_t)(head + 2 * (pp < p1 ? pp : p0)) + (j & 1);
-          if (lo && val <= *reinterpret_cast<volatile float*>(&thr[2 * k]))
-            offer32<ANG>(2 * k, val, px[j], py[j], i, s_best[2 * k][tid], s_bidx[2 * k][tid], thr, xy);
-          if (hi && val >= *reinterpret_cast<volatile float*>(&thr[2 * k + 1]))
-            offer32<ANG>(2 * k + 1, val, px[j], py[j], i, s_best[2 * k + 1][tid], s_bidx[2 * k + 1][tid],
-                         thr, xy);
-        }
-      }
-    }
-    if (st + 1 < nsteps) {
-#pragma unroll
-      for (int j = 0; j < PAIRS_PER_THREAD; ++j) cur[j] = nxt[j];
+    if (better32<ANG>(2 * k + 1, s_hi, i_hi, wbest[2 * k + 1], widx[2 * k + 1], xy)) {
+      wbest[2 * k + 1] = s_hi;
+      widx[2 * k + 1] = i_hi;
+      atomic_max_f(&thr[2 * k + 1], s_hi - band);
     }
   }
+  __syncwarp();
+}
+
+template <int ANG>
+__device__ __forceinline__ void ext_minmax(const float4& a, const float4& b, const float4& c, const float4& d,
+                                           float* tmin, float* tmax) {
+  // running min/max with three-input operations, two points at a time, so
+  // only two points' values are live
+  constexpr int NV = Dirs<ANG>::NV;
+  float v[NV], w[NV];
+  values32<ANG>(a.x, a.y, v);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) { tmin[k] = v[k]; tmax[k] = v[k]; }
+  auto pair = [&](float x0, float y0, float x1, float y1) {
+    values32<ANG>(x0, y0, v);
+    values32<ANG>(x1, y1, w);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { tmin[k] = min3f(tmin[k], v[k], w[k]); tmax[k] = max3f(tmax[k], v[k], w[k]); }
+  };
+  pair(a.z, a.w, b.x, b.y);
+  pair(b.z, b.w, c.x, c.y);
+  pair(c.z, c.w, d.x, d.y);
+  values32<ANG>(d.z, d.w, v);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) { tmin[k] = fminf(tmin[k], v[k]); tmax[k] = fmaxf(tmax[k], v[k]); }
+}
+
+// Warp-level seeding of the block thresholds from this warp's tile.
+template <int ANG>
+__device__ __forceinline__ void ext_seed(const float* tmin, const float* tmax, float* thr) {
+  constexpr int NV = Dirs<ANG>::NV;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float lo = tmin[k], hi = tmax[k];
+    for (int off = 16; off; off >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(FULL, lo, off));
+      hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, off));
+    }
+    if (lane == 0) {
+      const float band = band_of<ANG>(k);
+      atomic_min_f(&thr[2 * k], lo + band);
+      atomic_max_f(&thr[2 * k + 1], hi - band);
+    }
+  }
+  __syncwarp();
+}
+
+// Blocks per SM the streaming search is compiled for (registers per thread).
+#ifndef EXT_MIN_BLOCKS
+#define EXT_MIN_BLOCKS 3
+#endif
+
+template <int ANG>
+__global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(const float* __restrict__ xy, int64_t n,
+                                                                   int head, int64_t npairs, int64_t ppb,
+                                                                   WsHeader* h, BlockBest* bres) {
+  constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  using SS = StreamSmemT<3>;
+  SS& S = *reinterpret_cast<SS*>(dsm);
+  __shared__ __align__(16) float thr[ND];  // trigger thresholds in value space
+  __shared__ float w_best[CONSUMERS / 32][ND];   // per-warp running best (score space)
+  __shared__ uint32_t w_bidx[CONSUMERS / 32][ND];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool dead = *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
+  if (tid < CONSUMERS / 32 * ND) {
+    (&w_best[0][0])[tid] = -FLT_MAX;
+    (&w_bidx[0][0])[tid] = NONE;
+  }
+  if (tid < ND) thr[tid] = (tid & 1) ? -FLT_MAX : FLT_MAX;
+  stream_init(S);
+
+  const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
+  StreamRange R;
+  R.p0 = (int64_t)blockIdx.x * ppb;
+  R.p1 = dead ? R.p0 : min(R.p0 + ppb, npairs);
+  R.nchunks = R.p1 > R.p0 ? (R.p1 - R.p0 + CHUNK - 1) / CHUNK : 0;
+  R.reverse = false;
+
+  if (warp == PRODUCER_WARP) {
+    stream_produce(S, R, P, h);
+  } else {
+    for (int64_t c = 0; c < R.nchunks; ++c) {
+      const int s = (int)(c % SS::STAGES);
+      if (!mbar_wait(&S.full[s], (unsigned)((c / SS::STAGES) & 1), h)) break;
+      const int cnt = R.count(c);
+      const int64_t f = R.first_pair(c);
+      const float4* st = S.stage[s];
+      const float4 a = st[tid < cnt ? tid : 0];
+      const float4 b = st[tid + CONSUMERS < cnt ? tid + CONSUMERS : 0];
+      const float4 cc = st[tid + 2 * CONSUMERS < cnt ? tid + 2 * CONSUMERS : 0];
+      const float4 d = st[tid + 3 * CONSUMERS < cnt ? tid + 3 * CONSUMERS : 0];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.empty[s]);
+      float tmin[NV], tmax[NV];
+      ext_minmax<ANG>(a, b, cc, d, tmin, tmax);
+      if (c == 0) ext_seed<ANG>(tmin, tmax, thr);
+      float t[ND];
+#pragma unroll
+      for (int q = 0; q < ND / 4; ++q) {
+        const float4 v4 = lds_vol4(&thr[4 * q]);
+        t[4 * q] = v4.x; t[4 * q + 1] = v4.y; t[4 * q + 2] = v4.z; t[4 * q + 3] = v4.w;
+      }
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) any |= (tmin[k] <= t[2 * k]) | (tmax[k] >= t[2 * k + 1]);
+      if (__any_sync(FULL, any)) {  // rare: some lane's tile may improve a best
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          const bool lo = __any_sync(FULL, tmin[k] <= t[2 * k]), hi = __any_sync(FULL, tmax[k] >= t[2 * k + 1]);
+          if (lo || hi) ext_slow<ANG>(k, lo, hi, f, cnt, P, head, thr, w_best[warp], w_bidx[warp], xy);
+        }
+      }
+    }
+  }
+  __syncthreads();
   // Points outside the 16-byte-aligned pairs: a leading point (block 0) and
-  // a trailing point (last block).
+  // a trailing point (last block), offered to warp 0's bests.
   if (!dead && tid == 0) {
     const bool lead = blockIdx.x == 0 && head == 1;
     const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
@@ -525,49 +529,47 @@ __global__ void __launch_bounds__(BLOCK, 3) k_extremes32(const float* __restrict
       values32<ANG>(p.x, p.y, v);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
-        offer32<ANG>(2 * k, v[k], p.x, p.y, i, s_best[2 * k][tid], s_bidx[2 * k][tid], thr, xy);
-        offer32<ANG>(2 * k + 1, v[k], p.x, p.y, i, s_best[2 * k + 1][tid], s_bidx[2 * k + 1][tid], thr, xy);
+        if (better32<ANG>(2 * k, -v[k], i, w_best[0][2 * k], w_bidx[0][2 * k], xy)) {
+          w_best[0][2 * k] = -v[k];
+          w_bidx[0][2 * k] = i;
+        }
+        if (better32<ANG>(2 * k + 1, v[k], i, w_best[0][2 * k + 1], w_bidx[0][2 * k + 1], xy)) {
+          w_best[0][2 * k + 1] = v[k];
+          w_bidx[0][2 * k + 1] = i;
+        }
       }
     }
-  }
-  // Block reduction (warp butterfly, then across warps), exact.
-#pragma unroll 1
-  for (int d = 0; d < ND; ++d) {
-    float s = s_best[d][tid];
-    uint32_t i = s_bidx[d][tid];
-    for (int off = 16; off; off >>= 1) {
-      const float so = __shfl_xor_sync(FULL, s, off);
-      const uint32_t io = __shfl_xor_sync(FULL, i, off);
-      if (better32<ANG>(d, so, io, s, i, xy)) { s = so; i = io; }
-    }
-    if (lane == 0) { s_red[warp][d] = s; s_redi[warp][d] = i; }
   }
   __syncthreads();
-  if (warp == 0) {
-#pragma unroll 1
-    for (int d = 0; d < ND; ++d) {
-      float s = lane < BLOCK / 32 ? s_red[lane][d] : -FLT_MAX;
-      uint32_t i = lane < BLOCK / 32 ? s_redi[lane][d] : NONE;
-      for (int off = 16; off; off >>= 1) {
-        const float so = __shfl_xor_sync(FULL, s, off);
-        const uint32_t io = __shfl_xor_sync(FULL, i, off);
-        if (better32<ANG>(d, so, io, s, i, xy)) { s = so; i = io; }
-      }
-      if (lane == 0) {
-        BlockBest r;
-        r.idx = i;
-        r.pad_ = 0;
-        if (i != NONE) {
-          const float2 p = load_point(xy, i);
-          r.s = score64(ANG, d, p.x, p.y);
-        } else {
-          r.s = -DBL_MAX;
-        }
-        blockres[(size_t)blockIdx.x * ND + d] = r;
-      }
+  // Block result: the binary64 score of every warp's candidate (one lane per
+  // direction), then an exact (score, index) reduction over the warps.
+  __shared__ double w_s64[CONSUMERS / 32][ND];
+  if (warp < CONSUMERS / 32 && lane < ND) {
+    const uint32_t i = w_bidx[warp][lane];
+    double sc = -DBL_MAX;
+    if (i != NONE) {
+      const float2 p = load_point(xy, i);
+      sc = score64(ANG, lane, p.x, p.y);
     }
+    w_s64[warp][lane] = sc;
   }
-  if (last_block_arrives<ANG>(h)) finish_last_block<ANG>(xy, n, h, blockres, ext_out);
+  __syncthreads();
+  if (tid < ND) {
+    double bs = -DBL_MAX;
+    unsigned long long bk = 0;
+    uint32_t bi = NONE;
+    for (int w = 0; w < CONSUMERS / 32; ++w) {
+      const uint32_t i = w_bidx[w][tid];
+      const double sc = w_s64[w][tid];
+      const unsigned long long k = dkey(sc);
+      if (i != NONE && (bi == NONE || k > bk || (k == bk && i < bi))) { bs = sc; bk = k; bi = i; }
+    }
+    BlockBest r;
+    r.s = bs;
+    r.idx = bi;
+    r.pad_ = 0;
+    bres[(size_t)blockIdx.x * ND + tid] = r;
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -576,8 +578,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_extremes32(const float* __restrict
 template <int ANG>
 __global__ void __launch_bounds__(BLOCK) k_extremes64(const float* __restrict__ xy, int64_t n,
                                                        int head, int64_t npairs, int64_t ppb,
-                                                       WsHeader* h, BlockBest* blockres,
-                                                       uint32_t* ext_out) {
+                                                       WsHeader* h, BlockBest* blockres) {
   constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
   __shared__ double s_red[BLOCK / 32][ND];
   __shared__ uint32_t s_redi[BLOCK / 32][ND];
@@ -652,7 +653,119 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(const float* __restrict__ 
       }
     }
   }
-  if (last_block_arrives<ANG>(h)) finish_last_block<ANG>(xy, n, h, blockres, ext_out);
+}
+
+// ----------------------------------------------------------------------------
+// Finishing kernel (one block): the exact reduction of all candidates, the
+// 16 extremes, Step 2 (the polygon, its edge records and inner box) and the
+// cell grid of the inside test.
+
+constexpr int FIN_THREADS = 1024;
+
+template <int ANG>
+__global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(const float* __restrict__ xy, WsHeader* h,
+                                                               const BlockBest* bres, int64_t nent,
+                                                               uint32_t* ext_out, uint16_t* cells) {
+  constexpr int ND = Dirs<ANG>::ND;
+  __shared__ uint32_t s_ext[NSLOT];
+  __shared__ unsigned long long s_k[FIN_THREADS / 32][ND];
+  __shared__ uint32_t s_i[FIN_THREADS / 32][ND];
+  __shared__ long long s_ax[MAXV][GRID], s_by[MAXV][GRID];  // per edge: min of A x per column, B y per row
+  __shared__ long long s_c[MAXV], s_span[MAXV];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool dead = *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
+  // every direction at once: per thread over its strided entries, then a
+  // warp butterfly and a cross-warp pass (all exact)
+  unsigned long long ks[ND];
+  uint32_t bi[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) { ks[d] = 0; bi[d] = NONE; }
+  auto take = [&](int d, unsigned long long k, uint32_t i) {
+    return i != NONE && (bi[d] == NONE || k > ks[d] || (k == ks[d] && i < bi[d]));
+  };
+  for (int64_t e = tid; e < nent; e += FIN_THREADS) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const BlockBest b = bres[e * ND + d];
+      const unsigned long long k = dkey(b.s);
+      if (take(d, k, b.idx)) { ks[d] = k; bi[d] = b.idx; }
+    }
+  }
+  auto butterfly = [&](int d) {
+    for (int off = 16; off; off >>= 1) {
+      const uint32_t io = __shfl_xor_sync(FULL, bi[d], off);
+      const unsigned long long ko = __shfl_xor_sync(FULL, ks[d], off);
+      if (take(d, ko, io)) { ks[d] = ko; bi[d] = io; }
+    }
+  };
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    butterfly(d);
+    if (lane == 0) { s_k[warp][d] = ks[d]; s_i[warp][d] = bi[d]; }
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      ks[d] = s_k[lane][d]; bi[d] = s_i[lane][d];
+      butterfly(d);
+      if (lane == 0) s_ext[d] = bi[d];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (ANG == 0) {
+      // 120 degrees from 30 degrees: with the correctly rounded constants,
+      // x'(120) = -y'(30) and y'(120) = x'(30) exactly.
+      s_ext[12] = s_ext[7];  // argmin x'120 = argmax y'30
+      s_ext[13] = s_ext[6];  // argmax x'120 = argmin y'30
+      s_ext[14] = s_ext[4];  // argmin y'120 = argmin x'30
+      s_ext[15] = s_ext[5];  // argmax y'120 = argmax x'30
+    }
+    if (dead) for (int k = 0; k < NSLOT; ++k) s_ext[k] = NONE;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (ext_out && lane < NSLOT) ext_out[lane] = s_ext[lane];
+    hull16_warp(xy, s_ext, &h->poly);
+  }
+  __syncthreads();
+  // The cell grid.  For edge k the orientation is A x + B y + C (exact
+  // int64); its minimum over a cell is the minimum of A x over the cell's
+  // columns plus that of B y over its rows plus C (corners), likewise the
+  // maximum.  Bit k of a cell's mask: some point of the cell may fail edge
+  // k; a cell entirely outside edge k keeps only bit k.  Byte code: 0 inside,
+  // k + 1 only edge k, CELL_MULTI several edges.
+  const Poly& P = h->poly;
+  const int m = P.m;
+  if (dead || m < 3) return;
+  for (int t = tid; t < m * GRID; t += FIN_THREADS) {
+    const int k = t / GRID, c = t % GRID;
+    const Edge& e = P.e[k];
+    const long long A = -(long long)e.dy, B = e.dx;
+    const long long xa = (long long)P.gx0 + ((long long)c << P.kx), xb = xa + (1ll << P.kx) - 1;
+    const long long ya = (long long)P.gy0 + ((long long)c << P.ky), yb = ya + (1ll << P.ky) - 1;
+    s_ax[k][c] = min(A * xa, A * xb);
+    s_by[k][c] = min(B * ya, B * yb);
+    if (c == 0) {
+      s_c[k] = (long long)e.dy * e.ax - (long long)e.dx * e.ay;
+      // max - min over a cell: |A| (2^kx - 1) + |B| (2^ky - 1)
+      s_span[k] = (A < 0 ? -A : A) * ((1ll << P.kx) - 1) + (B < 0 ? -B : B) * ((1ll << P.ky) - 1);
+    }
+  }
+  __syncthreads();
+  uint8_t* code8 = reinterpret_cast<uint8_t*>(cells + GRID * GRID);
+  for (int c = tid; c < GRID * GRID; c += FIN_THREADS) {
+    const int cx = c & (GRID - 1), cy = c >> GRID_LOG;
+    uint32_t mask = 0;
+    for (int k = 0; k < m; ++k) {
+      const long long mn = s_ax[k][cx] + s_by[k][cy] + s_c[k];
+      if (mn + s_span[k] <= 0) { mask = 1u << k; break; }  // the cell's maximum
+      if (mn <= 0) mask |= 1u << k;
+    }
+    cells[c] = (uint16_t)mask;
+    code8[c] = mask == 0 ? 0 : ((mask & (mask - 1)) == 0 ? (uint8_t)__ffs(mask) : (uint8_t)CELL_MULTI);
+  }
 }
 
 // Domain check (finite, integer-valued, |v| <= 2^24).
@@ -685,36 +798,63 @@ cudaError_t launch_validate(const float* xy, int64_t n, WsHeader* h, cudaStream_
 }
 
 cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, WsHeader* h,
-                            BlockBest* blockres, int grid, int block, uint32_t* ext_out,
+                            void* partials, uint16_t* cells, int grid, int block, uint32_t* ext_out,
                             cudaStream_t st) {
   (void)block;
   const int head = (n > 0 && (reinterpret_cast<uintptr_t>(xy) & 15u)) ? 1 : 0;
   const int64_t npairs = n > head ? (n - head) / 2 : 0;
-  int occ = 1;
-  if (filter == HULL_FILTER_FP32)
-    occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes32<0>) : occupancy(k_extremes32<1>);
-  else
-    occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes64<0>) : occupancy(k_extremes64<1>);
-  int64_t G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
-  G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + STEP - 1) / STEP));
-  int64_t ppb = (npairs + G - 1) / G;
-  ppb = (ppb + STEP - 1) / STEP * STEP;
-  if (ppb == 0) ppb = STEP;
-  G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
+  int64_t G = 1;
   if (filter == HULL_FILTER_FP32) {
+    const size_t dsmem = sizeof(StreamSmemT<3>);
+    static bool attr[64][2] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev][angles]) {
+      cudaError_t e = angles == HULL_ANGLES_CUMULATIVE
+                          ? cudaFuncSetAttribute(k_extremes32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem)
+                          : cudaFuncSetAttribute(k_extremes32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+      if (e != cudaSuccess) return e;
+      attr[dev][angles] = true;
+    }
+    int occ = 0;
     if (angles == HULL_ANGLES_CUMULATIVE)
-      k_extremes32<0><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, blockres, ext_out);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_extremes32<0>, STREAM_THREADS, dsmem);
     else
-      k_extremes32<1><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, blockres, ext_out);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_extremes32<1>, STREAM_THREADS, dsmem);
+    occ = std::max(occ, 1);
+    G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
+    G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
+    int64_t ppb = (npairs + G - 1) / G;
+    ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;
+    if (ppb == 0) ppb = CHUNK;
+    G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
+    BlockBest* bres = static_cast<BlockBest*>(partials);
+    if (angles == HULL_ANGLES_CUMULATIVE) {
+      k_extremes32<0><<<(unsigned)G, STREAM_THREADS, dsmem, st>>>(xy, n, head, npairs, ppb, h, bres);
+      k_ext_finish<0><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+    } else {
+      k_extremes32<1><<<(unsigned)G, STREAM_THREADS, dsmem, st>>>(xy, n, head, npairs, ppb, h, bres);
+      k_ext_finish<1><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+    }
   } else {
-    if (angles == HULL_ANGLES_CUMULATIVE)
-      k_extremes64<0><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, blockres, ext_out);
-    else
-      k_extremes64<1><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, blockres, ext_out);
+    const int occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes64<0>) : occupancy(k_extremes64<1>);
+    G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
+    G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + STEP - 1) / STEP));
+    int64_t ppb = (npairs + G - 1) / G;
+    ppb = (ppb + STEP - 1) / STEP * STEP;
+    if (ppb == 0) ppb = STEP;
+    G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
+    BlockBest* bres = static_cast<BlockBest*>(partials);
+    if (angles == HULL_ANGLES_CUMULATIVE) {
+      k_extremes64<0><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, bres);
+      k_ext_finish<0><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+    } else {
+      k_extremes64<1><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, bres);
+      k_ext_finish<1><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+    }
   }
-  count_launches(1);
+  count_launches(2);
   return cudaGetLastError();
 }
-
 
 }  // namespace cudapre

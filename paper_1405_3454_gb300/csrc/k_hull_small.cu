@@ -1,20 +1,22 @@
 // k_hull_small.cu -- Andrew's monotone chain for a small survivor set (up to
-// SMALL_MAX points) in one thread block: the final step of the method, the
-// hull of the points that remain (section 3, case (2)).
+// SMALL_MAX points): the final step of the method, the hull of the points
+// that remain (section 3, case (2)).  Three launches:
 //
-// 1. Load the survivors into shared memory and bitonic-sort them by
-//    (x, y, index); keep the first of each run of equal coordinates, which
-//    has the lowest index.
-// 2. Split the sorted points into 32 chunks; one lane per chunk runs the
-//    lower and one the upper monotone chain of its chunk.
-// 3. A chunk-chain vertex v is a vertex of the whole lower hull iff every
-//    earlier point a and later point b make a strict left turn a -> v -> b.
-//    Equivalently, the most counter-clockwise incoming direction v - a turns
-//    strictly left into the most clockwise outgoing direction b - v.  Over
-//    one chunk's convex chain these extremes are unimodal, so each is a
-//    binary search; all candidates are tested in parallel.  The upper hull is
-//    the same test with the orientation sign flipped.
-// 4. Write the lower hull left to right, then the upper hull right to left.
+// prep  (one block) Load the survivors into shared memory and bitonic-sort
+//       them by (x, y, index); keep the first of each run of equal
+//       coordinates, which has the lowest index.  Split the sorted points
+//       into 32 chunks; one lane per chunk runs the lower and one the upper
+//       monotone chain of its chunk.
+// prune (whole grid, one warp per chunk-chain vertex) A vertex v is a vertex
+//       of the whole lower hull iff every earlier point a and later point b
+//       make a strict left turn a -> v -> b: the most counter-clockwise
+//       incoming direction v - a turns strictly left into the most clockwise
+//       outgoing direction b - v.  Over one chunk's convex chain these
+//       extremes are unimodal, so lane c finds chunk c's by binary search and
+//       a warp reduction combines the 32 chunks.  The upper hull is the same
+//       test with the orientation sign flipped.
+// emit  (one block) Write the lower hull left to right, then the upper hull
+//       right to left.
 #include "internal.cuh"
 
 namespace cudapre {
@@ -22,7 +24,11 @@ namespace cudapre {
 namespace {
 
 constexpr int SB = 1024;      // threads
-constexpr int NCH = 32;       // chunks (one warp each)
+
+#ifndef STAMP
+#define STAMP(i) ((void)0)
+#endif
+constexpr int NCH = SMALL_NCH;  // chunks (one warp each)
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 __device__ __forceinline__ long long cr(long long ax, long long ay, long long bx, long long by) {
@@ -78,105 +84,43 @@ __device__ int chunk_chain(Pts P, int lo, int hi, uint16_t* st) {
   return n;
 }
 
-// Over chain ch[0..k) of points all before v: the most counter-clockwise
-// incoming direction v - a (sign S), as an index into ch.
-template <int S>
-__device__ int best_in(Pts P, const uint16_t* ch, int k, long long vx, long long vy) {
-  int lo = 0, hi = k - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const int a = ch[mid], b = ch[mid + 1];
-    // is v - b counter-clockwise of v - a ?
-    const long long c = S * cr(vx - P.x[a], vy - P.y[a], vx - P.x[b], vy - P.y[b]);
-    if (c > 0) lo = mid + 1; else hi = mid;
-  }
-  return ch[lo];
-}
-
-// Over chain ch[0..k) of points all after v: the most clockwise outgoing
-// direction b - v (sign S).
-template <int S>
-__device__ int best_out(Pts P, const uint16_t* ch, int k, long long vx, long long vy) {
-  int lo = 0, hi = k - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const int a = ch[mid], b = ch[mid + 1];
-    // is b - v clockwise of a - v ?
-    const long long c = S * cr(P.x[a] - vx, P.y[a] - vy, P.x[b] - vx, P.y[b] - vy);
-    if (c < 0) lo = mid + 1; else hi = mid;
-  }
-  return ch[lo];
-}
-
-// Marks keep[j] for every candidate j (chunk-chain vertices, chunk-major).
-template <int S>
-__device__ void prune(Pts P, int u, int C, const uint16_t* ch, const int* cnt, const int* cbase, int total,
-                      uint8_t* keep) {
-  for (int j = threadIdx.x; j < total; j += SB) {
-    int w = 0;
-    while (w + 1 < NCH && cbase[w + 1] <= j) ++w;
-    const int k = j - cbase[w];
-    const uint16_t* own = ch + w * C;
-    const int v = own[k];
-    if (v == 0 || v == u - 1) { keep[j] = 1; continue; }
-    const long long vx = P.x[v], vy = P.y[v];
-    // most counter-clockwise incoming direction
-    long long ix = 0, iy = 0;
-    bool have_in = false;
-    auto offer_in = [&](int a) {
-      const long long dx = vx - P.x[a], dy = vy - P.y[a];
-      if (!have_in || S * cr(ix, iy, dx, dy) > 0) { ix = dx; iy = dy; have_in = true; }
-    };
-    if (k > 0) offer_in(own[k - 1]);
-    for (int c = 0; c < w; ++c)
-      if (cnt[c] > 0) offer_in(best_in<S>(P, ch + c * C, cnt[c], vx, vy));
-    long long ox = 0, oy = 0;
-    bool have_out = false;
-    auto offer_out = [&](int b) {
-      const long long dx = P.x[b] - vx, dy = P.y[b] - vy;
-      if (!have_out || S * cr(ox, oy, dx, dy) < 0) { ox = dx; oy = dy; have_out = true; }
-    };
-    if (k + 1 < cnt[w]) offer_out(own[k + 1]);
-    for (int c = w + 1; c < NCH; ++c)
-      if (cnt[c] > 0) offer_out(best_out<S>(P, ch + c * C, cnt[c], vx, vy));
-    keep[j] = (have_in && have_out && S * cr(ix, iy, ox, oy) > 0) ? 1 : 0;
-  }
-}
-
 __device__ __forceinline__ int64_t count_of(const WsHeader* h, const unsigned long long* c) {
   if (*reinterpret_cast<const volatile uint32_t*>(&h->status)) return 0;
   return (int64_t)*reinterpret_cast<const volatile unsigned long long*>(c);
 }
 
-__global__ void __launch_bounds__(SB, 1) k_small_hull(const unsigned long long* __restrict__ kin,
+// prep: sort, dedupe, chunk chains -> SmallWs (global).
+__global__ void __launch_bounds__(SB, 1) k_small_prep(const unsigned long long* __restrict__ kin,
                                                        const uint32_t* __restrict__ vin,
                                                        const unsigned long long* count, const WsHeader* h,
-                                                       uint32_t* __restrict__ out, int64_t* out_n) {
+                                                       SmallWs* sw, uint32_t* __restrict__ out, int64_t* out_n) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int s_w[32];
   __shared__ int s_tot;
-  __shared__ int s_cnt[2][NCH], s_base[2][NCH + 1];
-  __shared__ int s_lower;
+  __shared__ int s_cnt[2][NCH];
   const int tid = threadIdx.x;
   const int64_t m64 = count_of(h, count);
-  if (m64 > SMALL_MAX) return;  // the large path handles it
-  if (m64 == 0) {
-    if (tid == 0) *out_n = 0;
+  if (m64 > SMALL_MAX || m64 == 0) {  // the large path, or nothing to do
+    if (tid == 0) {
+      sw->active = 0;
+      if (m64 == 0) *out_n = 0;
+    }
     return;
   }
   const int m = (int)m64;
+  STAMP(0);
   int P2 = 2;
   while (P2 < m) P2 <<= 1;
   unsigned long long* sk = reinterpret_cast<unsigned long long*>(sm);
   uint32_t* si = reinterpret_cast<uint32_t*>(sk + SMALL_MAX);
   uint16_t* chain = reinterpret_cast<uint16_t*>(si + SMALL_MAX);  // [2][SMALL_MAX]
-  uint8_t* keep = reinterpret_cast<uint8_t*>(chain + 2 * SMALL_MAX);  // [2][SMALL_MAX]
   for (int i = tid; i < P2; i += SB) {
     sk[i] = i < m ? kin[i] : ~0ull;
     si[i] = i < m ? vin[i] : ~0u;
   }
   __syncthreads();
-  // 1. bitonic sort by (key, index)
+  STAMP(1);
+  // bitonic sort by (key, index)
   for (int k = 2; k <= P2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < P2; i += SB) {
@@ -191,6 +135,7 @@ __global__ void __launch_bounds__(SB, 1) k_small_hull(const unsigned long long* 
       __syncthreads();
     }
   }
+  STAMP(2);
   // dedupe: first of each run of equal keys (lowest index) -> unique arrays
   constexpr int E = SMALL_MAX / SB;  // elements per thread (blocked)
   unsigned long long rk[E];
@@ -208,7 +153,7 @@ __global__ void __launch_bounds__(SB, 1) k_small_hull(const unsigned long long* 
   __syncthreads();
   int pos = block_scan(c, s_w, &s_tot);
   const int u = s_tot;
-  int* ux = reinterpret_cast<int*>(sm);             // aliases sk (all reads done)
+  int* ux = reinterpret_cast<int*>(sm);  // aliases sk (all reads done)
   int* uy = ux + SMALL_MAX;
   uint32_t* uid = reinterpret_cast<uint32_t*>(uy + SMALL_MAX);  // aliases si
 #pragma unroll
@@ -222,11 +167,12 @@ __global__ void __launch_bounds__(SB, 1) k_small_hull(const unsigned long long* 
   }
   __syncthreads();
   if (u == 1) {
-    if (tid == 0) { out[0] = uid[0]; *out_n = 1; }
+    if (tid == 0) { out[0] = uid[0]; *out_n = 1; sw->active = 0; }
     return;
   }
   const Pts P{ux, uy};
-  // 2. chunk chains: warp w, lane 0 lower / lane 1 upper
+  STAMP(3);
+  // chunk chains: warp w, lane 0 lower / lane 1 upper
   const int C = (u + NCH - 1) / NCH;
   {
     const int w = tid >> 5, lane = tid & 31;
@@ -235,37 +181,146 @@ __global__ void __launch_bounds__(SB, 1) k_small_hull(const unsigned long long* 
     if (lane == 1) s_cnt[1][w] = chunk_chain<-1>(P, lo, hi, chain + SMALL_MAX + w * C);
   }
   __syncthreads();
+  STAMP(4);
+  // publish to global
+  for (int i = tid; i < u; i += SB) {
+    sw->pts[i] = make_int2(ux[i], uy[i]);
+    sw->uid[i] = uid[i];
+  }
+  for (int w = 0; w < NCH; ++w) {
+    for (int k = tid; k < s_cnt[0][w]; k += SB) sw->chain[0][w * C + k] = chain[w * C + k];
+    for (int k = tid; k < s_cnt[1][w]; k += SB) sw->chain[1][w * C + k] = chain[SMALL_MAX + w * C + k];
+  }
   if (tid < 2) {
     int run = 0;
-    for (int w = 0; w < NCH; ++w) { s_base[tid][w] = run; run += s_cnt[tid][w]; }
-    s_base[tid][NCH] = run;
+    for (int w = 0; w < NCH; ++w) {
+      sw->cnt[tid][w] = s_cnt[tid][w];
+      sw->base[tid][w] = run;
+      run += s_cnt[tid][w];
+    }
+    sw->base[tid][NCH] = run;
   }
-  __syncthreads();
-  // 3. global hull vertices among the chunk-chain vertices
-  prune<1>(P, u, C, chain, s_cnt[0], s_base[0], s_base[0][NCH], keep);
-  prune<-1>(P, u, C, chain + SMALL_MAX, s_cnt[1], s_base[1], s_base[1][NCH], keep + SMALL_MAX);
-  __syncthreads();
-  // 4. compact: the lower hull left to right without its last point, then
-  //    the upper hull right to left without its first and last points
+  if (tid == 0) { sw->u = u; sw->C = C; sw->active = 1; }
+  STAMP(5);
+}
+
+// Unique points read through the read-only path.
+struct GPts {
+  const int2* p;
+  __device__ __forceinline__ int2 at(int i) const { return __ldg(p + i); }
+};
+
+// Over chain ch[0..k) of points all before v: the most counter-clockwise
+// incoming direction v - a (sign S); returns the point.
+template <int S>
+__device__ int g_best_in(GPts P, const uint16_t* ch, int k, long long vx, long long vy) {
+  int lo = 0, hi = k - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int2 a = P.at(__ldg(ch + mid)), b = P.at(__ldg(ch + mid + 1));
+    const long long c = S * cr(vx - a.x, vy - a.y, vx - b.x, vy - b.y);
+    if (c > 0) lo = mid + 1; else hi = mid;
+  }
+  return __ldg(ch + lo);
+}
+
+// Over chain ch[0..k) of points all after v: the most clockwise outgoing
+// direction b - v (sign S); returns the point.
+template <int S>
+__device__ int g_best_out(GPts P, const uint16_t* ch, int k, long long vx, long long vy) {
+  int lo = 0, hi = k - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int2 a = P.at(__ldg(ch + mid)), b = P.at(__ldg(ch + mid + 1));
+    const long long c = S * cr(a.x - vx, a.y - vy, b.x - vx, b.y - vy);
+    if (c < 0) lo = mid + 1; else hi = mid;
+  }
+  return __ldg(ch + lo);
+}
+
+template <int S>
+__device__ __forceinline__ void prune_one(const SmallWs* sw, int s, int j) {
+  const int lane = threadIdx.x & 31;
+  const int u = sw->u, C = sw->C;
+  const int* cnt = sw->cnt[s];
+  const int* base = sw->base[s];
+  int w = 0;
+  while (w + 1 < NCH && base[w + 1] <= j) ++w;
+  const int k = j - base[w];
+  const uint16_t* ch = sw->chain[s];
+  const GPts P{sw->pts};
+  const int v = ch[w * C + k];
+  if (v == 0 || v == u - 1) {
+    if (lane == 0) const_cast<SmallWs*>(sw)->keep[s][j] = 1;
+    return;
+  }
+  const int2 pv = P.at(v);
+  const long long vx = pv.x, vy = pv.y;
+  // lane c: chunk c's most counter-clockwise incoming / most clockwise outgoing direction
+  long long ix = 0, iy = 0, ox = 0, oy = 0;
+  bool hin = false, hout = false;
+  const int c = lane;
+  if (c < w && cnt[c] > 0) {
+    const int2 a = P.at(g_best_in<S>(P, ch + c * C, cnt[c], vx, vy));
+    ix = vx - a.x; iy = vy - a.y; hin = true;
+  } else if (c == w) {
+    if (k > 0) { const int2 a = P.at(ch[w * C + k - 1]); ix = vx - a.x; iy = vy - a.y; hin = true; }
+    if (k + 1 < cnt[w]) { const int2 b = P.at(ch[w * C + k + 1]); ox = b.x - vx; oy = b.y - vy; hout = true; }
+  } else if (c > w && cnt[c] > 0) {
+    const int2 b = P.at(g_best_out<S>(P, ch + c * C, cnt[c], vx, vy));
+    ox = b.x - vx; oy = b.y - vy; hout = true;
+  }
+  for (int off = 16; off; off >>= 1) {
+    const long long jx = __shfl_xor_sync(FULL, ix, off), jy = __shfl_xor_sync(FULL, iy, off);
+    const bool jh = __shfl_xor_sync(FULL, hin, off);
+    if (jh && (!hin || S * cr(ix, iy, jx, jy) > 0)) { ix = jx; iy = jy; hin = true; }
+    const long long px = __shfl_xor_sync(FULL, ox, off), py = __shfl_xor_sync(FULL, oy, off);
+    const bool ph = __shfl_xor_sync(FULL, hout, off);
+    if (ph && (!hout || S * cr(ox, oy, px, py) < 0)) { ox = px; oy = py; hout = true; }
+  }
+  if (lane == 0) const_cast<SmallWs*>(sw)->keep[s][j] = (hin && hout && S * cr(ix, iy, ox, oy) > 0) ? 1 : 0;
+}
+
+// prune: one warp per chunk-chain vertex (lower ones first, then upper).
+__global__ void __launch_bounds__(256) k_small_prune(const SmallWs* sw) {
+  if (!*reinterpret_cast<const volatile int*>(&sw->active)) return;
+  const int nl = sw->base[0][NCH], total = nl + sw->base[1][NCH];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
+    if (g < nl) prune_one<1>(sw, 0, g);
+    else prune_one<-1>(sw, 1, g - nl);
+  }
+}
+
+// emit: the lower hull left to right without its last point, then the upper
+// hull right to left without its first and last points.
+__global__ void __launch_bounds__(SB, 1) k_small_emit(const SmallWs* sw, uint32_t* __restrict__ out,
+                                                       int64_t* out_n) {
+  __shared__ int s_w[32];
+  __shared__ int s_tot;
+  __shared__ int s_lower;
+  const int tid = threadIdx.x;
+  if (!*reinterpret_cast<const volatile int*>(&sw->active)) return;
+  const int C = sw->C;
   for (int s = 0; s < 2; ++s) {
-    const int total = s_base[s][NCH];
+    const int total = sw->base[s][NCH];
     const int per = (total + SB - 1) / SB;
     const int j0 = min(tid * per, total), j1 = min(j0 + per, total);
     int cnt = 0;
-    for (int j = j0; j < j1; ++j) cnt += keep[s * SMALL_MAX + j];
+    for (int j = j0; j < j1; ++j) cnt += sw->keep[s][j];
     int o = block_scan(cnt, s_w, &s_tot);
     const int a = s_tot;  // vertices of this chain, both end points included
     const int la = s == 0 ? a : s_lower;
+    int w = 0;
     for (int j = j0; j < j1; ++j) {
-      if (!keep[s * SMALL_MAX + j]) continue;
-      int w = 0;
-      while (w + 1 < NCH && s_base[s][w + 1] <= j) ++w;
-      const int v = chain[s * SMALL_MAX + w * C + (j - s_base[s][w])];
+      if (!sw->keep[s][j]) continue;
+      while (w + 1 < NCH && sw->base[s][w + 1] <= j) ++w;
+      const int v = sw->chain[s][w * C + (j - sw->base[s][w])];
       if (s == 0) {
-        if (o < a - 1) out[o] = uid[v];
+        if (o < a - 1) out[o] = sw->uid[v];
       } else if (o >= 1) {
         // upper vertex o (1 .. a-1) -> after the la-1 lower vertices, reversed
-        out[(la - 1) + (a - 1 - o)] = uid[v];
+        out[(la - 1) + (a - 1 - o)] = sw->uid[v];
       }
       ++o;
     }
@@ -280,23 +335,25 @@ __global__ void __launch_bounds__(SB, 1) k_small_hull(const unsigned long long* 
 }  // namespace
 
 size_t small_hull_smem() {
-  return SMALL_MAX * (sizeof(unsigned long long) + sizeof(uint32_t) + 2 * sizeof(uint16_t) + 2);
+  return SMALL_MAX * (sizeof(unsigned long long) + sizeof(uint32_t) + 2 * sizeof(uint16_t));
 }
 
 cudaError_t launch_small_hull(const unsigned long long* keys, const uint32_t* vals,
-                              const unsigned long long* count, const WsHeader* h, uint32_t* out,
+                              const unsigned long long* count, const WsHeader* h, SmallWs* sw, uint32_t* out,
                               int64_t* out_n, cudaStream_t st) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   const size_t smem = small_hull_smem();
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_small_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_small_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  k_small_hull<<<1, SB, smem, st>>>(keys, vals, count, h, out, out_n);
-  count_launches(1);
+  k_small_prep<<<1, SB, smem, st>>>(keys, vals, count, h, sw, out, out_n);
+  k_small_prune<<<(unsigned)(2 * SMALL_MAX / 8), 256, 0, st>>>(sw);
+  k_small_emit<<<1, SB, 0, st>>>(sw, out, out_n);
+  count_launches(3);
   return cudaGetLastError();
 }
 

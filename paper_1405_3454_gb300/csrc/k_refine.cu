@@ -45,12 +45,22 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_bins(const unsigned long long
   const int64_t m = count_of(h, &h->n_surv);
   const float ox = (float)h->poly.rox, oy = (float)h->poly.roy;
   if (h->poly.refine_on) {
-    for (int64_t j = (int64_t)blockIdx.x * RBLOCK + threadIdx.x; j < m; j += (int64_t)gridDim.x * RBLOCK) {
-      const unsigned long long k = keys[j];
-      const float qx = (float)key_x(k) - ox, qy = (float)key_y(k) - oy;
-      const float r2 = fmaf(qx, qx, qy * qy);
-      const unsigned long long packed = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)j;
-      atomicMax(&s_bin[bin_of(qx, qy)], packed);
+    // 4 independent loads in flight per thread
+    const int64_t stride = (int64_t)gridDim.x * RBLOCK;
+    for (int64_t j0 = (int64_t)blockIdx.x * RBLOCK + threadIdx.x; j0 < m; j0 += 4 * stride) {
+      unsigned long long kv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) kv[u] = j0 + u * stride < m ? keys[j0 + u * stride] : 0ull;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t j = j0 + u * stride;
+        if (j < m) {
+          const float qx = (float)key_x(kv[u]) - ox, qy = (float)key_y(kv[u]) - oy;
+          const float r2 = fmaf(qx, qx, qy * qy);
+          const unsigned long long packed = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)j;
+          atomicMax(&s_bin[bin_of(qx, qy)], packed);
+        }
+      }
     }
   }
   __syncthreads();
@@ -97,61 +107,66 @@ __device__ __forceinline__ long long orient_ll(long long ax, long long ay, long 
 }
 
 // Pass 2: keep the survivors not strictly inside their bin's triangles;
-// compacted to (kout, vout), count in h->n_surv2.
+// compacted to (kout, vout), count in h->n_surv2.  Few survive, so each warp
+// appends its survivors with one atomic (no block barrier).
 __global__ void __launch_bounds__(RBLOCK) k_refine_filter(const unsigned long long* __restrict__ kin,
                                                            const uint32_t* __restrict__ vin,
                                                            unsigned long long* __restrict__ kout,
                                                            uint32_t* __restrict__ vout, WsHeader* h,
                                                            const int4* __restrict__ tri) {
   __shared__ int4 s_tri[2 * REFINE_BINS];
-  __shared__ uint32_t s_wsum[RBLOCK / 32];
-  __shared__ unsigned long long s_base;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   for (int k = tid; k < 2 * REFINE_BINS; k += RBLOCK) s_tri[k] = tri[k];
   __syncthreads();
   const int64_t m = count_of(h, &h->n_surv);
   const long long ox = h->poly.rox, oy = h->poly.roy;
   const float oxf = (float)ox, oyf = (float)oy;
   const int64_t stride = (int64_t)gridDim.x * RBLOCK;
-  for (int64_t j0 = (int64_t)blockIdx.x * RBLOCK; j0 < m; j0 += stride) {
-    const int64_t j = j0 + tid;
-    bool keep = false;
-    unsigned long long key = 0;
-    if (j < m) {
-      key = kin[j];
-      const long long px = key_x(key), py = key_y(key);
-      keep = true;
-      const int b = bin_of((float)px - oxf, (float)py - oyf);
-      const int4 a = s_tri[2 * b], c = s_tri[2 * b + 1];
-      if (c.z & 1) {
-        if (c.z & 2) {
-          const long long ow = orient_ll(ox, oy, a.z, a.w, px, py);
-          if (ow < 0) {  // the L side of ray O->W: triangle (O, L, W)
-            keep = !(orient_ll(ox, oy, a.x, a.y, px, py) > 0 && orient_ll(a.x, a.y, a.z, a.w, px, py) > 0);
-          } else if (ow > 0) {  // triangle (O, W, R)
-            keep = !(orient_ll(a.z, a.w, c.x, c.y, px, py) > 0 && orient_ll(c.x, c.y, ox, oy, px, py) > 0);
+  // 4 independent loads in flight per thread; a warp handles 4 x 32
+  // consecutive survivors per round
+  for (int64_t j0 = (int64_t)blockIdx.x * RBLOCK * 4; j0 < m; j0 += 4 * stride) {
+    unsigned long long kv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = j0 + u * RBLOCK + tid;
+      kv[u] = j < m ? kin[j] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = j0 + u * RBLOCK + tid;
+      bool keep = false;
+      if (j < m) {
+        const unsigned long long key = kv[u];
+        const long long px = key_x(key), py = key_y(key);
+        keep = true;
+        const int b = bin_of((float)px - oxf, (float)py - oyf);
+        const int4 a = s_tri[2 * b], c = s_tri[2 * b + 1];
+        if (c.z & 1) {
+          if (c.z & 2) {
+            const long long ow = orient_ll(ox, oy, a.z, a.w, px, py);
+            if (ow < 0) {  // the L side of ray O->W: triangle (O, L, W)
+              keep = !(orient_ll(ox, oy, a.x, a.y, px, py) > 0 && orient_ll(a.x, a.y, a.z, a.w, px, py) > 0);
+            } else if (ow > 0) {  // triangle (O, W, R)
+              keep = !(orient_ll(a.z, a.w, c.x, c.y, px, py) > 0 && orient_ll(c.x, c.y, ox, oy, px, py) > 0);
+            }
+          } else {  // empty bin: triangle (O, L, R)
+            keep = !(orient_ll(ox, oy, a.x, a.y, px, py) > 0 && orient_ll(a.x, a.y, c.x, c.y, px, py) > 0 &&
+                     orient_ll(c.x, c.y, ox, oy, px, py) > 0);
           }
-        } else {  // empty bin: triangle (O, L, R)
-          keep = !(orient_ll(ox, oy, a.x, a.y, px, py) > 0 && orient_ll(a.x, a.y, c.x, c.y, px, py) > 0 &&
-                   orient_ll(c.x, c.y, ox, oy, px, py) > 0);
+        }
+      }
+      const unsigned bal = __ballot_sync(FULL, keep);
+      if (bal) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&h->n_surv2, (unsigned long long)__popc(bal));
+        base = __shfl_sync(FULL, base, 0);
+        if (keep) {
+          const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+          kout[pos] = kv[u];
+          vout[pos] = vin[j];
         }
       }
     }
-    const unsigned bal = __ballot_sync(FULL, keep);
-    if (lane == 0) s_wsum[warp] = __popc(bal);
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t run = 0;
-      for (int w = 0; w < RBLOCK / 32; ++w) { const uint32_t t = s_wsum[w]; s_wsum[w] = run; run += t; }
-      s_base = run ? atomicAdd(&h->n_surv2, (unsigned long long)run) : 0ull;
-    }
-    __syncthreads();
-    if (keep) {
-      const unsigned long long pos = s_base + s_wsum[warp] + __popc(bal & ((1u << lane) - 1u));
-      kout[pos] = key;
-      vout[pos] = vin[j];
-    }
-    __syncthreads();
   }
 }
 
