@@ -56,40 +56,6 @@ __device__ __noinline__ unsigned fails_any(const Edge* E, uint32_t code, float x
 }
 
 template <>
-struct Tester<HULL_FILTER_FP32> {
-  const Edge* E;
-  const uint8_t* code8;      // shared memory
-  const uint16_t* mask16;    // global memory (several-edge cells only)
-  float gx, gy, ix_scale, iy_scale;
-  unsigned esc;
-
-  // Branch-free for the common cases: the cell lookup and the float32 test
-  // of the cell's edge run for every point; only several-edge cells and
-  // undecided float32 tests take a branch.
-  __device__ __forceinline__ bool survives(float x, float y) {
-    // exact cell coordinates: floor((x - gx) / 2^kx) from round-down
-    // arithmetic (both steps are exact or round toward the floor)
-    const float u = __fsub_rd(x, gx), v = __fsub_rd(y, gy);
-    const int cx = __float_as_int(__fmaf_rd(u, ix_scale, 8388608.0f)) - MAGIC;
-    const int cy = __float_as_int(__fmaf_rd(v, iy_scale, 8388608.0f)) - MAGIC;
-    const bool in_grid = (unsigned)(cx | cy) < (unsigned)GRID;
-    const int cell = in_grid ? ((cy << GRID_LOG) | cx) : 0;
-    const uint32_t code = code8[cell];
-    const int k = code != 0 && code != CELL_MULTI ? (int)code - 1 : 0;
-    const float4 c = *reinterpret_cast<const float4*>(&E[k].A);
-    const float s = fmaf(c.x, x, fmaf(c.y, y, c.z));
-    const bool decided = s > c.w || s < -c.w;
-    if (in_grid && code != 0 && (code == CELL_MULTI || !decided)) {
-      const uint32_t mask = code == CELL_MULTI ? (uint32_t)__ldg(mask16 + cell) : 1u << k;
-      const unsigned r = fails_any(E, mask, x, y);
-      esc += r >> 1;
-      return r & 1;
-    }
-    return !in_grid || (code != 0 && s < -c.w);
-  }
-};
-
-template <>
 struct Tester<HULL_FILTER_EXACT> {
   const Edge* E;
   int m;
@@ -102,18 +68,19 @@ struct Tester<HULL_FILTER_EXACT> {
   }
 };
 
-// Survivor output through a per-warp staging buffer in shared memory: per
-// tile each lane counts its survivors, a warp scan places them, and a buffer
-// that could overflow is first flushed by its warp with one global atomic and
-// coalesced stores.  No block-wide barrier in the loop.
-constexpr int WBUF = 128;  // >= 4 points x 32 lanes (a half tile)
+// ----------------------------------------------------------------------------
+// Survivor output: a per-warp staging buffer of point indices in shared
+// memory; a full buffer is flushed by its warp with one global atomic and
+// coalesced stores (the keys are formed then, from the coordinates re-read
+// from L2).  No block-wide barrier in the streaming loop.
+constexpr int WBUF = 256;
 
 template <bool KEYS>
 struct WarpOut {
-  uint32_t* s_idx;             // [WBUF] of this warp
-  float2* s_xy;                // [WBUF] of this warp (coordinates, for the keys)
-  int count;                   // warp-uniform fill level
+  uint32_t* s_idx;  // [WBUF] of this warp
+  int count;        // warp-uniform fill level
   WsHeader* h;
+  const float* xy;
   uint32_t* g_idx;
   unsigned long long* g_key;
 
@@ -124,9 +91,10 @@ struct WarpOut {
     if (lane == 0 && count) base = atomicAdd(&h->n_surv, (unsigned long long)count);
     base = __shfl_sync(FULL, base, 0);
     for (int k = lane; k < count; k += 32) {
-      g_idx[base + k] = s_idx[k];
+      const uint32_t i = s_idx[k];
+      g_idx[base + k] = i;
       if (KEYS) {
-        const float2 p = s_xy[k];
+        const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
         g_key[base + k] = point_key(__float2int_rn(p.x), __float2int_rn(p.y));
       }
     }
@@ -134,7 +102,8 @@ struct WarpOut {
     count = 0;
   }
 
-  // Reserve room for this lane's c survivors; returns its first slot.
+  // Reserve room for this lane's c (<= 32 * 8 total) survivors; returns its
+  // first slot.
   __device__ __forceinline__ int reserve(int c) {
     const int lane = threadIdx.x & 31;
     int incl = c;
@@ -150,57 +119,92 @@ struct WarpOut {
     return base;
   }
 
-  __device__ __forceinline__ void put(int pos, uint32_t idx, float x, float y) {
-    s_idx[pos] = idx;
-    if (KEYS) s_xy[pos] = make_float2(x, y);
+  // One survivor per lane at most (ballot placement).
+  __device__ __forceinline__ void push(bool keep, uint32_t idx) {
+    const unsigned bal = __ballot_sync(FULL, keep);
+    if (!bal) return;
+    if (count + 32 > WBUF) flush();
+    if (keep) s_idx[count + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = idx;
+    count += __popc(bal);
   }
 };
 
-using FilterStream = StreamSmemT<2>;
+// ----------------------------------------------------------------------------
+// The FP32-filtered inside test.
 
-template <int FILTER, bool KEYS>
-__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter(const float* __restrict__ xy, int64_t n, int head,
-                                                               int64_t npairs, int64_t ppb, WsHeader* h,
-                                                               const uint16_t* __restrict__ gcells,
-                                                               uint32_t* __restrict__ surv_idx,
-                                                               unsigned long long* __restrict__ surv_key) {
+using FilterStream = StreamSmemT<2>;
+constexpr int QCAP = 320;  // per-warp ring of boundary points (>= 31 + 8 * 32)
+
+struct Cells {
+  const uint8_t* code8;    // shared memory
+  const uint16_t* mask16;  // global memory (several-edge cells)
+  float gx, gy, sx, sy;
+
+  // Byte code of the point's cell; 255 + 1 (256) when outside the grid.
+  __device__ __forceinline__ uint32_t code(float x, float y, int& cell) const {
+    // exact cell coordinates: floor((x - gx) / 2^kx) from round-down
+    // arithmetic (both steps are exact or round toward the floor)
+    const float u = __fsub_rd(x, gx), v = __fsub_rd(y, gy);
+    const int cx = __float_as_int(__fmaf_rd(u, sx, 8388608.0f)) - MAGIC;
+    const int cy = __float_as_int(__fmaf_rd(v, sy, 8388608.0f)) - MAGIC;
+    const bool in_grid = (unsigned)(cx | cy) < (unsigned)GRID;
+    cell = in_grid ? ((cy << GRID_LOG) | cx) : 0;
+    return in_grid ? (uint32_t)code8[cell] : 256u;
+  }
+};
+
+// Full test of a boundary point (cell code 1..255): float32 edge test with
+// exact escalation.  Returns 2 * escalations + (survives ? 1 : 0).
+__device__ __forceinline__ unsigned boundary_test(const Edge* E, const Cells& C, float x, float y) {
+  int cell;
+  const uint32_t code = C.code(x, y, cell);
+  if (code == 0) return 0;
+  if (code == 256) return 1;
+  if (code == CELL_MULTI) return fails_any(E, __ldg(C.mask16 + cell), x, y);
+  const int k = (int)code - 1;
+  const float4 c = *reinterpret_cast<const float4*>(&E[k].A);
+  const float s = fmaf(c.x, x, fmaf(c.y, y, c.z));
+  if (s > c.w) return 0;
+  if (s < -c.w) return 1;
+  return 2 + (exact_left(E[k], __float2int_rn(x), __float2int_rn(y)) ? 0u : 1u);
+}
+
+template <bool KEYS>
+__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __restrict__ xy, int64_t n, int head,
+                                                                 int64_t npairs, int64_t ppb, WsHeader* h,
+                                                                 const uint16_t* __restrict__ gcells,
+                                                                 uint32_t* __restrict__ surv_idx,
+                                                                 unsigned long long* __restrict__ surv_key) {
   extern __shared__ __align__(128) unsigned char dsm[];
   FilterStream& S = *reinterpret_cast<FilterStream*>(dsm);
-  uint8_t* s_code = reinterpret_cast<uint8_t*>(dsm + sizeof(FilterStream));  // GRID*GRID (FP32)
+  uint8_t* s_code = reinterpret_cast<uint8_t*>(dsm + sizeof(FilterStream));  // GRID*GRID
   __shared__ __align__(16) Edge s_e[MAXV];
   __shared__ uint32_t s_oidx[CONSUMERS / 32][WBUF];
-  __shared__ float2 s_oxy[KEYS ? CONSUMERS / 32 : 1][WBUF];
+  __shared__ uint32_t s_q[CONSUMERS / 32][QCAP];
   __shared__ int s_pm[5];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   if (*reinterpret_cast<volatile uint32_t*>(&h->status) != 0) return;
-  // Stage the polygon (and the cell grid) in shared memory (section 2, Step 3).
+  // Stage the polygon and the cell grid in shared memory (section 2, Step 3).
   if (tid < MAXV * (int)(sizeof(Edge) / 4))
     reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
   if (tid == 0) {
     s_pm[0] = h->poly.m; s_pm[1] = h->poly.gx0; s_pm[2] = h->poly.gy0; s_pm[3] = h->poly.kx; s_pm[4] = h->poly.ky;
   }
-  const int m_pre = h->poly.m;
-  if (FILTER == HULL_FILTER_FP32 && m_pre >= 3) {
+  if (h->poly.m >= 3) {
     const uint4* src = reinterpret_cast<const uint4*>(gcells + GRID * GRID);  // the byte codes
     uint4* dst = reinterpret_cast<uint4*>(s_code);
     for (int k = tid; k < GRID * GRID / 16; k += STREAM_THREADS) dst[k] = src[k];
   }
   stream_init(S);  // includes a block barrier
-  const int m = s_pm[0];
-  Tester<FILTER> T;
-  T.E = s_e;
-  T.esc = 0;
-  if constexpr (FILTER == HULL_FILTER_FP32) {
-    T.code8 = s_code;
-    T.mask16 = gcells;
-    T.gx = (float)s_pm[1];
-    T.gy = (float)s_pm[2];
-    T.ix_scale = __int_as_float((127 - s_pm[3]) << 23);  // 2^-kx
-    T.iy_scale = __int_as_float((127 - s_pm[4]) << 23);
-  } else {
-    T.m = m;
-  }
-  const bool all_survive = m < 3;
+  const bool all_survive = s_pm[0] < 3;
+  Cells C;
+  C.code8 = s_code;
+  C.mask16 = gcells;
+  C.gx = (float)s_pm[1];
+  C.gy = (float)s_pm[2];
+  C.sx = __int_as_float((127 - s_pm[3]) << 23);  // 2^-kx
+  C.sy = __int_as_float((127 - s_pm[4]) << 23);
   const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
   StreamRange R;
   R.p0 = (int64_t)blockIdx.x * ppb;
@@ -209,18 +213,34 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter(const float* __res
   // Chunks run last-to-first: the extreme search streamed each block's range
   // first-to-last, so the tail of every range is still in L2.
   R.reverse = true;
-
   if (warp == PRODUCER_WARP) {
     stream_produce(S, R, P, h);
     return;
   }
   WarpOut<KEYS> O;
   O.s_idx = s_oidx[warp];
-  O.s_xy = s_oxy[KEYS ? warp : 0];
   O.count = 0;
   O.h = h;
+  O.xy = xy;
   O.g_idx = surv_idx;
   O.g_key = surv_key;
+  uint32_t* q = s_q[warp];
+  int qhead = 0, qtail = 0;  // warp-uniform ring positions
+  unsigned esc = 0;
+  // Test 32 queued boundary points, one per lane.
+  auto drain = [&](int count) {
+    const bool mine = lane < count;
+    const uint32_t i = mine ? q[(qhead + lane) % QCAP] : 0u;
+    bool keep = false;
+    if (mine) {
+      const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
+      const unsigned r = boundary_test(s_e, C, p.x, p.y);
+      esc += r >> 1;
+      keep = r & 1;
+    }
+    qhead += count;
+    O.push(keep, i);
+  };
   for (int64_t c = 0; c < R.nchunks; ++c) {
     const int s = (int)(c % FilterStream::STAGES);
     if (!mbar_wait(&S.full[s], (unsigned)((c / FilterStream::STAGES) & 1), h)) break;
@@ -232,37 +252,33 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter(const float* __res
     for (int j = 0; j < 4; ++j) v[j] = st[tid + j * CONSUMERS];  // beyond cnt: ignored below
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.empty[s]);
+    const uint32_t i0 = (uint32_t)(head + 2 * (f + tid));
     uint32_t keep = 0;
-    if (cnt == CHUNK) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (all_survive || T.survives(v[j].x, v[j].y)) keep |= 1u << (2 * j);
-        if (all_survive || T.survives(v[j].z, v[j].w)) keep |= 2u << (2 * j);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (tid + j * CONSUMERS < cnt) {
-          if (all_survive || T.survives(v[j].x, v[j].y)) keep |= 1u << (2 * j);
-          if (all_survive || T.survives(v[j].z, v[j].w)) keep |= 2u << (2 * j);
-        }
+    for (int j = 0; j < 8; ++j) {
+      const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
+      const bool ok = tid + (j >> 1) * CONSUMERS < cnt;
+      int cell;
+      const uint32_t code = C.code(x, y, cell);
+      const bool bnd = ok && !all_survive && code != 0 && code != 256;
+      if (ok && (all_survive || code == 256)) keep |= 1u << j;
+      // boundary points go to the warp's ring
+      const unsigned bal = __ballot_sync(FULL, bnd);
+      if (bal) {
+        if (bnd) q[(qtail + __popc(bal & lt)) % QCAP] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+        qtail += __popc(bal);
       }
     }
-    const uint32_t i0 = (uint32_t)(head + 2 * (f + tid));
-    // two half tiles of 4 points each, so one half never exceeds WBUF
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const uint32_t kh = (keep >> (4 * half)) & 15u;
-      int pos = O.reserve(__popc(kh));
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int j = 4 * half + jj;
-        if (kh & (1u << jj)) {
-          const float4& q = v[j >> 1];
-          O.put(pos++, i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1), (j & 1) ? q.z : q.x,
-                (j & 1) ? q.w : q.y);
-        }
+    __syncwarp();
+    while (qtail - qhead >= 32) drain(32);
+    if (__any_sync(FULL, keep != 0)) {
+      int pos = O.reserve(__popc(keep));
+      while (keep) {  // usually none or one
+        const int j = __ffs(keep) - 1;
+        keep &= keep - 1;
+        O.s_idx[pos++] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
       }
+      __syncwarp();
     }
   }
   // Points outside the aligned pairs: block 0 takes the leading point, the
@@ -272,57 +288,132 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter(const float* __res
     const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
     bool k = false;
     uint32_t i = 0;
-    float2 p = make_float2(0.f, 0.f);
     if ((lane == 0 && lead) || (lane == 1 && trail)) {
       i = lane == 0 ? 0u : (uint32_t)(n - 1);
-      p = __ldg(reinterpret_cast<const float2*>(xy) + i);
+      const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
+      if (all_survive) {
+        k = true;
+      } else {
+        const unsigned r = boundary_test(s_e, C, p.x, p.y);
+        esc += r >> 1;
+        k = r & 1;
+      }
+    }
+    O.push(k, i);
+  }
+  __syncwarp();
+  if (qtail > qhead) drain(qtail - qhead);
+  O.flush();
+  for (int off = 16; off; off >>= 1) esc += __shfl_xor_sync(FULL, esc, off);
+  if (lane == 0 && esc) atomicAdd(&h->n_escalated, (unsigned long long)esc);
+}
+
+// ----------------------------------------------------------------------------
+// The plain inside test (int64 orientation against every edge), same stream.
+
+template <bool KEYS>
+__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(const float* __restrict__ xy, int64_t n,
+                                                                     int head, int64_t npairs, int64_t ppb,
+                                                                     WsHeader* h, uint32_t* __restrict__ surv_idx,
+                                                                     unsigned long long* __restrict__ surv_key) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  FilterStream& S = *reinterpret_cast<FilterStream*>(dsm);
+  __shared__ __align__(16) Edge s_e[MAXV];
+  __shared__ uint32_t s_oidx[CONSUMERS / 32][WBUF];
+  __shared__ int s_m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (*reinterpret_cast<volatile uint32_t*>(&h->status) != 0) return;
+  if (tid < MAXV * (int)(sizeof(Edge) / 4))
+    reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
+  if (tid == 0) s_m = h->poly.m;
+  stream_init(S);
+  Tester<HULL_FILTER_EXACT> T;
+  T.E = s_e;
+  T.m = s_m;
+  T.esc = 0;
+  const bool all_survive = s_m < 3;
+  const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
+  StreamRange R;
+  R.p0 = (int64_t)blockIdx.x * ppb;
+  R.p1 = min(R.p0 + ppb, npairs);
+  R.nchunks = R.p1 > R.p0 ? (R.p1 - R.p0 + CHUNK - 1) / CHUNK : 0;
+  R.reverse = true;
+  if (warp == PRODUCER_WARP) {
+    stream_produce(S, R, P, h);
+    return;
+  }
+  WarpOut<KEYS> O;
+  O.s_idx = s_oidx[warp];
+  O.count = 0;
+  O.h = h;
+  O.xy = xy;
+  O.g_idx = surv_idx;
+  O.g_key = surv_key;
+  for (int64_t c = 0; c < R.nchunks; ++c) {
+    const int s = (int)(c % FilterStream::STAGES);
+    if (!mbar_wait(&S.full[s], (unsigned)((c / FilterStream::STAGES) & 1), h)) break;
+    const int cnt = R.count(c);
+    const int64_t f = R.first_pair(c);
+    const float4* st = S.stage[s];
+    float4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = st[tid + j * CONSUMERS];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.empty[s]);
+    const uint32_t i0 = (uint32_t)(head + 2 * (f + tid));
+    uint32_t keep = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
+      if (tid + (j >> 1) * CONSUMERS < cnt && (all_survive || T.survives(x, y))) keep |= 1u << j;
+    }
+    if (__any_sync(FULL, keep != 0)) {
+      int pos = O.reserve(__popc(keep));
+      while (keep) {
+        const int j = __ffs(keep) - 1;
+        keep &= keep - 1;
+        O.s_idx[pos++] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+      }
+      __syncwarp();
+    }
+  }
+  if (warp == 0) {
+    const bool lead = blockIdx.x == 0 && head == 1;
+    const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
+    bool k = false;
+    uint32_t i = 0;
+    if ((lane == 0 && lead) || (lane == 1 && trail)) {
+      i = lane == 0 ? 0u : (uint32_t)(n - 1);
+      const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
       k = all_survive || T.survives(p.x, p.y);
     }
-    const int pos = O.reserve(k ? 1 : 0);
-    if (k) O.put(pos, i, p.x, p.y);
+    O.push(k, i);
   }
   O.flush();
-  if (FILTER == HULL_FILTER_FP32) {
-    unsigned e = T.esc;
-    for (int off = 16; off; off >>= 1) e += __shfl_xor_sync(FULL, e, off);
-    if (lane == 0 && e) atomicAdd(&h->n_escalated, (unsigned long long)e);
-  }
 }
 
 __global__ void k_copy_count(const WsHeader* h, int64_t* out) {
   *out = h->status ? 0 : (int64_t)h->n_surv;
 }
 
-template <int FILTER, bool KEYS>
-size_t filter_dsmem() {
-  return sizeof(FilterStream) + (FILTER == HULL_FILTER_FP32 ? (size_t)GRID * GRID : 0);
-}
-
-template <int FILTER, bool KEYS>
-cudaError_t filter_launch(const float* xy, int64_t n, int head, int64_t npairs, int grid, WsHeader* h,
-                          uint16_t* cells, uint32_t* surv_idx, unsigned long long* surv_key, cudaStream_t st) {
-  static bool attr[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const size_t dsmem = filter_dsmem<FILTER, KEYS>();
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_filter<FILTER, KEYS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+template <class K>
+cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npairs, int grid, int64_t& G,
+                          int64_t& ppb) {
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
     if (e != cudaSuccess) return e;
-    attr[dev] = true;
+    attr_done = true;
   }
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_filter<FILTER, KEYS>, STREAM_THREADS, dsmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, STREAM_THREADS, dsmem);
   occ = std::max(occ, 1);
-  int64_t G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
+  G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
   G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
-  int64_t ppb = (npairs + G - 1) / G;
+  ppb = (npairs + G - 1) / G;
   ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;
   if (ppb == 0) ppb = CHUNK;
   G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
-  k_filter<FILTER, KEYS><<<(unsigned)G, STREAM_THREADS, dsmem, st>>>(xy, n, head, npairs, ppb, h, cells, surv_idx,
-                                                                       surv_key);
-  count_launches(1);
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -335,11 +426,33 @@ cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, u
   const bool keys = surv_key != nullptr;
   const int head = (reinterpret_cast<uintptr_t>(xy) & 15u) ? 1 : 0;
   const int64_t npairs = n > head ? (n - head) / 2 : 0;
-  if (filter == HULL_FILTER_FP32)
-    return keys ? filter_launch<HULL_FILTER_FP32, true>(xy, n, head, npairs, grid, h, cells, surv_idx, surv_key, st)
-                : filter_launch<HULL_FILTER_FP32, false>(xy, n, head, npairs, grid, h, cells, surv_idx, surv_key, st);
-  return keys ? filter_launch<HULL_FILTER_EXACT, true>(xy, n, head, npairs, grid, h, cells, surv_idx, surv_key, st)
-              : filter_launch<HULL_FILTER_EXACT, false>(xy, n, head, npairs, grid, h, cells, surv_idx, surv_key, st);
+  static bool attr[64][4] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  int64_t G = 1, ppb = CHUNK;
+  cudaError_t e;
+  if (filter == HULL_FILTER_FP32) {
+    const size_t ds = sizeof(FilterStream) + (size_t)GRID * GRID;
+    if (keys) {
+      if ((e = stream_launch(k_filter32<true>, attr[dev][0], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      k_filter32<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, cells, surv_idx, surv_key);
+    } else {
+      if ((e = stream_launch(k_filter32<false>, attr[dev][1], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      k_filter32<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, cells, surv_idx, surv_key);
+    }
+  } else {
+    const size_t ds = sizeof(FilterStream);
+    if (keys) {
+      if ((e = stream_launch(k_filter_exact<true>, attr[dev][2], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      k_filter_exact<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, surv_idx, surv_key);
+    } else {
+      if ((e = stream_launch(k_filter_exact<false>, attr[dev][3], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      k_filter_exact<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, surv_idx, surv_key);
+    }
+  }
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st) {
