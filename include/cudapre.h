@@ -131,6 +131,28 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
                          uint32_t* d_hull_idx, int64_t* d_n_hull,
                          const hull_options* opt, void* stream);
 
+/* hull_compute without a caller workspace; the paper has no counterpart (it
+ * is a library convenience, not a step of the method).  The workspace is a
+ * fixed device array inside the library (about 26 MiB per device, allocated
+ * by the CUDA runtime when the library's module loads), so the call allocates
+ * nothing.  It is meant for callers that cannot allocate: loops where
+ * cudaMalloc / cudaFree would synchronise the device, or programs whose
+ * device memory is already fully reserved.
+ *   n                at most HULL_STATIC_MAX_POINTS; larger n returns
+ *                    HULL_ERR_BUDGET before any CUDA call.
+ *   d_hull_idx, d_n_hull, opt, stream   as for hull_compute.
+ * The first call on a device looks up the array's device address (a runtime
+ * query, not a stream operation); make it before any stream capture begins
+ * on that device.  The counters that must start at zero are cleared by every
+ * call on its stream.  There is ONE such workspace per device: calls on the
+ * same device that may overlap on the GPU (other streams, other host threads)
+ * race on it and corrupt each other's results; order them on one stream.
+ * hull_read_stats and the other readers take a workspace pointer and cannot
+ * see this one. */
+#define HULL_STATIC_MAX_POINTS 1048576
+hull_status hull_compute_static(const float* d_xy, int64_t n, uint32_t* d_hull_idx, int64_t* d_n_hull,
+                                const hull_options* opt, void* stream);
+
 /* Number of survivors and of FP32 decisions escalated to the exact test by
  * the last hull_prefilter / hull_compute on this workspace.  Synchronises the
  * stream.  Either output pointer may be NULL (host memory). */

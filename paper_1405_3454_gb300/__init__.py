@@ -37,6 +37,7 @@ ABI_SYMBOLS = (
     "hull_prefilter", "hull_compute", "hull_read_counters", "hull_read_polygon",
     "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version", "hull_read_stats",
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
+    "hull_compute_static",
 )
 HULL_STAGES = 5
 STAGE_NAMES = ("validate", "extremes", "filter", "sort", "chain")
@@ -109,6 +110,8 @@ def load(path: str | None = None):
     lib.hull_timer_read.restype = st
     lib.hull_launch_count.argtypes = []
     lib.hull_launch_count.restype = ctypes.c_int64
+    lib.hull_compute_static.argtypes = [P, i64, P, P, OP, P]
+    lib.hull_compute_static.restype = st
     _lib = lib
     return lib
 
@@ -183,6 +186,17 @@ def hull_compute(d_xy: int, n: int, d_ws: int, ws_bytes: int, d_hull_idx: int, d
                  opt: Options | None, stream: int) -> int:
     o = (opt or Options()).c()
     return load().hull_compute(d_xy, n, d_ws, ws_bytes, d_hull_idx, d_n_hull, ctypes.byref(o), stream or None)
+
+
+HULL_STATIC_MAX_POINTS = 1 << 20
+
+
+def hull_compute_static(d_xy: int, n: int, d_hull_idx: int, d_n_hull: int, opt: Options | None,
+                        stream: int) -> int:
+    """hull_compute on the library's fixed per-device workspace (at most
+    HULL_STATIC_MAX_POINTS points; the call allocates nothing)."""
+    o = (opt or Options()).c()
+    return load().hull_compute_static(d_xy, n, d_hull_idx, d_n_hull, ctypes.byref(o), stream or None)
 
 
 # --------------------------------------------------------------------------
