@@ -73,7 +73,11 @@ struct Poly {
   int32_t kx, ky;       // log2 of the cell sizes
   int32_t rox, roy;     // integer point strictly inside (centre of the inner box)
   int32_t refine_on;    // 1 when (rox, roy) is valid
-  int32_t pad_[4];
+  // Inscribed circle for a quick discard: every point whose float32
+  // (x - ccx)^2 + (y - ccy)^2, computed as fma(dx, dx, dy * dy), is below
+  // cr2 is strictly inside the polygon; cr2 = -1 when there is none.
+  float ccx, ccy, cr2;
+  int32_t pad_;
   float box[4];         // closed inner box x0, x1, y0, y1 (integer-valued);
                         // every point of it is strictly inside; x0 > x1 if empty
   int32_t vx[MAXV], vy[MAXV];

@@ -248,7 +248,34 @@ __device__ void build_edges_and_box(Poly* P, int m, int lane) {
       }
     }
   }
+  // Inscribed circle around the box centre O: r^2 = min over the edges of
+  // orient(O)^2 / (A^2 + B^2), orient exact in int64 and the quotient in
+  // binary64, then shrunk by 2^-18 and rounded down to float32.  The float32
+  // test fma(dx, dx, dy * dy) < cr2 under-estimates the true squared distance
+  // by at most a factor (1 - 2^-24)^4, far inside that margin, so a point
+  // that passes is at distance < r from O: strictly inside every edge.
+  float cr2 = -1.0f;
+  const bool has_box = m >= 3 && box[0] <= box[1];
+  const long long cox = has_box ? (long long)floorf(0.5f * (box[0] + box[1])) : 0;
+  const long long coy = has_box ? (long long)floorf(0.5f * (box[2] + box[3])) : 0;
+  if (has_box) {
+    double d2 = 1e300;
+    if (lane < m) {
+      const int j = (lane + 1) % m;
+      const long long ax = P->vx[lane], ay = P->vy[lane];
+      const long long dx = (long long)P->vx[j] - ax, dy = (long long)P->vy[j] - ay;
+      const long long S = dx * (coy - ay) - dy * (cox - ax);  // > 0: O is strictly inside
+      const double Sd = (double)S;
+      d2 = (Sd * Sd) / (double)(dx * dx + dy * dy);
+    }
+    for (int off = 16; off; off >>= 1) d2 = fmin(d2, __shfl_xor_sync(FULL, d2, off));
+    cr2 = __double2float_rd(d2 * (1.0 - 0x1p-18));
+  }
   if (lane == 0) {
+    P->ccx = (float)cox;
+    P->ccy = (float)coy;
+    P->cr2 = cr2;
+    P->pad_ = 0;
     for (int c = 0; c < 4; ++c) P->box[c] = box[c];
     // An integer point strictly inside: the centre of a non-empty inner box.
     P->refine_on = box[0] <= box[1] ? 1 : 0;

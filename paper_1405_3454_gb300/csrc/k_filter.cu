@@ -7,14 +7,17 @@
 // pass through per-warp staging buffers in shared memory (one global atomic
 // per buffer flush, no block-wide barrier in the streaming loop).
 //
-// FP32 mode.  A point inside the exact inner box is discarded at once.  Else
-// its cell of a GRID x GRID grid over the polygon's bounding box is found with
-// two directed-rounding operations per coordinate; the cell's code lists the
-// edges some point of the cell may fail (0: every point of the cell is
-// strictly inside).  Only those edges are tested: s = fma(A, px, fma(B, py, C))
-// with static bound E -- s > E certainly left, s < -E certainly not (the point
-// survives), otherwise the exact int64 orientation decides (an escalation).
-// Points beyond the grid are outside the bounding box and survive.
+// FP32 mode.  A point inside the polygon's inscribed circle (float32 test with
+// a proven margin) is discarded at once.  Every other point goes, with its
+// coordinates, to a per-warp queue; 32 queued points at a time take the full
+// test.  Its cell of a GRID x GRID grid over the polygon's bounding box is
+// found with two directed-rounding operations per coordinate; the cell's code
+// lists the edges some point of the cell may fail (0: every point of the cell
+// is strictly inside).  Only those edges are tested: s = fma(A, px, fma(B, py,
+// C)) with static bound E -- s > E certainly left, s < -E certainly not (the
+// point survives), otherwise the exact int64 orientation decides (an
+// escalation).  Points beyond the grid are outside the bounding box and
+// survive.
 // EXACT mode (the plain method): the int64 orientation against every edge.
 // Both modes give identical survivor sets.
 #include "internal.cuh"
@@ -69,18 +72,18 @@ struct Tester<HULL_FILTER_EXACT> {
 };
 
 // ----------------------------------------------------------------------------
-// Survivor output: a per-warp staging buffer of point indices in shared
-// memory; a full buffer is flushed by its warp with one global atomic and
-// coalesced stores (the keys are formed then, from the coordinates re-read
-// from L2).  No block-wide barrier in the streaming loop.
-constexpr int WBUF = 256;
+// Survivor output: a per-warp staging buffer of (index, sort key) in shared
+// memory, filled while the point's coordinates are still in registers; a full
+// buffer is flushed by its warp with one global atomic and coalesced stores.
+// No block-wide barrier in the streaming loop.
+constexpr int WBUF = 128;
 
 template <bool KEYS>
 struct WarpOut {
-  uint32_t* s_idx;  // [WBUF] of this warp
-  int count;        // warp-uniform fill level
+  uint32_t* s_idx;            // [WBUF] of this warp
+  unsigned long long* s_key;  // [WBUF] of this warp (KEYS only)
+  int count;                  // warp-uniform fill level
   WsHeader* h;
-  const float* xy;
   uint32_t* g_idx;
   unsigned long long* g_key;
 
@@ -91,56 +94,46 @@ struct WarpOut {
     if (lane == 0 && count) base = atomicAdd(&h->n_surv, (unsigned long long)count);
     base = __shfl_sync(FULL, base, 0);
     for (int k = lane; k < count; k += 32) {
-      const uint32_t i = s_idx[k];
-      g_idx[base + k] = i;
-      if (KEYS) {
-        const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
-        g_key[base + k] = point_key(__float2int_rn(p.x), __float2int_rn(p.y));
-      }
+      g_idx[base + k] = s_idx[k];
+      if (KEYS) g_key[base + k] = s_key[k];
     }
     __syncwarp();
     count = 0;
   }
 
-  // Reserve room for this lane's c (<= 32 * 8 total) survivors; returns its
-  // first slot.
-  __device__ __forceinline__ int reserve(int c) {
-    const int lane = threadIdx.x & 31;
-    int incl = c;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int t = __shfl_up_sync(FULL, incl, off);
-      if (lane >= off) incl += t;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    if (count + total > WBUF) flush();
-    const int base = count + incl - c;
-    count += total;
-    return base;
-  }
-
-  // One survivor per lane at most (ballot placement).
-  __device__ __forceinline__ void push(bool keep, uint32_t idx) {
+  // At most one survivor per lane (ballot placement).
+  __device__ __forceinline__ void push(bool keep, uint32_t idx, float x, float y) {
     const unsigned bal = __ballot_sync(FULL, keep);
     if (!bal) return;
     if (count + 32 > WBUF) flush();
-    if (keep) s_idx[count + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = idx;
+    if (keep) {
+      const int pos = count + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+      s_idx[pos] = idx;
+      if (KEYS) s_key[pos] = point_key(__float2int_rn(x), __float2int_rn(y));
+    }
     count += __popc(bal);
   }
 };
 
 // ----------------------------------------------------------------------------
 // The FP32-filtered inside test.
+//
+// Streaming pass: a point inside the polygon's inscribed circle (float32
+// test with a proven margin) is discarded at once; every other point is
+// queued, with its coordinates and index, in a per-warp ring in shared
+// memory.  Whenever 32 are queued, each lane takes one and runs the full
+// test: cell lookup, then the float32 edge test(s) with exact escalation.
+// No point is read from memory twice.
 
 using FilterStream = StreamSmemT<2>;
-constexpr int QCAP = 320;  // per-warp ring of boundary points (>= 31 + 8 * 32)
+constexpr int QCAP = 288;  // >= 31 left over + 8 * 32 pushed per chunk
 
 struct Cells {
-  const uint8_t* code8;    // shared memory
-  const uint16_t* mask16;  // global memory (several-edge cells)
+  const uint8_t* code8;    // GRID*GRID byte codes (global memory, L1-cached)
+  const uint16_t* mask16;  // GRID*GRID edge masks (several-edge cells)
   float gx, gy, sx, sy;
 
-  // Byte code of the point's cell; 255 + 1 (256) when outside the grid.
+  // Byte code of the point's cell; 256 when outside the grid.
   __device__ __forceinline__ uint32_t code(float x, float y, int& cell) const {
     // exact cell coordinates: floor((x - gx) / 2^kx) from round-down
     // arithmetic (both steps are exact or round toward the floor)
@@ -149,13 +142,13 @@ struct Cells {
     const int cy = __float_as_int(__fmaf_rd(v, sy, 8388608.0f)) - MAGIC;
     const bool in_grid = (unsigned)(cx | cy) < (unsigned)GRID;
     cell = in_grid ? ((cy << GRID_LOG) | cx) : 0;
-    return in_grid ? (uint32_t)code8[cell] : 256u;
+    return in_grid ? (uint32_t)__ldg(code8 + cell) : 256u;
   }
 };
 
-// Full test of a boundary point (cell code 1..255): float32 edge test with
-// exact escalation.  Returns 2 * escalations + (survives ? 1 : 0).
-__device__ __forceinline__ unsigned boundary_test(const Edge* E, const Cells& C, float x, float y) {
+// Full inside test of one point: cell lookup, float32 edge test(s), exact
+// escalation.  Returns 2 * escalations + (survives ? 1 : 0).
+__device__ __forceinline__ unsigned full_test(const Edge* E, const Cells& C, float x, float y) {
   int cell;
   const uint32_t code = C.code(x, y, cell);
   if (code == 0) return 0;
@@ -177,34 +170,34 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __r
                                                                  unsigned long long* __restrict__ surv_key) {
   extern __shared__ __align__(128) unsigned char dsm[];
   FilterStream& S = *reinterpret_cast<FilterStream*>(dsm);
-  uint8_t* s_code = reinterpret_cast<uint8_t*>(dsm + sizeof(FilterStream));  // GRID*GRID
   __shared__ __align__(16) Edge s_e[MAXV];
+  __shared__ __align__(8) float2 s_qxy[CONSUMERS / 32][QCAP];
+  __shared__ uint32_t s_qi[CONSUMERS / 32][QCAP];
+  __shared__ __align__(8) unsigned long long s_okey[CONSUMERS / 32][KEYS ? WBUF : 1];
   __shared__ uint32_t s_oidx[CONSUMERS / 32][WBUF];
-  __shared__ uint32_t s_q[CONSUMERS / 32][QCAP];
   __shared__ int s_pm[5];
+  __shared__ float s_circ[3];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   if (*reinterpret_cast<volatile uint32_t*>(&h->status) != 0) return;
-  // Stage the polygon and the cell grid in shared memory (section 2, Step 3).
+  // Stage the polygon in shared memory (section 2, Step 3).
   if (tid < MAXV * (int)(sizeof(Edge) / 4))
     reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
   if (tid == 0) {
     s_pm[0] = h->poly.m; s_pm[1] = h->poly.gx0; s_pm[2] = h->poly.gy0; s_pm[3] = h->poly.kx; s_pm[4] = h->poly.ky;
-  }
-  if (h->poly.m >= 3) {
-    const uint4* src = reinterpret_cast<const uint4*>(gcells + GRID * GRID);  // the byte codes
-    uint4* dst = reinterpret_cast<uint4*>(s_code);
-    for (int k = tid; k < GRID * GRID / 16; k += STREAM_THREADS) dst[k] = src[k];
+    s_circ[0] = h->poly.ccx; s_circ[1] = h->poly.ccy; s_circ[2] = h->poly.cr2;
   }
   stream_init(S);  // includes a block barrier
   const bool all_survive = s_pm[0] < 3;
   Cells C;
-  C.code8 = s_code;
+  C.code8 = reinterpret_cast<const uint8_t*>(gcells + GRID * GRID);
   C.mask16 = gcells;
   C.gx = (float)s_pm[1];
   C.gy = (float)s_pm[2];
   C.sx = __int_as_float((127 - s_pm[3]) << 23);  // 2^-kx
   C.sy = __int_as_float((127 - s_pm[4]) << 23);
+  const float ccx = s_circ[0], ccy = s_circ[1];
+  const float cr2 = all_survive ? -1.0f : s_circ[2];
   const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
   StreamRange R;
   R.p0 = (int64_t)blockIdx.x * ppb;
@@ -219,27 +212,38 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __r
   }
   WarpOut<KEYS> O;
   O.s_idx = s_oidx[warp];
+  O.s_key = s_okey[warp];
   O.count = 0;
   O.h = h;
-  O.xy = xy;
   O.g_idx = surv_idx;
   O.g_key = surv_key;
-  uint32_t* q = s_q[warp];
-  int qhead = 0, qtail = 0;  // warp-uniform ring positions
+  float2* qxy = s_qxy[warp];
+  uint32_t* qi = s_qi[warp];
+  int qhead = 0, qtail = 0, qn = 0;  // warp-uniform ring state
   unsigned esc = 0;
-  // Test 32 queued boundary points, one per lane.
+  // Full test of `count` (<= 32) queued points, one per lane.
   auto drain = [&](int count) {
     const bool mine = lane < count;
-    const uint32_t i = mine ? q[(qhead + lane) % QCAP] : 0u;
+    int slot = qhead + lane;
+    if (slot >= QCAP) slot -= QCAP;
+    float2 p = make_float2(0.0f, 0.0f);
+    uint32_t i = 0;
     bool keep = false;
     if (mine) {
-      const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
-      const unsigned r = boundary_test(s_e, C, p.x, p.y);
-      esc += r >> 1;
-      keep = r & 1;
+      p = qxy[slot];
+      i = qi[slot];
+      if (all_survive) {
+        keep = true;
+      } else {
+        const unsigned r = full_test(s_e, C, p.x, p.y);
+        esc += r >> 1;
+        keep = r & 1;
+      }
     }
     qhead += count;
-    O.push(keep, i);
+    if (qhead >= QCAP) qhead -= QCAP;
+    qn -= count;
+    O.push(keep, i, p.x, p.y);
   };
   for (int64_t c = 0; c < R.nchunks; ++c) {
     const int s = (int)(c % FilterStream::STAGES);
@@ -253,34 +257,30 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __r
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.empty[s]);
     const uint32_t i0 = (uint32_t)(head + 2 * (f + tid));
-    uint32_t keep = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
-      const bool ok = tid + (j >> 1) * CONSUMERS < cnt;
-      int cell;
-      const uint32_t code = C.code(x, y, cell);
-      const bool bnd = ok && !all_survive && code != 0 && code != 256;
-      if (ok && (all_survive || code == 256)) keep |= 1u << j;
-      // boundary points go to the warp's ring
-      const unsigned bal = __ballot_sync(FULL, bnd);
+      const float dx = x - ccx, dy = y - ccy;
+      const bool need = tid + (j >> 1) * CONSUMERS < cnt && !(fmaf(dx, dx, dy * dy) < cr2);
+      const unsigned bal = __ballot_sync(FULL, need);
       if (bal) {
-        if (bnd) q[(qtail + __popc(bal & lt)) % QCAP] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
-        qtail += __popc(bal);
+        if (need) {
+          int slot = qtail + __popc(bal & lt);
+          if (slot >= QCAP) slot -= QCAP;
+          qxy[slot] = make_float2(x, y);
+          qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+        }
+        const int k = __popc(bal);
+        qtail += k;
+        if (qtail >= QCAP) qtail -= QCAP;
+        qn += k;
       }
     }
     __syncwarp();
-    while (qtail - qhead >= 32) drain(32);
-    if (__any_sync(FULL, keep != 0)) {
-      int pos = O.reserve(__popc(keep));
-      while (keep) {  // usually none or one
-        const int j = __ffs(keep) - 1;
-        keep &= keep - 1;
-        O.s_idx[pos++] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
-      }
-      __syncwarp();
-    }
+    while (qn >= 32) drain(32);
   }
+  __syncwarp();
+  if (qn > 0) drain(qn);
   // Points outside the aligned pairs: block 0 takes the leading point, the
   // last block the trailing one (lanes 0 and 1 of warp 0).
   if (warp == 0) {
@@ -288,21 +288,20 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __r
     const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
     bool k = false;
     uint32_t i = 0;
+    float2 p = make_float2(0.0f, 0.0f);
     if ((lane == 0 && lead) || (lane == 1 && trail)) {
       i = lane == 0 ? 0u : (uint32_t)(n - 1);
-      const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
+      p = __ldg(reinterpret_cast<const float2*>(xy) + i);
       if (all_survive) {
         k = true;
       } else {
-        const unsigned r = boundary_test(s_e, C, p.x, p.y);
+        const unsigned r = full_test(s_e, C, p.x, p.y);
         esc += r >> 1;
         k = r & 1;
       }
     }
-    O.push(k, i);
+    O.push(k, i, p.x, p.y);
   }
-  __syncwarp();
-  if (qtail > qhead) drain(qtail - qhead);
   O.flush();
   for (int off = 16; off; off >>= 1) esc += __shfl_xor_sync(FULL, esc, off);
   if (lane == 0 && esc) atomicAdd(&h->n_escalated, (unsigned long long)esc);
@@ -319,6 +318,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(const float*
   extern __shared__ __align__(128) unsigned char dsm[];
   FilterStream& S = *reinterpret_cast<FilterStream*>(dsm);
   __shared__ __align__(16) Edge s_e[MAXV];
+  __shared__ __align__(8) unsigned long long s_okey[CONSUMERS / 32][KEYS ? WBUF : 1];
   __shared__ uint32_t s_oidx[CONSUMERS / 32][WBUF];
   __shared__ int s_m;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -344,9 +344,9 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(const float*
   }
   WarpOut<KEYS> O;
   O.s_idx = s_oidx[warp];
+  O.s_key = s_okey[warp];
   O.count = 0;
   O.h = h;
-  O.xy = xy;
   O.g_idx = surv_idx;
   O.g_key = surv_key;
   for (int64_t c = 0; c < R.nchunks; ++c) {
@@ -361,20 +361,11 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(const float*
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.empty[s]);
     const uint32_t i0 = (uint32_t)(head + 2 * (f + tid));
-    uint32_t keep = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
-      if (tid + (j >> 1) * CONSUMERS < cnt && (all_survive || T.survives(x, y))) keep |= 1u << j;
-    }
-    if (__any_sync(FULL, keep != 0)) {
-      int pos = O.reserve(__popc(keep));
-      while (keep) {
-        const int j = __ffs(keep) - 1;
-        keep &= keep - 1;
-        O.s_idx[pos++] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
-      }
-      __syncwarp();
+      const bool keep = tid + (j >> 1) * CONSUMERS < cnt && (all_survive || T.survives(x, y));
+      O.push(keep, i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1), x, y);
     }
   }
   if (warp == 0) {
@@ -382,12 +373,13 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(const float*
     const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
     bool k = false;
     uint32_t i = 0;
+    float2 p = make_float2(0.0f, 0.0f);
     if ((lane == 0 && lead) || (lane == 1 && trail)) {
       i = lane == 0 ? 0u : (uint32_t)(n - 1);
-      const float2 p = __ldg(reinterpret_cast<const float2*>(xy) + i);
+      p = __ldg(reinterpret_cast<const float2*>(xy) + i);
       k = all_survive || T.survives(p.x, p.y);
     }
-    O.push(k, i);
+    O.push(k, i, p.x, p.y);
   }
   O.flush();
 }
@@ -433,7 +425,7 @@ cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, u
   int64_t G = 1, ppb = CHUNK;
   cudaError_t e;
   if (filter == HULL_FILTER_FP32) {
-    const size_t ds = sizeof(FilterStream) + (size_t)GRID * GRID;
+    const size_t ds = sizeof(FilterStream);
     if (keys) {
       if ((e = stream_launch(k_filter32<true>, attr[dev][0], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
       k_filter32<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, cells, surv_idx, surv_key);
