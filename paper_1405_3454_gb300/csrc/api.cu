@@ -223,8 +223,9 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   const int64_t cap = std::max<int64_t>(n, 1);
   // The hull of the survivors.  With refinement the survivors in (ka, va)
   // are thinned into (kb, vb) first.  Sets up to SMALL_MAX points take the
-  // one-block path; larger ones the device radix sort (7 passes, ending in
-  // the other buffer) and the chunked chain (its upper chains in the input).
+  // one-block path; larger ones one cooperative launch of the device radix
+  // sort (7 passes, ending in the other buffer) and the chunked chain (its
+  // upper chains in the input).
   const bool refine = o.refine != 0;
   unsigned long long* kin = ka;
   uint32_t* vin = va;
@@ -238,10 +239,17 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   }
   HULL_TRY(launch_small_hull(kin, vin, count, h, reinterpret_cast<SmallWs*>(ws + L.small), d_hull_idx, d_n_hull,
                              st));
-  HULL_TRY(launch_sort(cap, h, count, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt), st));
+  LargeJob J;
+  J.h = h;
+  J.count = count;
+  J.ka = kin; J.va = vin; J.kb = kot; J.vb = vot;
+  J.tilecnt = reinterpret_cast<uint32_t*>(ws + L.tilecnt);
+  J.cnt = reinterpret_cast<uint32_t*>(ws + L.cnt);
+  J.out_idx = d_hull_idx;
+  J.out_n = d_n_hull;
+  J.cap = cap;
+  HULL_TRY(launch_large(nullptr, 1, J, &h->bar_count, &h->status, st));
   mark(4, st);
-  HULL_TRY(launch_chain(cap, h, count, kot, vot, kin, vin, reinterpret_cast<uint32_t*>(ws + L.cnt), d_hull_idx,
-                        d_n_hull, st));
   mark(5, st);
   return HULL_OK;
 }

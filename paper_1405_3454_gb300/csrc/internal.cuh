@@ -100,7 +100,7 @@ struct WsHeader {
   uint32_t done_blocks;   // last-block-done counter of the extreme search
   unsigned long long n_surv;      // survivors written by the inside test
   unsigned long long n_escalated; // float32 decisions escalated to int64
-  unsigned long long pad0_;
+  uint32_t bar_count, bar_gen;  // grid barrier of the cooperative large-set kernel
   uint32_t hist[8][256];  // radix-sort digit histograms (all passes)
   unsigned long long n_surv2;  // survivors left by the refinement round
   unsigned long long pad1_;
@@ -149,14 +149,26 @@ cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, 
 cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, uint16_t* cells,
                           uint32_t* surv_idx, unsigned long long* surv_key, int grid, int block,
                           cudaStream_t st);
-// The large path (sort + chunked chain) runs only when *count > SMALL_MAX.
-cudaError_t launch_sort(int64_t cap, WsHeader* h, const unsigned long long* count,
-                        unsigned long long* keys_a, uint32_t* vals_a, unsigned long long* keys_b,
-                        uint32_t* vals_b, uint32_t* tilecnt, cudaStream_t st);
-cudaError_t launch_chain(int64_t cap, WsHeader* h, const unsigned long long* count,
-                         unsigned long long* keys_s, uint32_t* vals_s, unsigned long long* keys_u,
-                         uint32_t* vals_u, uint32_t* cnt, uint32_t* out_idx, int64_t* out_n,
-                         cudaStream_t st);
+// The large path (sort + chunked chain) of one point set; it runs only when
+// *count > SMALL_MAX and the set's status word is clear.
+struct LargeJob {
+  WsHeader* h;                      // status word and digit histograms of the set
+  const unsigned long long* count;  // survivors to sort (device)
+  unsigned long long* ka;           // survivor keys / indices (capacity cap)
+  uint32_t* va;
+  unsigned long long* kb;           // second buffer pair (capacity cap)
+  uint32_t* vb;
+  uint32_t* tilecnt;                // 256 * sort_tiles(cap)
+  uint32_t* cnt;                    // 4 * ceil(cap / CHAIN_C0)
+  uint32_t* out_idx;                // hull vertex indices (local to the set)
+  int64_t* out_n;
+  int64_t cap;
+};
+// One cooperative launch over `table[0..njobs)` (or `single` when table is
+// null); bar = two zeroed words for the grid barrier, bar_status = where a
+// barrier timeout is recorded.
+cudaError_t launch_large(const LargeJob* table, int njobs, const LargeJob& single, uint32_t* bar,
+                         uint32_t* bar_status, cudaStream_t st);
 cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st);
 
 constexpr int REFINE_BINS = 1024;         // angular bins of the refinement round
@@ -190,7 +202,7 @@ constexpr int SORT_PASSES = 7;            // 8-bit digits over the 52-bit key
 constexpr int CHAIN_C0 = 1024;            // sorted elements per level-0 chunk
 constexpr int CHAIN_FAN = 32;             // chunks merged per later-level group
 
-inline int64_t sort_tiles(int64_t cap) { return (cap + SORT_TILE - 1) / SORT_TILE; }
+__host__ __device__ inline int64_t sort_tiles(int64_t cap) { return (cap + SORT_TILE - 1) / SORT_TILE; }
 int chain_levels(int64_t cap);
 
 }  // namespace cudapre
