@@ -95,6 +95,7 @@ typedef struct hull_options {
 #define HULL_DEVICE_DOMAIN 1u   /* validate found a coordinate outside the domain */
 #define HULL_DEVICE_TIMEOUT 2u  /* a bounded wait expired */
 #define HULL_DEVICE_OVERFLOW 4u /* an internal capacity was exceeded */
+#define HULL_DEVICE_OFFSETS 8u  /* hull_batch: offsets[0] != 0, decreasing, or offsets[S] != n_total */
 
 /* Fills *opt with the defaults (cumulative angles, FP32 filter, no validation,
  * tuned launch shapes, refinement on). */
@@ -130,6 +131,35 @@ hull_status hull_prefilter(const float* d_xy, int64_t n, void* d_ws, size_t ws_b
 hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_bytes,
                          uint32_t* d_hull_idx, int64_t* d_n_hull,
                          const hull_options* opt, void* stream);
+
+/* Bytes of workspace needed by hull_batch for S sets of n_total points in
+ * all: about 28 bytes per point plus about 1.2 MB per set. */
+size_t hull_batch_workspace_bytes(int64_t n_total, int32_t S, const hull_options* opt);
+
+/* The whole method (as hull_compute) on each of S point sets in one call.
+ * Every step runs for all sets at once: the two streaming passes split the
+ * concatenated points evenly over the GPU, the per-set steps run one block
+ * (or a few) per set.
+ *   d_xy             n_total points; set s is points [offsets[s], offsets[s+1]).
+ *                    A set may start at any point (8-byte alignment).
+ *   d_offsets        S+1 int64 in device memory: 0 = offsets[0] <= offsets[1]
+ *                    <= ... <= offsets[S] = n_total; each set below 2^32
+ *                    points.  Checked on the device: a violation records
+ *                    HULL_DEVICE_OFFSETS and every set's hull is empty.
+ *   S                number of sets, >= 0.
+ *   n_total          offsets[S] as known to the caller (sizes the workspace).
+ *   d_ws, ws_bytes   at least hull_batch_workspace_bytes(n_total, S).
+ *   d_hull_idx       room for n_total int64: the hulls of all sets, set after
+ *                    set, as GLOBAL point indices (offsets[s] + the index
+ *                    within the set), each as described under Hull above.
+ *   d_hull_offsets   S+1 int64: set s's hull is d_hull_idx[d_hull_offsets[s]
+ *                    .. d_hull_offsets[s+1]).
+ * Device-side conditions of any set (and HULL_DEVICE_OFFSETS) are or-ed into
+ * the word hull_get_device_status reads from d_ws; then every hull is empty.
+ * The stats and polygon readers do not apply to a batch workspace. */
+hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, int64_t n_total, void* d_ws,
+                       size_t ws_bytes, int64_t* d_hull_idx, int64_t* d_hull_offsets,
+                       const hull_options* opt, void* stream);
 
 /* hull_compute without a caller workspace; the paper has no counterpart (it
  * is a library convenience, not a step of the method).  The workspace is a

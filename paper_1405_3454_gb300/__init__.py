@@ -37,7 +37,7 @@ ABI_SYMBOLS = (
     "hull_prefilter", "hull_compute", "hull_read_counters", "hull_read_polygon",
     "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version", "hull_read_stats",
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
-    "hull_compute_static",
+    "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes",
 )
 HULL_STAGES = 5
 STAGE_NAMES = ("validate", "extremes", "filter", "sort", "chain")
@@ -112,6 +112,10 @@ def load(path: str | None = None):
     lib.hull_launch_count.restype = ctypes.c_int64
     lib.hull_compute_static.argtypes = [P, i64, P, P, OP, P]
     lib.hull_compute_static.restype = st
+    lib.hull_batch_workspace_bytes.argtypes = [i64, ctypes.c_int32, OP]
+    lib.hull_batch_workspace_bytes.restype = sz
+    lib.hull_batch.argtypes = [P, P, ctypes.c_int32, i64, P, sz, P, P, OP, P]
+    lib.hull_batch.restype = st
     _lib = lib
     return lib
 
@@ -189,6 +193,19 @@ def hull_compute(d_xy: int, n: int, d_ws: int, ws_bytes: int, d_hull_idx: int, d
 
 
 HULL_STATIC_MAX_POINTS = 1 << 20
+HULL_DEVICE_OFFSETS = 8
+
+
+def hull_batch_workspace_bytes(n_total: int, S: int, opt: Options | None = None) -> int:
+    o = (opt or Options()).c()
+    return int(load().hull_batch_workspace_bytes(n_total, S, ctypes.byref(o)))
+
+
+def hull_batch(d_xy: int, d_offsets: int, S: int, n_total: int, d_ws: int, ws_bytes: int, d_hull_idx: int,
+               d_hull_offsets: int, opt: Options | None, stream: int) -> int:
+    o = (opt or Options()).c()
+    return load().hull_batch(d_xy or None, d_offsets, S, n_total, d_ws, ws_bytes, d_hull_idx or None,
+                             d_hull_offsets, ctypes.byref(o), stream or None)
 
 
 def hull_compute_static(d_xy: int, n: int, d_hull_idx: int, d_n_hull: int, opt: Options | None,
@@ -239,6 +256,30 @@ def compute(xy, opt: Options | None = None, ws=None, stream=None):
     _check(hull_compute(_ptr(xy), n, _ptr(ws), ws.numel(), _ptr(out), _ptr(cnt), opt, _stream_handle(stream)),
            "hull_compute")
     return out, cnt, ws
+
+
+def batch(xy, offsets, opt: Options | None = None, ws=None, stream=None):
+    """The whole method on each set of a batch.  xy: float32 [n_total, 2] on
+    the device; offsets: int64 [S+1] on the device (set s = rows offsets[s] ..
+    offsets[s+1]).  Returns (hull_idx int64 [n_total] of global row indices,
+    hull_offsets int64 [S+1], ws); set s's hull is
+    hull_idx[hull_offsets[s]:hull_offsets[s+1]]."""
+    import torch
+    n_total = _check_points(xy)
+    if offsets.dtype != torch.int64 or offsets.dim() != 1 or offsets.device != xy.device:
+        raise ValueError("offsets must be a 1-D int64 tensor on the points' device")
+    S = offsets.numel() - 1
+    if S < 0:
+        raise ValueError("offsets must hold S+1 >= 1 entries")
+    opt = opt or Options()
+    need = hull_batch_workspace_bytes(n_total, S, opt)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, xy.device)
+    out = torch.empty(max(n_total, 1), dtype=torch.int64, device=xy.device)
+    hoff = torch.empty(S + 1, dtype=torch.int64, device=xy.device)
+    _check(hull_batch(_ptr(xy), _ptr(offsets), S, n_total, _ptr(ws), ws.numel(), _ptr(out), _ptr(hoff), opt,
+                      _stream_handle(stream)), "hull_batch")
+    return out, hoff, ws
 
 
 def read_counters(ws, stream=None):

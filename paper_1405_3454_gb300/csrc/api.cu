@@ -64,7 +64,7 @@ Layout layout(int64_t n, bool full) {
   size_t off = HEADER_BYTES;
   L.header = 0;
   L.blockres = off;
-  off += align_up(sizeof(BlockBest) * NSLOT * MAX_BLOCKS, 256);
+  off += align_up(sizeof(BlockBest) * NSLOT * (MAX_BLOCKS + 1), 256);
   L.cells = off;
   off += align_up(CELL_BYTES, 256);
   if (full) {
@@ -82,6 +82,47 @@ Layout layout(int64_t n, bool full) {
   L.total = off;
   return L;
 }
+
+// Workspace of hull_batch (S sets, n_total points): a 256-byte batch word
+// block, then the per-set headers and tables, then the per-point buffers
+// (each set's part at its element offset).
+struct BatchLayout {
+  size_t bhdr = 0, hdr = 0, pp = 0, tp = 0, jobs = 0, hcnt = 0, blockres = 0, cells = 0, tri = 0, small = 0,
+         keys_a = 0, vals_a = 0, keys_b = 0, vals_b = 0, tilecnt = 0, cnt = 0, hstage = 0, total = 0;
+};
+
+BatchLayout batch_layout(int64_t n_total, int32_t S) {
+  BatchLayout L;
+  const size_t s = (size_t)std::max<int32_t>(S, 0);
+  const size_t n = (size_t)std::max<int64_t>(n_total, 1);
+  size_t off = 0;
+  auto put = [&](size_t& at, size_t bytes) { at = off; off += align_up(bytes, 256); };
+  put(L.bhdr, 256);
+  put(L.hdr, HEADER_BYTES * s);
+  put(L.pp, 8 * (s + 1));
+  put(L.tp, 8 * (s + 1));
+  put(L.jobs, sizeof(LargeJob) * s);
+  put(L.hcnt, 8 * s);
+  put(L.blockres, sizeof(BlockBest) * NSLOT * ((size_t)MAX_BLOCKS + s));
+  put(L.cells, CELL_BYTES * s);
+  put(L.tri, sizeof(int4) * 2 * REFINE_BINS * s);
+  put(L.small, sizeof(SmallWs) * s);
+  put(L.keys_a, 8 * n);
+  put(L.vals_a, 4 * n);
+  put(L.keys_b, 8 * n);
+  put(L.vals_b, 4 * n);
+  put(L.tilecnt, 4 * 256 * (n / SORT_TILE + s + 1));
+  put(L.cnt, 4 * 4 * (n / CHAIN_C0 + s + 1));
+  put(L.hstage, 4 * n);
+  L.total = off;
+  return L;
+}
+
+// The batch word block: status, then the grid barrier of the large path.
+struct BatchWords {
+  uint32_t status;
+  uint32_t bar_count, bar_gen;
+};
 
 hull_status check_opts(const hull_options* o) {
   if (!o) return HULL_OK;
@@ -107,20 +148,33 @@ hull_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HULL_OK : HUL
     if (e_ != cudaSuccess) return HULL_ERR_CUDA;     \
   } while (0)
 
+Sets single_set(const float* d_xy, int64_t n, char* ws) {
+  Sets S;
+  S.xy = d_xy;
+  S.off = nullptr;
+  S.pp = nullptr;
+  S.n1 = n;
+  S.S = 1;
+  S.hdr = ws;
+  return S;
+}
+
 // Steps 1-3 shared by hull_prefilter and hull_compute.
 hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& L,
                           uint32_t* surv_idx, unsigned long long* surv_key, uint32_t* ext_out,
                           const hull_options& o, cudaStream_t st) {
   WsHeader* h = reinterpret_cast<WsHeader*>(ws + L.header);
+  const Sets S = single_set(d_xy, n, ws + L.header);
   mark(0, st);
   HULL_TRY(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
-  if (o.validate) HULL_TRY(launch_validate(d_xy, n, h, st));
+  if (o.validate) HULL_TRY(launch_validate(d_xy, n, &h->status, st));
   mark(1, st);
-  HULL_TRY(launch_extremes(d_xy, n, o.angles, o.filter, h, ws + L.blockres,
-                           reinterpret_cast<uint16_t*>(ws + L.cells), o.grid, o.block, ext_out, st));
+  const int64_t npairs = S.npairs_of(0);
+  uint16_t* cells = reinterpret_cast<uint16_t*>(ws + L.cells);
+  HULL_TRY(launch_extremes(S, npairs, o.angles, o.filter, &h->status, ws + L.blockres, cells, o.grid, ext_out,
+                           surv_idx, surv_key, st));
   mark(2, st);
-  HULL_TRY(launch_filter(d_xy, n, o.filter, h, reinterpret_cast<uint16_t*>(ws + L.cells), surv_idx,
-                         surv_key, o.grid, o.block, st));
+  HULL_TRY(launch_filter(S, npairs, o.filter, &h->status, cells, surv_idx, surv_key, o.grid, st));
   mark(3, st);
   return HULL_OK;
 }
@@ -227,18 +281,19 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   // sort (7 passes, ending in the other buffer) and the chunked chain (its
   // upper chains in the input).
   const bool refine = o.refine != 0;
+  const Sets S = single_set(d_xy, n, ws);
   unsigned long long* kin = ka;
   uint32_t* vin = va;
   unsigned long long* kot = kb;
   uint32_t* vot = vb;
   const unsigned long long* count = &h->n_surv;
   if (refine) {
-    HULL_TRY(launch_refine(h, ka, va, kb, vb, reinterpret_cast<int4*>(ws + L.tri), cap, st));
+    HULL_TRY(launch_refine(S, &h->status, nullptr, ka, va, kb, vb, reinterpret_cast<int4*>(ws + L.tri), cap, st));
     kin = kb; vin = vb; kot = ka; vot = va;
     count = &h->n_surv2;
   }
-  HULL_TRY(launch_small_hull(kin, vin, count, h, reinterpret_cast<SmallWs*>(ws + L.small), d_hull_idx, d_n_hull,
-                             st));
+  HULL_TRY(launch_small_hull(S, &h->status, refine ? 1 : 0, kin, vin, reinterpret_cast<SmallWs*>(ws + L.small),
+                             d_hull_idx, d_n_hull, st));
   LargeJob J;
   J.h = h;
   J.count = count;
@@ -250,6 +305,82 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   J.cap = cap;
   HULL_TRY(launch_large(nullptr, 1, J, &h->bar_count, &h->status, st));
   mark(4, st);
+  mark(5, st);
+  return HULL_OK;
+}
+
+size_t hull_batch_workspace_bytes(int64_t n_total, int32_t S, const hull_options* opt) {
+  (void)opt;
+  return batch_layout(n_total, S).total;
+}
+
+hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, int64_t n_total, void* d_ws,
+                       size_t ws_bytes, int64_t* d_hull_idx, int64_t* d_hull_offsets, const hull_options* opt,
+                       void* stream) {
+  if (S < 0 || n_total < 0 || n_total > ((int64_t)1 << 40)) return HULL_ERR_INVALID_ARG;
+  if (!d_offsets || !d_hull_offsets || !d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u))
+    return HULL_ERR_INVALID_ARG;
+  if (n_total > 0 && (!d_xy || (reinterpret_cast<uintptr_t>(d_xy) & 7u) || !d_hull_idx)) return HULL_ERR_INVALID_ARG;
+  hull_status s;
+  if ((s = check_opts(opt)) != HULL_OK) return s;
+  const BatchLayout L = batch_layout(n_total, S);
+  if (ws_bytes < L.total) return HULL_ERR_WORKSPACE;
+  const hull_options o = opts_or_default(opt);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(d_ws);
+  BatchWords* bw = reinterpret_cast<BatchWords*>(ws + L.bhdr);
+  // the words and per-set counters that must start at zero
+  HULL_TRY(cudaMemsetAsync(ws, 0, L.hdr + HEADER_BYTES * (size_t)S, st));
+  if (S == 0) {
+    HULL_TRY(cudaMemsetAsync(d_hull_offsets, 0, sizeof(int64_t), st));
+    return HULL_OK;
+  }
+  Sets SS;
+  SS.xy = d_xy;
+  SS.off = d_offsets;
+  SS.pp = reinterpret_cast<const int64_t*>(ws + L.pp);
+  SS.n1 = 0;
+  SS.S = S;
+  SS.hdr = ws + L.hdr;
+  uint32_t* bstatus = &bw->status;
+  auto* ka = reinterpret_cast<unsigned long long*>(ws + L.keys_a);
+  auto* va = reinterpret_cast<uint32_t*>(ws + L.vals_a);
+  auto* kb = reinterpret_cast<unsigned long long*>(ws + L.keys_b);
+  auto* vb = reinterpret_cast<uint32_t*>(ws + L.vals_b);
+  auto* hstage = reinterpret_cast<uint32_t*>(ws + L.hstage);
+  auto* hcnt = reinterpret_cast<int64_t*>(ws + L.hcnt);
+  uint16_t* cells = reinterpret_cast<uint16_t*>(ws + L.cells);
+  mark(0, st);
+  if (o.validate) HULL_TRY(launch_validate(d_xy, n_total, bstatus, st));
+  HULL_TRY(launch_batch_setup(SS, n_total, bstatus, reinterpret_cast<int64_t*>(ws + L.pp), st));
+  mark(1, st);
+  const int64_t pairs_bound = n_total / 2;
+  HULL_TRY(launch_extremes(SS, pairs_bound, o.angles, o.filter, bstatus, ws + L.blockres, cells, o.grid, nullptr, va,
+                           ka, st));
+  mark(2, st);
+  HULL_TRY(launch_filter(SS, pairs_bound, o.filter, bstatus, cells, va, ka, o.grid, st));
+  mark(3, st);
+  const int64_t cap = std::max<int64_t>(n_total, 1);
+  const bool refine = o.refine != 0;
+  unsigned long long* kin = ka;
+  uint32_t* vin = va;
+  unsigned long long* kot = kb;
+  uint32_t* vot = vb;
+  if (refine) {
+    HULL_TRY(launch_refine(SS, bstatus, reinterpret_cast<int64_t*>(ws + L.tp), ka, va, kb, vb,
+                           reinterpret_cast<int4*>(ws + L.tri), cap, st));
+    kin = kb; vin = vb; kot = ka; vot = va;
+  }
+  const int which = refine ? 1 : 0;
+  HULL_TRY(launch_small_hull(SS, bstatus, which, kin, vin, reinterpret_cast<SmallWs*>(ws + L.small), hstage, hcnt,
+                             st));
+  LargeJob* jobs = reinterpret_cast<LargeJob*>(ws + L.jobs);
+  HULL_TRY(launch_batch_jobs(SS, which, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt),
+                             reinterpret_cast<uint32_t*>(ws + L.cnt), hstage, hcnt, jobs, st));
+  LargeJob none{};
+  HULL_TRY(launch_large(jobs, S, none, &bw->bar_count, bstatus, st));
+  mark(4, st);
+  HULL_TRY(launch_batch_emit(SS, bstatus, hcnt, hstage, d_hull_offsets, d_hull_idx, st));
   mark(5, st);
   return HULL_OK;
 }
@@ -305,6 +436,7 @@ hull_status hull_get_device_status(const void* d_ws, uint32_t* h_bits, void* str
   if (h_bits) *h_bits = bits;
   if (bits & HULL_DEVICE_DOMAIN) return HULL_ERR_DOMAIN;
   if (bits & HULL_DEVICE_TIMEOUT) return HULL_ERR_TIMEOUT;
+  if (bits & HULL_DEVICE_OFFSETS) return HULL_ERR_INVALID_ARG;
   if (bits) return HULL_ERR_CUDA;
   return HULL_OK;
 }

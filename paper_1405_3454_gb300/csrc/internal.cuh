@@ -133,22 +133,72 @@ __host__ __device__ inline int32_t key_y(unsigned long long k) {
 }
 
 // ----------------------------------------------------------------------------
+// The point sets of one call.  A single set (hull_prefilter, hull_compute)
+// travels by value with no device tables; a batch keeps its S+1 element
+// offsets (the caller's) and its S+1 pair prefix in device memory.  Set s
+// holds points [off(s), off(s+1)) of xy; its float4 pairs start at its
+// first 16-byte aligned point (the "head" point before it, if any, and an
+// odd trailing point are handled by the finishing kernel).  The pairs of all
+// sets, concatenated, form the virtual pair axis that the streaming passes
+// split evenly over their blocks.
+struct Sets {
+  const float* xy;
+  const int64_t* off;  // S+1 element offsets, or null: one set of n1 points
+  const int64_t* pp;   // S+1 prefix of the sets' pair counts, or null
+  int64_t n1;
+  int S;
+  char* hdr;           // S headers, HEADER_BYTES apart
+
+  __host__ __device__ int64_t off_at(int s) const { return off ? off[s] : (s == 0 ? 0 : n1); }
+  __host__ __device__ const float* xy_of(int s) const { return xy + 2 * off_at(s); }
+  __host__ __device__ int64_t n_of(int s) const { return off_at(s + 1) - off_at(s); }
+  __host__ __device__ int head_of(int s) const {
+    return (n_of(s) > 0 && (reinterpret_cast<uintptr_t>(xy_of(s)) & 15u)) ? 1 : 0;
+  }
+  __host__ __device__ int64_t npairs_of(int s) const {
+    const int64_t n = n_of(s);
+    const int h = head_of(s);
+    return n > h ? (n - h) / 2 : 0;
+  }
+  __host__ __device__ int64_t pp_at(int s) const { return pp ? pp[s] : (s == 0 ? 0 : npairs_of(0)); }
+  __host__ __device__ WsHeader* h(int s) const {
+    return reinterpret_cast<WsHeader*>(hdr + (size_t)s * HEADER_BYTES);
+  }
+  // The set holding virtual pair p (0 <= p < total pairs).
+  __device__ int set_of_pair(int64_t p) const {
+    if (!pp) return 0;
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pp[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+};
+
+// ----------------------------------------------------------------------------
 // Launch shapes and per-device facts.
 int device_sm_count();
 
 // Process-wide count of kernels enqueued by this library (instrumentation).
 void count_launches(int k);
 
-// Launchers (one per translation unit); all enqueue on `st`.
-cudaError_t launch_validate(const float* xy, int64_t n, WsHeader* h, cudaStream_t st);
-// Steps 1-2 and the cell grid: the streaming search, then one finishing block.
-// `partials` holds the per-warp (float32) or per-block (binary64) candidates.
-cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, WsHeader* h,
-                            void* partials, uint16_t* cells, int grid, int block, uint32_t* ext_out,
-                            cudaStream_t st);
-cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, uint16_t* cells,
-                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, int block,
-                          cudaStream_t st);
+// Launchers (one per translation unit); all enqueue on `st`.  `gstatus` is
+// the status word every step checks first (the header's for one set, the
+// batch word for a batch); a nonzero word skips the work.
+cudaError_t launch_validate(const float* xy, int64_t n, uint32_t* status, cudaStream_t st);
+// Steps 1-2 for every set: the streaming search (pairs_bound >= the total
+// pairs of all sets), then one finishing block per set (the 16 extremes,
+// the polygon, the cell grid, and the inside test of the points outside the
+// 16-byte pairs, whose survivors go to surv_idx / surv_key at the set's
+// offset).  `partials` holds (blocks + S) x 16 block results.
+cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int filter, uint32_t* gstatus,
+                            void* partials, uint16_t* cells, int grid, uint32_t* ext_out, uint32_t* surv_idx,
+                            unsigned long long* surv_key, cudaStream_t st);
+// Step 3 for every set: survivors (set-local indices, keys when surv_key is
+// not null) at the set's offset, counted in its header.
+cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32_t* gstatus, uint16_t* cells,
+                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st);
 // The large path (sort + chunked chain) of one point set; it runs only when
 // *count > SMALL_MAX and the set's status word is clear.
 struct LargeJob {
@@ -174,9 +224,10 @@ cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st);
 constexpr int REFINE_BINS = 1024;         // angular bins of the refinement round
 constexpr int SMALL_MAX = 8192;           // survivor sets up to this size: one-block hull
 
-cudaError_t launch_refine(WsHeader* h, const unsigned long long* keys_in, const uint32_t* vals_in,
-                          unsigned long long* keys_out, uint32_t* vals_out, int4* tri, int64_t cap,
-                          cudaStream_t st);
+// The refinement round for every set; tp = S+1 work-tile prefix (batch).
+cudaError_t launch_refine(const Sets& S, const uint32_t* gstatus, int64_t* tp, const unsigned long long* keys_in,
+                          const uint32_t* vals_in, unsigned long long* keys_out, uint32_t* vals_out, int4* tri,
+                          int64_t cap, cudaStream_t st);
 // State of the small-set hull between its launches (in the workspace).
 constexpr int SMALL_NCH = 32;
 struct SmallWs {
@@ -192,9 +243,11 @@ struct SmallWs {
   uint8_t keep[2][SMALL_MAX];
 };
 
-cudaError_t launch_small_hull(const unsigned long long* keys, const uint32_t* vals,
-                              const unsigned long long* count, const WsHeader* h, SmallWs* sw, uint32_t* out,
-                              int64_t* out_n, cudaStream_t st);
+// The one-block hull of every set with 1..SMALL_MAX survivors (which = 0:
+// after Step 3, 1: after the refinement round); sets without survivors get
+// count 0.  out / out_n: per-set hull (set-local indices) and count.
+cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which, const unsigned long long* keys,
+                              const uint32_t* vals, SmallWs* sw, uint32_t* out, int64_t* out_n, cudaStream_t st);
 
 // Sizes used by the sort and chain stages.
 constexpr int SORT_TILE = 4096;           // elements per sort tile
@@ -203,6 +256,19 @@ constexpr int CHAIN_C0 = 1024;            // sorted elements per level-0 chunk
 constexpr int CHAIN_FAN = 32;             // chunks merged per later-level group
 
 __host__ __device__ inline int64_t sort_tiles(int64_t cap) { return (cap + SORT_TILE - 1) / SORT_TILE; }
+// Per-set regions of the sort-tile and chain-count arrays, from the set's
+// element offset: 256 * sort_tiles(n_s) resp. 4 * ceil(n_s / CHAIN_C0)
+// entries fit between consecutive sets' starts (0 for set 0).
+__host__ __device__ inline size_t tiles_at(int64_t off, int s) { return 256 * (size_t)(off / SORT_TILE + s); }
+__host__ __device__ inline size_t chains_at(int64_t off, int s) { return 4 * (size_t)(off / CHAIN_C0 + s); }
 int chain_levels(int64_t cap);
+
+// Batch-only steps (k_batch.cu).
+cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, uint32_t* bstatus, int64_t* pp, cudaStream_t st);
+cudaError_t launch_batch_jobs(const Sets& S, int which, unsigned long long* ka, uint32_t* va, unsigned long long* kb,
+                              uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out, int64_t* out_n,
+                              LargeJob* jobs, cudaStream_t st);
+cudaError_t launch_batch_emit(const Sets& S, uint32_t* bstatus, const int64_t* hcnt, const uint32_t* hstage,
+                              int64_t* hull_offsets, int64_t* hull_idx, cudaStream_t st);
 
 }  // namespace cudapre

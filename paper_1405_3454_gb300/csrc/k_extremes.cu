@@ -18,6 +18,8 @@
 // point.
 #include <cfloat>
 
+#include <utility>
+
 #include "internal.cuh"
 #include "stream.cuh"
 
@@ -480,50 +482,56 @@ __device__ __forceinline__ void ext_seed(const float* tmin, const float* tmax, f
 #endif
 
 template <int ANG>
-__global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(const float* __restrict__ xy, int64_t n,
-                                                                   int head, int64_t npairs, int64_t ppb,
-                                                                   WsHeader* h, BlockBest* bres) {
+__global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(Sets S, int64_t ppb, uint32_t* gstatus,
+                                                                   BlockBest* bres) {
   constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
   extern __shared__ __align__(128) unsigned char dsm[];
   using SS = StreamSmemT<3>;
-  SS& S = *reinterpret_cast<SS*>(dsm);
+  SS& SM = *reinterpret_cast<SS*>(dsm);
   __shared__ __align__(16) float thr[ND];  // trigger thresholds in value space
   __shared__ float w_best[CONSUMERS / 32][ND];   // per-warp running best (score space)
   __shared__ uint32_t w_bidx[CONSUMERS / 32][ND];
+  __shared__ double w_s64[CONSUMERS / 32][ND];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool dead = *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
-  if (tid < CONSUMERS / 32 * ND) {
-    (&w_best[0][0])[tid] = -FLT_MAX;
-    (&w_bidx[0][0])[tid] = NONE;
-  }
-  if (tid < ND) thr[tid] = (tid & 1) ? -FLT_MAX : FLT_MAX;
-  stream_init(S);
-
-  const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
-  StreamRange R;
-  R.p0 = (int64_t)blockIdx.x * ppb;
-  R.p1 = dead ? R.p0 : min(R.p0 + ppb, npairs);
-  R.nchunks = R.p1 > R.p0 ? (R.p1 - R.p0 + CHUNK - 1) / CHUNK : 0;
-  R.reverse = false;
-
+  const bool dead = *reinterpret_cast<volatile uint32_t*>(gstatus) != 0;
+  stream_init(SM);
+  const int64_t P = S.pp_at(S.S);
+  const int64_t v0 = (int64_t)blockIdx.x * ppb;
+  const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
   if (warp == PRODUCER_WARP) {
-    stream_produce(S, R, P, h);
-  } else {
-    for (int64_t c = 0; c < R.nchunks; ++c) {
-      const int s = (int)(c % SS::STAGES);
-      if (!mbar_wait(&S.full[s], (unsigned)((c / SS::STAGES) & 1), h)) break;
-      const int cnt = R.count(c);
-      const int64_t f = R.first_pair(c);
-      const float4* st = S.stage[s];
-      const float4 a = st[tid < cnt ? tid : 0];
-      const float4 b = st[tid + CONSUMERS < cnt ? tid + CONSUMERS : 0];
-      const float4 cc = st[tid + 2 * CONSUMERS < cnt ? tid + 2 * CONSUMERS : 0];
-      const float4 d = st[tid + 3 * CONSUMERS < cnt ? tid + 3 * CONSUMERS : 0];
+    stream_produce_sets(SM, S, v0, v1, false, gstatus);
+    return;
+  }
+  int c = 0;
+  bool stop = false;
+  walk_segments(S, v0, v1, false, [&](int s, int64_t lo, int n) {
+    const float* xy = S.xy_of(s);
+    const int head = S.head_of(s);
+    const float4* Pp = reinterpret_cast<const float4*>(xy + 2 * head);
+    // a new set: clear the running bests and thresholds
+    if (tid < CONSUMERS / 32 * ND) {
+      (&w_best[0][0])[tid] = -FLT_MAX;
+      (&w_bidx[0][0])[tid] = NONE;
+    }
+    if (tid < ND) thr[tid] = (tid & 1) ? -FLT_MAX : FLT_MAX;
+    consumers_sync();
+    const int nck = nchunks(n);
+    for (int k = 0; k < nck; ++k, ++c) {
+      const int st = c % SS::STAGES;
+      if (!stop && !mbar_wait_status(&SM.full[st], (unsigned)((c / SS::STAGES) & 1), gstatus)) stop = true;
+      if (stop) continue;
+      const int f = k * CHUNK;
+      const int cnt = min(CHUNK, n - f);
+      const float4* sp = SM.stage[st];
+      const float4 a = sp[tid < cnt ? tid : 0];
+      const float4 b = sp[tid + CONSUMERS < cnt ? tid + CONSUMERS : 0];
+      const float4 cc = sp[tid + 2 * CONSUMERS < cnt ? tid + 2 * CONSUMERS : 0];
+      const float4 d = sp[tid + 3 * CONSUMERS < cnt ? tid + 3 * CONSUMERS : 0];
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.empty[s]);
+      if (lane == 0) mbar_arrive(&SM.empty[st]);
       float tmin[NV], tmax[NV];
       ext_minmax<ANG>(a, b, cc, d, tmin, tmax);
-      if (c == 0) ext_seed<ANG>(tmin, tmax, thr);
+      if (k == 0) ext_seed<ANG>(tmin, tmax, thr);
       float t[ND];
 #pragma unroll
       for (int q = 0; q < ND / 4; ++q) {
@@ -532,89 +540,62 @@ __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(c
       }
       bool any = false;
 #pragma unroll
-      for (int k = 0; k < NV; ++k) any |= (tmin[k] <= t[2 * k]) | (tmax[k] >= t[2 * k + 1]);
+      for (int kk = 0; kk < NV; ++kk) any |= (tmin[kk] <= t[2 * kk]) | (tmax[kk] >= t[2 * kk + 1]);
       if (__any_sync(FULL, any)) {  // rare: some lane's tile may improve a best
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-          const bool lo = __any_sync(FULL, tmin[k] <= t[2 * k]), hi = __any_sync(FULL, tmax[k] >= t[2 * k + 1]);
-          if (lo || hi) ext_slow<ANG>(k, lo, hi, f, cnt, P, head, thr, w_best[warp], w_bidx[warp], xy);
+        for (int kk = 0; kk < NV; ++kk) {
+          const bool lo2 = __any_sync(FULL, tmin[kk] <= t[2 * kk]), hi2 = __any_sync(FULL, tmax[kk] >= t[2 * kk + 1]);
+          if (lo2 || hi2) ext_slow<ANG>(kk, lo2, hi2, lo + f, cnt, Pp, head, thr, w_best[warp], w_bidx[warp], xy);
         }
       }
     }
-  }
-  __syncthreads();
-  // Points outside the 16-byte-aligned pairs: a leading point (block 0) and
-  // a trailing point (last block), offered to warp 0's bests.
-  if (!dead && tid == 0) {
-    const bool lead = blockIdx.x == 0 && head == 1;
-    const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
-    for (int r = 0; r < 2; ++r) {
-      if (!(r == 0 ? lead : trail)) continue;
-      const uint32_t i = r == 0 ? 0u : (uint32_t)(n - 1);
-      const float2 p = load_point(xy, i);
-      float v[NV];
-      values32<ANG>(p.x, p.y, v);
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        if (better32<ANG>(2 * k, -v[k], i, w_best[0][2 * k], w_bidx[0][2 * k], xy)) {
-          w_best[0][2 * k] = -v[k];
-          w_bidx[0][2 * k] = i;
-        }
-        if (better32<ANG>(2 * k + 1, v[k], i, w_best[0][2 * k + 1], w_bidx[0][2 * k + 1], xy)) {
-          w_best[0][2 * k + 1] = v[k];
-          w_bidx[0][2 * k + 1] = i;
-        }
+    // this block's result for set s: the binary64 score of every warp's
+    // candidate (one lane per direction), then an exact (score, index)
+    // reduction over the warps, into slot (block + set)
+    consumers_sync();
+    if (lane < ND) {
+      const uint32_t i = w_bidx[warp][lane];
+      double sc = -DBL_MAX;
+      if (i != NONE) {
+        const float2 p = load_point(xy, i);
+        sc = score64(ANG, lane, p.x, p.y);
       }
+      w_s64[warp][lane] = sc;
     }
-  }
-  __syncthreads();
-  // Block result: the binary64 score of every warp's candidate (one lane per
-  // direction), then an exact (score, index) reduction over the warps.
-  __shared__ double w_s64[CONSUMERS / 32][ND];
-  if (warp < CONSUMERS / 32 && lane < ND) {
-    const uint32_t i = w_bidx[warp][lane];
-    double sc = -DBL_MAX;
-    if (i != NONE) {
-      const float2 p = load_point(xy, i);
-      sc = score64(ANG, lane, p.x, p.y);
+    consumers_sync();
+    if (tid < ND) {
+      double bs = -DBL_MAX;
+      unsigned long long bk = 0;
+      uint32_t bi = NONE;
+      for (int w = 0; w < CONSUMERS / 32; ++w) {
+        const uint32_t i = w_bidx[w][tid];
+        const double sc = w_s64[w][tid];
+        const unsigned long long kk = dkey(sc);
+        if (i != NONE && (bi == NONE || kk > bk || (kk == bk && i < bi))) { bs = sc; bk = kk; bi = i; }
+      }
+      BlockBest r;
+      r.s = bs;
+      r.idx = bi;
+      r.pad_ = 0;
+      bres[((size_t)blockIdx.x + s) * ND + tid] = r;
     }
-    w_s64[warp][lane] = sc;
-  }
-  __syncthreads();
-  if (tid < ND) {
-    double bs = -DBL_MAX;
-    unsigned long long bk = 0;
-    uint32_t bi = NONE;
-    for (int w = 0; w < CONSUMERS / 32; ++w) {
-      const uint32_t i = w_bidx[w][tid];
-      const double sc = w_s64[w][tid];
-      const unsigned long long k = dkey(sc);
-      if (i != NONE && (bi == NONE || k > bk || (k == bk && i < bi))) { bs = sc; bk = k; bi = i; }
-    }
-    BlockBest r;
-    r.s = bs;
-    r.idx = bi;
-    r.pad_ = 0;
-    bres[(size_t)blockIdx.x * ND + tid] = r;
-  }
+    consumers_sync();
+  });
 }
 
 // ----------------------------------------------------------------------------
 // EXACT mode: the binary64 definition for every point.
 
 template <int ANG>
-__global__ void __launch_bounds__(BLOCK) k_extremes64(const float* __restrict__ xy, int64_t n,
-                                                       int head, int64_t npairs, int64_t ppb,
-                                                       WsHeader* h, BlockBest* blockres) {
+__global__ void __launch_bounds__(BLOCK) k_extremes64(Sets S, int64_t ppb, const uint32_t* gstatus,
+                                                       BlockBest* blockres) {
   constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
   __shared__ double s_red[BLOCK / 32][ND];
   __shared__ uint32_t s_redi[BLOCK / 32][ND];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool dead = *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
+  const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0;
   double best[ND];
   uint32_t bidx[ND];
-#pragma unroll
-  for (int d = 0; d < ND; ++d) { best[d] = -DBL_MAX; bidx[d] = NONE; }
 
   auto offer = [&](float x, float y, uint32_t i) {
 #pragma unroll
@@ -630,56 +611,57 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(const float* __restrict__ 
     }
   };
 
-  const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
-  const int64_t p0 = (int64_t)blockIdx.x * ppb;
-  const int64_t p1 = dead ? p0 : min(p0 + ppb, npairs);
-  for (int64_t base = p0; base < p1; base += STEP) {
+  const int64_t P = S.pp_at(S.S);
+  const int64_t v0 = (int64_t)blockIdx.x * ppb;
+  const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
+  walk_segments(S, v0, v1, false, [&](int s, int64_t lo, int n) {
 #pragma unroll
-    for (int j = 0; j < PAIRS_PER_THREAD; ++j) {
-      const int64_t pp = base + j * BLOCK + tid;
-      if (pp < p1) {
-        const float4 v = __ldcs(P + pp);
-        const uint32_t i = (uint32_t)(head + 2 * pp);
-        offer(v.x, v.y, i);
-        offer(v.z, v.w, i + 1);
+    for (int d = 0; d < ND; ++d) { best[d] = -DBL_MAX; bidx[d] = NONE; }
+    const int head = S.head_of(s);
+    const float4* Pp = reinterpret_cast<const float4*>(S.xy_of(s) + 2 * head) + lo;
+    const uint32_t ibase = (uint32_t)(head + 2 * lo);
+    for (int f = 0; f < n; f += STEP) {
+#pragma unroll
+      for (int j = 0; j < PAIRS_PER_THREAD; ++j) {
+        const int o = f + j * BLOCK + tid;
+        if (o < n) {
+          const float4 v = __ldcs(Pp + o);
+          const uint32_t i = ibase + 2u * (uint32_t)o;
+          offer(v.x, v.y, i);
+          offer(v.z, v.w, i + 1);
+        }
       }
     }
-  }
-  if (!dead && tid == 0) {
-    if (blockIdx.x == 0 && head == 1) { const float2 p = load_point(xy, 0); offer(p.x, p.y, 0); }
-    if (blockIdx.x == gridDim.x - 1 && ((n - head) & 1)) {
-      const float2 p = load_point(xy, (uint32_t)(n - 1));
-      offer(p.x, p.y, (uint32_t)(n - 1));
-    }
-  }
 #pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    double s = best[d];
-    uint32_t i = bidx[d];
-    for (int off = 16; off; off >>= 1) {
-      const double so = __shfl_xor_sync(FULL, s, off);
-      const uint32_t io = __shfl_xor_sync(FULL, i, off);
-      if (io != NONE && (i == NONE || so > s || (so == s && io < i))) { s = so; i = io; }
-    }
-    if (lane == 0) { s_red[warp][d] = s; s_redi[warp][d] = i; }
-  }
-  __syncthreads();
-  if (warp == 0) {
     for (int d = 0; d < ND; ++d) {
-      double s = lane < BLOCK / 32 ? s_red[lane][d] : -DBL_MAX;
-      uint32_t i = lane < BLOCK / 32 ? s_redi[lane][d] : NONE;
+      double sc = best[d];
+      uint32_t i = bidx[d];
       for (int off = 16; off; off >>= 1) {
-        const double so = __shfl_xor_sync(FULL, s, off);
+        const double so = __shfl_xor_sync(FULL, sc, off);
         const uint32_t io = __shfl_xor_sync(FULL, i, off);
-        if (io != NONE && (i == NONE || so > s || (so == s && io < i))) { s = so; i = io; }
+        if (io != NONE && (i == NONE || so > sc || (so == sc && io < i))) { sc = so; i = io; }
       }
-      if (lane == 0) {
-        BlockBest r;
-        r.s = s; r.idx = i; r.pad_ = 0;
-        blockres[(size_t)blockIdx.x * ND + d] = r;
+      if (lane == 0) { s_red[warp][d] = sc; s_redi[warp][d] = i; }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int d = 0; d < ND; ++d) {
+        double sc = lane < BLOCK / 32 ? s_red[lane][d] : -DBL_MAX;
+        uint32_t i = lane < BLOCK / 32 ? s_redi[lane][d] : NONE;
+        for (int off = 16; off; off >>= 1) {
+          const double so = __shfl_xor_sync(FULL, sc, off);
+          const uint32_t io = __shfl_xor_sync(FULL, i, off);
+          if (io != NONE && (i == NONE || so > sc || (so == sc && io < i))) { sc = so; i = io; }
+        }
+        if (lane == 0) {
+          BlockBest r;
+          r.s = sc; r.idx = i; r.pad_ = 0;
+          blockres[((size_t)blockIdx.x + s) * ND + d] = r;
+        }
       }
     }
-  }
+    __syncthreads();
+  });
 }
 
 // ----------------------------------------------------------------------------
@@ -690,9 +672,10 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(const float* __restrict__ 
 constexpr int FIN_THREADS = 1024;
 
 template <int ANG>
-__global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(const float* __restrict__ xy, WsHeader* h,
-                                                               const BlockBest* bres, int64_t nent,
-                                                               uint32_t* ext_out, uint16_t* cells) {
+__global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(Sets S, int64_t ppb, const uint32_t* gstatus,
+                                                               const BlockBest* bres, uint32_t* ext_out,
+                                                               uint16_t* cells_base, uint32_t* surv_idx,
+                                                               unsigned long long* surv_key) {
   constexpr int ND = Dirs<ANG>::ND;
   __shared__ uint32_t s_ext[NSLOT];
   __shared__ unsigned long long s_k[FIN_THREADS / 32][ND];
@@ -700,7 +683,24 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(const float* __re
   __shared__ long long s_ax[MAXV][GRID], s_by[MAXV][GRID];  // per edge: min of A x per column, B y per row
   __shared__ long long s_c[MAXV], s_span[MAXV];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool dead = *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
+  const int set = blockIdx.x;
+  WsHeader* h = S.h(set);
+  const float* xy = S.xy_of(set);
+  const int64_t n = S.n_of(set);
+  const int head = S.head_of(set);
+  uint16_t* cells = cells_base + (size_t)set * (CELL_BYTES / 2);
+  const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0 ||
+                    *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
+  // this set's partial results: slot (block + set) of every block whose
+  // share of the pair axis meets the set
+  int64_t e0 = 0, e1 = 0;
+  if (!dead && S.npairs_of(set) > 0) {
+    e0 = S.pp_at(set) / ppb + set;
+    e1 = (S.pp_at(set + 1) - 1) / ppb + set + 1;
+  }
+  // points outside the 16-byte pairs: the head point and an odd last point
+  const bool lead = !dead && head == 1;
+  const bool trail = !dead && n > head && ((n - head) & 1);
   // every direction at once: per thread over its strided entries, then a
   // warp butterfly and a cross-warp pass (all exact)
   unsigned long long ks[ND];
@@ -710,12 +710,24 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(const float* __re
   auto take = [&](int d, unsigned long long k, uint32_t i) {
     return i != NONE && (bi[d] == NONE || k > ks[d] || (k == ks[d] && i < bi[d]));
   };
-  for (int64_t e = tid; e < nent; e += FIN_THREADS) {
+  for (int64_t e = e0 + tid; e < e1; e += FIN_THREADS) {
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       const BlockBest b = bres[e * ND + d];
       const unsigned long long k = dkey(b.s);
       if (take(d, k, b.idx)) { ks[d] = k; bi[d] = b.idx; }
+    }
+  }
+  if (tid == FIN_THREADS - 1) {
+    for (int r = 0; r < 2; ++r) {
+      if (!(r == 0 ? lead : trail)) continue;
+      const uint32_t i = r == 0 ? 0u : (uint32_t)(n - 1);
+      const float2 p = load_point(xy, i);
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        const unsigned long long k = dkey(score64(ANG, d, p.x, p.y));
+        if (take(d, k, i)) { ks[d] = k; bi[d] = i; }
+      }
     }
   }
   auto butterfly = [&](int d) {
@@ -753,10 +765,30 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(const float* __re
   }
   __syncthreads();
   if (warp == 0) {
-    if (ext_out && lane < NSLOT) ext_out[lane] = s_ext[lane];
+    if (ext_out && lane < NSLOT) ext_out[(size_t)set * NSLOT + lane] = s_ext[lane];
     hull16_warp(xy, s_ext, &h->poly);
   }
   __syncthreads();
+  // The loose points' inside test (Step 3): exact against every edge.
+  if (!dead && tid == 0) {
+    const int mm = h->poly.m;
+    for (int r = 0; r < 2; ++r) {
+      if (!(r == 0 ? lead : trail)) continue;
+      const uint32_t i = r == 0 ? 0u : (uint32_t)(n - 1);
+      const float2 p = load_point(xy, i);
+      const long long px = __float2ll_rn(p.x), py = __float2ll_rn(p.y);
+      bool inside = mm >= 3;
+      for (int k = 0; k < mm && inside; ++k) {
+        const Edge& e = h->poly.e[k];
+        inside = (long long)e.dx * (py - e.ay) - (long long)e.dy * (px - e.ax) > 0;
+      }
+      if (!inside) {
+        const unsigned long long pos = atomicAdd(&h->n_surv, 1ull);
+        surv_idx[S.off_at(set) + pos] = i;
+        if (surv_key) surv_key[S.off_at(set) + pos] = point_key((int32_t)px, (int32_t)py);
+      }
+    }
+  }
   // The cell grid.  For edge k the orientation is A x + B y + C (exact
   // int64); its minimum over a cell is the minimum of A x over the cell's
   // columns plus that of B y over its rows plus C (corners), likewise the
@@ -796,14 +828,14 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(const float* __re
 }
 
 // Domain check (finite, integer-valued, |v| <= 2^24).
-__global__ void k_validate(const float* __restrict__ xy, int64_t n2, WsHeader* h) {
+__global__ void k_validate(const float* __restrict__ xy, int64_t n2, uint32_t* status) {
   bool bad = false;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n2;
        k += (int64_t)gridDim.x * blockDim.x) {
     const float v = __ldg(xy + k);
     bad |= !(fabsf(v) <= 16777216.0f) || truncf(v) != v;  // NaN fails the first test
   }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&h->status, HULL_DEVICE_DOMAIN);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, HULL_DEVICE_DOMAIN);
 }
 
 template <typename K>
@@ -815,22 +847,32 @@ int occupancy(K kernel) {
 
 }  // namespace
 
-cudaError_t launch_validate(const float* xy, int64_t n, WsHeader* h, cudaStream_t st) {
+cudaError_t launch_validate(const float* xy, int64_t n, uint32_t* status, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int64_t want = (2 * n + 255) / 256;
   const int grid = (int)std::min<int64_t>(want, (int64_t)device_sm_count() * 8);
-  k_validate<<<grid, 256, 0, st>>>(xy, 2 * n, h);
+  k_validate<<<grid, 256, 0, st>>>(xy, 2 * n, status);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, WsHeader* h,
-                            void* partials, uint16_t* cells, int grid, int block, uint32_t* ext_out,
-                            cudaStream_t st) {
-  (void)block;
-  const int head = (n > 0 && (reinterpret_cast<uintptr_t>(xy) & 15u)) ? 1 : 0;
-  const int64_t npairs = n > head ? (n - head) / 2 : 0;
-  int64_t G = 1;
+cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int filter, uint32_t* gstatus,
+                            void* partials, uint16_t* cells, int grid, uint32_t* ext_out, uint32_t* surv_idx,
+                            unsigned long long* surv_key, cudaStream_t st) {
+  const int64_t npairs = std::max<int64_t>(pairs_bound, 0);
+  BlockBest* bres = static_cast<BlockBest*>(partials);
+  const unsigned nsets = (unsigned)S.S;
+  // blocks and pairs per block: at most one wave of resident blocks, each
+  // share a whole number of chunks
+  auto shape = [&](int occ) {
+    int64_t G = grid > 0 ? grid : (int64_t)device_sm_count() * std::max(occ, 1);
+    G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
+    int64_t ppb = (npairs + G - 1) / G;
+    ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;
+    if (ppb == 0) ppb = CHUNK;
+    G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
+    return std::make_pair(G, ppb);
+  };
   if (filter == HULL_FILTER_FP32) {
     const size_t dsmem = sizeof(StreamSmemT<3>);
     static bool attr[64][2] = {};
@@ -848,36 +890,23 @@ cudaError_t launch_extremes(const float* xy, int64_t n, int angles, int filter, 
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_extremes32<0>, STREAM_THREADS, dsmem);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_extremes32<1>, STREAM_THREADS, dsmem);
-    occ = std::max(occ, 1);
-    G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
-    G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
-    int64_t ppb = (npairs + G - 1) / G;
-    ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;
-    if (ppb == 0) ppb = CHUNK;
-    G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
-    BlockBest* bres = static_cast<BlockBest*>(partials);
+    const auto gp = shape(occ);
     if (angles == HULL_ANGLES_CUMULATIVE) {
-      k_extremes32<0><<<(unsigned)G, STREAM_THREADS, dsmem, st>>>(xy, n, head, npairs, ppb, h, bres);
-      k_ext_finish<0><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+      k_extremes32<0><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
+      k_ext_finish<0><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
     } else {
-      k_extremes32<1><<<(unsigned)G, STREAM_THREADS, dsmem, st>>>(xy, n, head, npairs, ppb, h, bres);
-      k_ext_finish<1><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+      k_extremes32<1><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
+      k_ext_finish<1><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
     }
   } else {
     const int occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes64<0>) : occupancy(k_extremes64<1>);
-    G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
-    G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + STEP - 1) / STEP));
-    int64_t ppb = (npairs + G - 1) / G;
-    ppb = (ppb + STEP - 1) / STEP * STEP;
-    if (ppb == 0) ppb = STEP;
-    G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
-    BlockBest* bres = static_cast<BlockBest*>(partials);
+    const auto gp = shape(occ);
     if (angles == HULL_ANGLES_CUMULATIVE) {
-      k_extremes64<0><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, bres);
-      k_ext_finish<0><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+      k_extremes64<0><<<(unsigned)gp.first, BLOCK, 0, st>>>(S, gp.second, gstatus, bres);
+      k_ext_finish<0><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
     } else {
-      k_extremes64<1><<<(unsigned)G, BLOCK, 0, st>>>(xy, n, head, npairs, ppb, h, bres);
-      k_ext_finish<1><<<1, FIN_THREADS, 0, st>>>(xy, h, bres, G, ext_out, cells);
+      k_extremes64<1><<<(unsigned)gp.first, BLOCK, 0, st>>>(S, gp.second, gstatus, bres);
+      k_ext_finish<1><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
     }
   }
   count_launches(2);

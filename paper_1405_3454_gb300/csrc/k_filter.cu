@@ -163,13 +163,12 @@ __device__ __forceinline__ unsigned full_test(const Edge* E, const Cells& C, flo
 }
 
 template <bool KEYS>
-__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __restrict__ xy, int64_t n, int head,
-                                                                 int64_t npairs, int64_t ppb, WsHeader* h,
-                                                                 const uint16_t* __restrict__ gcells,
+__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(Sets S, int64_t ppb, uint32_t* gstatus,
+                                                                 const uint16_t* __restrict__ cells_base,
                                                                  uint32_t* __restrict__ surv_idx,
                                                                  unsigned long long* __restrict__ surv_key) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  FilterStream& S = *reinterpret_cast<FilterStream*>(dsm);
+  FilterStream& SM = *reinterpret_cast<FilterStream*>(dsm);
   __shared__ __align__(16) Edge s_e[MAXV];
   __shared__ __align__(8) float2 s_qxy[CONSUMERS / 32][QCAP];
   __shared__ uint32_t s_qi[CONSUMERS / 32][QCAP];
@@ -179,48 +178,27 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __r
   __shared__ float s_circ[3];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  if (*reinterpret_cast<volatile uint32_t*>(&h->status) != 0) return;
-  // Stage the polygon in shared memory (section 2, Step 3).
-  if (tid < MAXV * (int)(sizeof(Edge) / 4))
-    reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
-  if (tid == 0) {
-    s_pm[0] = h->poly.m; s_pm[1] = h->poly.gx0; s_pm[2] = h->poly.gy0; s_pm[3] = h->poly.kx; s_pm[4] = h->poly.ky;
-    s_circ[0] = h->poly.ccx; s_circ[1] = h->poly.ccy; s_circ[2] = h->poly.cr2;
-  }
-  stream_init(S);  // includes a block barrier
-  const bool all_survive = s_pm[0] < 3;
-  Cells C;
-  C.code8 = reinterpret_cast<const uint8_t*>(gcells + GRID * GRID);
-  C.mask16 = gcells;
-  C.gx = (float)s_pm[1];
-  C.gy = (float)s_pm[2];
-  C.sx = __int_as_float((127 - s_pm[3]) << 23);  // 2^-kx
-  C.sy = __int_as_float((127 - s_pm[4]) << 23);
-  const float ccx = s_circ[0], ccy = s_circ[1];
-  const float cr2 = all_survive ? -1.0f : s_circ[2];
-  const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
-  StreamRange R;
-  R.p0 = (int64_t)blockIdx.x * ppb;
-  R.p1 = min(R.p0 + ppb, npairs);
-  R.nchunks = R.p1 > R.p0 ? (R.p1 - R.p0 + CHUNK - 1) / CHUNK : 0;
+  const bool dead = *reinterpret_cast<volatile uint32_t*>(gstatus) != 0;
+  stream_init(SM);
+  const int64_t P = S.pp_at(S.S);
+  const int64_t v0 = (int64_t)blockIdx.x * ppb;
+  const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
   // Chunks run last-to-first: the extreme search streamed each block's range
   // first-to-last, so the tail of every range is still in L2.
-  R.reverse = true;
   if (warp == PRODUCER_WARP) {
-    stream_produce(S, R, P, h);
+    stream_produce_sets(SM, S, v0, v1, true, gstatus);
     return;
   }
   WarpOut<KEYS> O;
   O.s_idx = s_oidx[warp];
   O.s_key = s_okey[warp];
   O.count = 0;
-  O.h = h;
-  O.g_idx = surv_idx;
-  O.g_key = surv_key;
   float2* qxy = s_qxy[warp];
   uint32_t* qi = s_qi[warp];
   int qhead = 0, qtail = 0, qn = 0;  // warp-uniform ring state
   unsigned esc = 0;
+  bool all_survive = true;
+  Cells C;
   // Full test of `count` (<= 32) queued points, one per lane.
   auto drain = [&](int count) {
     const bool mine = lane < count;
@@ -245,143 +223,151 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(const float* __r
     qn -= count;
     O.push(keep, i, p.x, p.y);
   };
-  for (int64_t c = 0; c < R.nchunks; ++c) {
-    const int s = (int)(c % FilterStream::STAGES);
-    if (!mbar_wait(&S.full[s], (unsigned)((c / FilterStream::STAGES) & 1), h)) break;
-    const int cnt = R.count(c);
-    const int64_t f = R.first_pair(c);
-    const float4* st = S.stage[s];
-    float4 v[4];
+  int c = 0;
+  bool stop = false;
+  walk_segments(S, v0, v1, true, [&](int set, int64_t lo, int n) {
+    // a new set: its polygon, inscribed circle and cell grid (section 2,
+    // Step 3: the polygon goes to shared memory), its output
+    consumers_sync();
+    WsHeader* h = S.h(set);
+    if (tid < MAXV * (int)(sizeof(Edge) / 4))
+      reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
+    if (tid == 0) {
+      s_pm[0] = h->poly.m; s_pm[1] = h->poly.gx0; s_pm[2] = h->poly.gy0; s_pm[3] = h->poly.kx; s_pm[4] = h->poly.ky;
+      s_circ[0] = h->poly.ccx; s_circ[1] = h->poly.ccy; s_circ[2] = h->poly.cr2;
+    }
+    consumers_sync();
+    all_survive = s_pm[0] < 3;
+    const uint16_t* cells = cells_base + (size_t)set * (CELL_BYTES / 2);
+    C.code8 = reinterpret_cast<const uint8_t*>(cells + GRID * GRID);
+    C.mask16 = cells;
+    C.gx = (float)s_pm[1];
+    C.gy = (float)s_pm[2];
+    C.sx = __int_as_float((127 - s_pm[3]) << 23);  // 2^-kx
+    C.sy = __int_as_float((127 - s_pm[4]) << 23);
+    const float ccx = s_circ[0], ccy = s_circ[1];
+    const float cr2 = all_survive ? -1.0f : s_circ[2];
+    O.h = h;
+    O.g_idx = surv_idx + S.off_at(set);
+    O.g_key = KEYS ? surv_key + S.off_at(set) : nullptr;
+    esc = 0;
+    const uint32_t ibase = (uint32_t)(S.head_of(set) + 2 * lo) + 2u * (uint32_t)tid;
+    const int nck = nchunks(n);
+    for (int k = 0; k < nck; ++k, ++c) {
+      const int st = c % FilterStream::STAGES;
+      if (!stop && !mbar_wait_status(&SM.full[st], (unsigned)((c / FilterStream::STAGES) & 1), gstatus)) stop = true;
+      if (stop) continue;
+      const int f = chunk_first(k, nck, true);
+      const int cnt = min(CHUNK, n - f);
+      const float4* sp = SM.stage[st];
+      float4 v[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = st[tid + j * CONSUMERS];  // beyond cnt: ignored below
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&S.empty[s]);
-    const uint32_t i0 = (uint32_t)(head + 2 * (f + tid));
+      for (int j = 0; j < 4; ++j) v[j] = sp[tid + j * CONSUMERS];  // beyond cnt: ignored below
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&SM.empty[st]);
+      const uint32_t i0 = ibase + 2u * (uint32_t)f;
+      const int lim = cnt - tid;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
-      const float dx = x - ccx, dy = y - ccy;
-      const bool need = tid + (j >> 1) * CONSUMERS < cnt && !(fmaf(dx, dx, dy * dy) < cr2);
-      const unsigned bal = __ballot_sync(FULL, need);
-      if (bal) {
-        if (need) {
-          int slot = qtail + __popc(bal & lt);
-          if (slot >= QCAP) slot -= QCAP;
-          qxy[slot] = make_float2(x, y);
-          qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+      for (int j = 0; j < 8; ++j) {
+        const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
+        const float dx = x - ccx, dy = y - ccy;
+        const bool need = (j >> 1) * CONSUMERS < lim && !(fmaf(dx, dx, dy * dy) < cr2);
+        const unsigned bal = __ballot_sync(FULL, need);
+        if (bal) {
+          if (need) {
+            int slot = qtail + __popc(bal & lt);
+            if (slot >= QCAP) slot -= QCAP;
+            qxy[slot] = make_float2(x, y);
+            qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+          }
+          const int kq = __popc(bal);
+          qtail += kq;
+          if (qtail >= QCAP) qtail -= QCAP;
+          qn += kq;
         }
-        const int k = __popc(bal);
-        qtail += k;
-        if (qtail >= QCAP) qtail -= QCAP;
-        qn += k;
       }
+      __syncwarp();
+      while (qn >= 32) drain(32);
     }
+    // finish the set: queued points, buffered survivors, counters
     __syncwarp();
-    while (qn >= 32) drain(32);
-  }
-  __syncwarp();
-  if (qn > 0) drain(qn);
-  // Points outside the aligned pairs: block 0 takes the leading point, the
-  // last block the trailing one (lanes 0 and 1 of warp 0).
-  if (warp == 0) {
-    const bool lead = blockIdx.x == 0 && head == 1;
-    const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
-    bool k = false;
-    uint32_t i = 0;
-    float2 p = make_float2(0.0f, 0.0f);
-    if ((lane == 0 && lead) || (lane == 1 && trail)) {
-      i = lane == 0 ? 0u : (uint32_t)(n - 1);
-      p = __ldg(reinterpret_cast<const float2*>(xy) + i);
-      if (all_survive) {
-        k = true;
-      } else {
-        const unsigned r = full_test(s_e, C, p.x, p.y);
-        esc += r >> 1;
-        k = r & 1;
-      }
-    }
-    O.push(k, i, p.x, p.y);
-  }
-  O.flush();
-  for (int off = 16; off; off >>= 1) esc += __shfl_xor_sync(FULL, esc, off);
-  if (lane == 0 && esc) atomicAdd(&h->n_escalated, (unsigned long long)esc);
+    if (qn > 0) drain(qn);
+    O.flush();
+    for (int off = 16; off; off >>= 1) esc += __shfl_xor_sync(FULL, esc, off);
+    if (lane == 0 && esc) atomicAdd(&h->n_escalated, (unsigned long long)esc);
+  });
 }
 
 // ----------------------------------------------------------------------------
 // The plain inside test (int64 orientation against every edge), same stream.
 
 template <bool KEYS>
-__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(const float* __restrict__ xy, int64_t n,
-                                                                     int head, int64_t npairs, int64_t ppb,
-                                                                     WsHeader* h, uint32_t* __restrict__ surv_idx,
+__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(Sets S, int64_t ppb, uint32_t* gstatus,
+                                                                     uint32_t* __restrict__ surv_idx,
                                                                      unsigned long long* __restrict__ surv_key) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  FilterStream& S = *reinterpret_cast<FilterStream*>(dsm);
+  FilterStream& SM = *reinterpret_cast<FilterStream*>(dsm);
   __shared__ __align__(16) Edge s_e[MAXV];
   __shared__ __align__(8) unsigned long long s_okey[CONSUMERS / 32][KEYS ? WBUF : 1];
   __shared__ uint32_t s_oidx[CONSUMERS / 32][WBUF];
   __shared__ int s_m;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (*reinterpret_cast<volatile uint32_t*>(&h->status) != 0) return;
-  if (tid < MAXV * (int)(sizeof(Edge) / 4))
-    reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
-  if (tid == 0) s_m = h->poly.m;
-  stream_init(S);
-  Tester<HULL_FILTER_EXACT> T;
-  T.E = s_e;
-  T.m = s_m;
-  T.esc = 0;
-  const bool all_survive = s_m < 3;
-  const float4* P = reinterpret_cast<const float4*>(xy + 2 * head);
-  StreamRange R;
-  R.p0 = (int64_t)blockIdx.x * ppb;
-  R.p1 = min(R.p0 + ppb, npairs);
-  R.nchunks = R.p1 > R.p0 ? (R.p1 - R.p0 + CHUNK - 1) / CHUNK : 0;
-  R.reverse = true;
+  const bool dead = *reinterpret_cast<volatile uint32_t*>(gstatus) != 0;
+  stream_init(SM);
+  const int64_t P = S.pp_at(S.S);
+  const int64_t v0 = (int64_t)blockIdx.x * ppb;
+  const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
   if (warp == PRODUCER_WARP) {
-    stream_produce(S, R, P, h);
+    stream_produce_sets(SM, S, v0, v1, true, gstatus);
     return;
   }
+  Tester<HULL_FILTER_EXACT> T;
+  T.E = s_e;
+  T.m = 0;
+  T.esc = 0;
+  bool all_survive = true;
   WarpOut<KEYS> O;
   O.s_idx = s_oidx[warp];
   O.s_key = s_okey[warp];
   O.count = 0;
-  O.h = h;
-  O.g_idx = surv_idx;
-  O.g_key = surv_key;
-  for (int64_t c = 0; c < R.nchunks; ++c) {
-    const int s = (int)(c % FilterStream::STAGES);
-    if (!mbar_wait(&S.full[s], (unsigned)((c / FilterStream::STAGES) & 1), h)) break;
-    const int cnt = R.count(c);
-    const int64_t f = R.first_pair(c);
-    const float4* st = S.stage[s];
-    float4 v[4];
+  int c = 0;
+  bool stop = false;
+  walk_segments(S, v0, v1, true, [&](int set, int64_t lo, int n) {
+    consumers_sync();
+    WsHeader* h = S.h(set);
+    if (tid < MAXV * (int)(sizeof(Edge) / 4))
+      reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
+    if (tid == 0) s_m = h->poly.m;
+    consumers_sync();
+    T.m = s_m;
+    all_survive = s_m < 3;
+    O.h = h;
+    O.g_idx = surv_idx + S.off_at(set);
+    O.g_key = KEYS ? surv_key + S.off_at(set) : nullptr;
+    const uint32_t ibase = (uint32_t)(S.head_of(set) + 2 * lo) + 2u * (uint32_t)tid;
+    const int nck = nchunks(n);
+    for (int k = 0; k < nck; ++k, ++c) {
+      const int st = c % FilterStream::STAGES;
+      if (!stop && !mbar_wait_status(&SM.full[st], (unsigned)((c / FilterStream::STAGES) & 1), gstatus)) stop = true;
+      if (stop) continue;
+      const int f = chunk_first(k, nck, true);
+      const int cnt = min(CHUNK, n - f);
+      const float4* sp = SM.stage[st];
+      float4 v[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = st[tid + j * CONSUMERS];
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&S.empty[s]);
-    const uint32_t i0 = (uint32_t)(head + 2 * (f + tid));
+      for (int j = 0; j < 4; ++j) v[j] = sp[tid + j * CONSUMERS];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&SM.empty[st]);
+      const uint32_t i0 = ibase + 2u * (uint32_t)f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
-      const bool keep = tid + (j >> 1) * CONSUMERS < cnt && (all_survive || T.survives(x, y));
-      O.push(keep, i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1), x, y);
+      for (int j = 0; j < 8; ++j) {
+        const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
+        const bool keep = tid + (j >> 1) * CONSUMERS < cnt && (all_survive || T.survives(x, y));
+        O.push(keep, i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1), x, y);
+      }
     }
-  }
-  if (warp == 0) {
-    const bool lead = blockIdx.x == 0 && head == 1;
-    const bool trail = blockIdx.x == gridDim.x - 1 && ((n - head) & 1);
-    bool k = false;
-    uint32_t i = 0;
-    float2 p = make_float2(0.0f, 0.0f);
-    if ((lane == 0 && lead) || (lane == 1 && trail)) {
-      i = lane == 0 ? 0u : (uint32_t)(n - 1);
-      p = __ldg(reinterpret_cast<const float2*>(xy) + i);
-      k = all_survive || T.survives(p.x, p.y);
-    }
-    O.push(k, i, p.x, p.y);
-  }
-  O.flush();
+    O.flush();
+  });
 }
 
 __global__ void k_copy_count(const WsHeader* h, int64_t* out) {
@@ -410,37 +396,33 @@ cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npair
 
 }  // namespace
 
-cudaError_t launch_filter(const float* xy, int64_t n, int filter, WsHeader* h, uint16_t* cells,
-                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, int block,
-                          cudaStream_t st) {
-  (void)block;
-  if (n == 0) return cudaSuccess;
+cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32_t* gstatus, uint16_t* cells,
+                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st) {
+  const int64_t npairs = std::max<int64_t>(pairs_bound, 0);
+  if (npairs == 0) return cudaSuccess;  // every point is a loose point (finishing kernel)
   const bool keys = surv_key != nullptr;
-  const int head = (reinterpret_cast<uintptr_t>(xy) & 15u) ? 1 : 0;
-  const int64_t npairs = n > head ? (n - head) / 2 : 0;
   static bool attr[64][4] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   int64_t G = 1, ppb = CHUNK;
   cudaError_t e;
+  const size_t ds = sizeof(FilterStream);
   if (filter == HULL_FILTER_FP32) {
-    const size_t ds = sizeof(FilterStream);
     if (keys) {
       if ((e = stream_launch(k_filter32<true>, attr[dev][0], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
-      k_filter32<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, cells, surv_idx, surv_key);
+      k_filter32<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key);
     } else {
       if ((e = stream_launch(k_filter32<false>, attr[dev][1], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
-      k_filter32<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, cells, surv_idx, surv_key);
+      k_filter32<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key);
     }
   } else {
-    const size_t ds = sizeof(FilterStream);
     if (keys) {
       if ((e = stream_launch(k_filter_exact<true>, attr[dev][2], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
-      k_filter_exact<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, surv_idx, surv_key);
+      k_filter_exact<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, surv_idx, surv_key);
     } else {
       if ((e = stream_launch(k_filter_exact<false>, attr[dev][3], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
-      k_filter_exact<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(xy, n, head, npairs, ppb, h, surv_idx, surv_key);
+      k_filter_exact<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, surv_idx, surv_key);
     }
   }
   count_launches(1);

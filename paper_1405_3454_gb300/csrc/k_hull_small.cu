@@ -90,16 +90,25 @@ __device__ __forceinline__ int64_t count_of(const WsHeader* h, const unsigned lo
 }
 
 // prep: sort, dedupe, chunk chains -> SmallWs (global).
-__global__ void __launch_bounds__(SB, 1) k_small_prep(const unsigned long long* __restrict__ kin,
-                                                       const uint32_t* __restrict__ vin,
-                                                       const unsigned long long* count, const WsHeader* h,
-                                                       SmallWs* sw, uint32_t* __restrict__ out, int64_t* out_n) {
+__global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gstatus, int which,
+                                                       const unsigned long long* __restrict__ kin_base,
+                                                       const uint32_t* __restrict__ vin_base, SmallWs* sw_base,
+                                                       uint32_t* __restrict__ out_base, int64_t* out_n_base) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int s_w[32];
   __shared__ int s_tot;
   __shared__ int s_cnt[2][NCH];
   const int tid = threadIdx.x;
-  const int64_t m64 = count_of(h, count);
+  const int set = blockIdx.x;
+  const WsHeader* h = S.h(set);
+  const int64_t o = S.off_at(set);
+  const unsigned long long* kin = kin_base + o;
+  const uint32_t* vin = vin_base + o;
+  uint32_t* out = out_base + o;
+  int64_t* out_n = out_n_base + set;
+  SmallWs* sw = sw_base + set;
+  const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0;
+  const int64_t m64 = dead ? 0 : count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
   if (m64 > SMALL_MAX || m64 == 0) {  // the large path, or nothing to do
     if (tid == 0) {
       sw->active = 0;
@@ -282,11 +291,12 @@ __device__ __forceinline__ void prune_one(const SmallWs* sw, int s, int j) {
 }
 
 // prune: one warp per chunk-chain vertex (lower ones first, then upper).
-__global__ void __launch_bounds__(256) k_small_prune(const SmallWs* sw) {
+__global__ void __launch_bounds__(256) k_small_prune(const SmallWs* sw_base) {
+  const SmallWs* sw = sw_base + blockIdx.x;  // one set per grid column
   if (!*reinterpret_cast<const volatile int*>(&sw->active)) return;
   const int nl = sw->base[0][NCH], total = nl + sw->base[1][NCH];
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
+  const int warps = (gridDim.y * blockDim.x) >> 5;
+  for (int g = (blockIdx.y * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
     if (g < nl) prune_one<1>(sw, 0, g);
     else prune_one<-1>(sw, 1, g - nl);
   }
@@ -294,12 +304,16 @@ __global__ void __launch_bounds__(256) k_small_prune(const SmallWs* sw) {
 
 // emit: the lower hull left to right without its last point, then the upper
 // hull right to left without its first and last points.
-__global__ void __launch_bounds__(SB, 1) k_small_emit(const SmallWs* sw, uint32_t* __restrict__ out,
-                                                       int64_t* out_n) {
+__global__ void __launch_bounds__(SB, 1) k_small_emit(Sets S, const SmallWs* sw_base, uint32_t* __restrict__ out_base,
+                                                       int64_t* out_n_base) {
   __shared__ int s_w[32];
   __shared__ int s_tot;
   __shared__ int s_lower;
   const int tid = threadIdx.x;
+  const int set = blockIdx.x;
+  const SmallWs* sw = sw_base + set;
+  uint32_t* out = out_base + S.off_at(set);
+  int64_t* out_n = out_n_base + set;
   if (!*reinterpret_cast<const volatile int*>(&sw->active)) return;
   const int C = sw->C;
   for (int s = 0; s < 2; ++s) {
@@ -338,9 +352,8 @@ size_t small_hull_smem() {
   return SMALL_MAX * (sizeof(unsigned long long) + sizeof(uint32_t) + 2 * sizeof(uint16_t));
 }
 
-cudaError_t launch_small_hull(const unsigned long long* keys, const uint32_t* vals,
-                              const unsigned long long* count, const WsHeader* h, SmallWs* sw, uint32_t* out,
-                              int64_t* out_n, cudaStream_t st) {
+cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which, const unsigned long long* keys,
+                              const uint32_t* vals, SmallWs* sw, uint32_t* out, int64_t* out_n, cudaStream_t st) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -350,9 +363,12 @@ cudaError_t launch_small_hull(const unsigned long long* keys, const uint32_t* va
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  k_small_prep<<<1, SB, smem, st>>>(keys, vals, count, h, sw, out, out_n);
-  k_small_prune<<<(unsigned)(2 * SMALL_MAX / 8), 256, 0, st>>>(sw);
-  k_small_emit<<<1, SB, 0, st>>>(sw, out, out_n);
+  const unsigned nsets = (unsigned)S.S;
+  k_small_prep<<<nsets, SB, smem, st>>>(S, gstatus, which, keys, vals, sw, out, out_n);
+  // one set: a wide grid (one warp per candidate); a batch: a few blocks per set
+  const unsigned px = S.S == 1 ? (unsigned)(2 * SMALL_MAX / 8) : 8u;
+  k_small_prune<<<dim3(nsets, px), 256, 0, st>>>(sw);
+  k_small_emit<<<nsets, SB, 0, st>>>(S, sw, out, out_n);
   count_launches(3);
   return cudaGetLastError();
 }

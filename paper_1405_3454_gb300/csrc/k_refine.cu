@@ -35,46 +35,98 @@ __device__ __forceinline__ int bin_of(float qx, float qy) {
   return min(max(b, 0), REFINE_BINS - 1);
 }
 
+constexpr int RT = 4 * RBLOCK;  // survivors per work tile (4 per thread)
+
+// Work tiles over the sets' survivor counts: tile t of set s covers its
+// survivors [(t - tp[s]) RT, ...).  One set: tp == null and the tiles of set
+// 0 follow from its count.
+struct Tiles {
+  const int64_t* tp;
+  int S;
+  __device__ int64_t total(const Sets& SS, const uint32_t* gstatus) const {
+    if (*reinterpret_cast<const volatile uint32_t*>(gstatus)) return 0;
+    if (tp) return tp[S];
+    const WsHeader* h = SS.h(0);
+    return (count_of(h, &h->n_surv) + RT - 1) / RT;
+  }
+  __device__ int set_of(int64_t t) const {
+    if (!tp) return 0;
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tp[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+  __device__ int64_t first(int s) const { return tp ? tp[s] : 0; }
+};
+
 // Pass 1: per bin, the survivor farthest from O (packed squared distance and
 // survivor position; ties go to the larger position, any choice is valid).
-__global__ void __launch_bounds__(RBLOCK) k_refine_bins(const unsigned long long* __restrict__ keys,
-                                                         WsHeader* h) {
+// A block accumulates in shared memory while its tiles stay in one set.
+__global__ void __launch_bounds__(RBLOCK) k_refine_bins(Sets S, Tiles T, const uint32_t* gstatus,
+                                                         const unsigned long long* __restrict__ keys_base) {
   __shared__ unsigned long long s_bin[REFINE_BINS];
-  for (int k = threadIdx.x; k < REFINE_BINS; k += RBLOCK) s_bin[k] = 0;
-  __syncthreads();
-  const int64_t m = count_of(h, &h->n_surv);
-  const float ox = (float)h->poly.rox, oy = (float)h->poly.roy;
-  if (h->poly.refine_on) {
-    // 4 independent loads in flight per thread
-    const int64_t stride = (int64_t)gridDim.x * RBLOCK;
-    for (int64_t j0 = (int64_t)blockIdx.x * RBLOCK + threadIdx.x; j0 < m; j0 += 4 * stride) {
-      unsigned long long kv[4];
+  const int64_t nt = T.total(S, gstatus);
+  int cur = -1;
+  WsHeader* h = nullptr;
+  float ox = 0.0f, oy = 0.0f;
+  bool on = false;
+  int64_t m = 0;
+  const unsigned long long* keys = nullptr;
+  auto flush = [&]() {
+    __syncthreads();
+    if (cur >= 0)
+      for (int k = threadIdx.x; k < REFINE_BINS; k += RBLOCK)
+        if (s_bin[k]) atomicMax(&h->rbin[k], s_bin[k]);
+    __syncthreads();
+  };
+  for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int s = T.set_of(t);
+    if (s != cur) {
+      flush();
+      for (int k = threadIdx.x; k < REFINE_BINS; k += RBLOCK) s_bin[k] = 0;
+      cur = s;
+      h = S.h(s);
+      ox = (float)h->poly.rox;
+      oy = (float)h->poly.roy;
+      on = h->poly.refine_on;
+      m = count_of(h, &h->n_surv);
+      keys = keys_base + S.off_at(s);
+      __syncthreads();
+    }
+    if (!on) continue;
+    const int64_t j0 = (t - T.first(s)) * RT + threadIdx.x;
+    unsigned long long kv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) kv[u] = j0 + u * stride < m ? keys[j0 + u * stride] : 0ull;
+    for (int u = 0; u < 4; ++u) kv[u] = j0 + u * RBLOCK < m ? keys[j0 + u * RBLOCK] : 0ull;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t j = j0 + u * stride;
-        if (j < m) {
-          const float qx = (float)key_x(kv[u]) - ox, qy = (float)key_y(kv[u]) - oy;
-          const float r2 = fmaf(qx, qx, qy * qy);
-          const unsigned long long packed = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)j;
-          atomicMax(&s_bin[bin_of(qx, qy)], packed);
-        }
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = j0 + u * RBLOCK;
+      if (j < m) {
+        const float qx = (float)key_x(kv[u]) - ox, qy = (float)key_y(kv[u]) - oy;
+        const float r2 = fmaf(qx, qx, qy * qy);
+        const unsigned long long packed = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)j;
+        atomicMax(&s_bin[bin_of(qx, qy)], packed);
       }
     }
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < REFINE_BINS; k += RBLOCK)
-    if (s_bin[k]) atomicMax(&h->rbin[k], s_bin[k]);
+  flush();
 }
 
 // For every bin: its winner W (if any) and the nearest winners L before and R
-// after it (cyclically), as coordinates.
-__global__ void __launch_bounds__(REFINE_BINS) k_refine_links(const unsigned long long* __restrict__ keys,
-                                                               WsHeader* h, int4* __restrict__ tri) {
+// after it (cyclically), as coordinates.  One block per set.
+__global__ void __launch_bounds__(REFINE_BINS) k_refine_links(Sets S, const uint32_t* gstatus,
+                                                               const unsigned long long* __restrict__ keys_base,
+                                                               int4* __restrict__ tri_base) {
   __shared__ int s_x[REFINE_BINS], s_y[REFINE_BINS], s_has[REFINE_BINS];
+  const int set = blockIdx.x;
+  WsHeader* h = S.h(set);
+  const unsigned long long* keys = keys_base + S.off_at(set);
+  int4* tri = tri_base + (size_t)set * 2 * REFINE_BINS;
+  const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0;
   const int b = threadIdx.x;
-  const unsigned long long w = h->rbin[b];
+  const unsigned long long w = dead ? 0ull : h->rbin[b];
   const bool has = w != 0;
   s_has[b] = has;
   if (has) {
@@ -92,7 +144,7 @@ __global__ void __launch_bounds__(REFINE_BINS) k_refine_links(const unsigned lon
   const int nw = __syncthreads_count(has);
   int4 a = make_int4(0, 0, 0, 0), c = make_int4(0, 0, 0, 0);
   int flags = 0;
-  if (h->poly.refine_on && nw >= 2 && l >= 0 && r >= 0) {
+  if (!dead && h->poly.refine_on && nw >= 2 && l >= 0 && r >= 0) {
     flags = 1 | (has ? 2 : 0);
     a = make_int4(s_x[l], s_y[l], has ? s_x[b] : 0, has ? s_y[b] : 0);
     c = make_int4(s_x[r], s_y[r], flags, 0);
@@ -107,24 +159,46 @@ __device__ __forceinline__ long long orient_ll(long long ax, long long ay, long 
 }
 
 // Pass 2: keep the survivors not strictly inside their bin's triangles;
-// compacted to (kout, vout), count in h->n_surv2.  Few survive, so each warp
-// appends its survivors with one atomic (no block barrier).
-__global__ void __launch_bounds__(RBLOCK) k_refine_filter(const unsigned long long* __restrict__ kin,
-                                                           const uint32_t* __restrict__ vin,
-                                                           unsigned long long* __restrict__ kout,
-                                                           uint32_t* __restrict__ vout, WsHeader* h,
-                                                           const int4* __restrict__ tri) {
+// compacted to the set's (kout, vout) region, count in its n_surv2.  Few
+// survive, so each warp appends its survivors with one atomic.
+__global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const uint32_t* gstatus,
+                                                           const unsigned long long* __restrict__ kin_base,
+                                                           const uint32_t* __restrict__ vin_base,
+                                                           unsigned long long* __restrict__ kout_base,
+                                                           uint32_t* __restrict__ vout_base,
+                                                           const int4* __restrict__ tri_base) {
   __shared__ int4 s_tri[2 * REFINE_BINS];
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int k = tid; k < 2 * REFINE_BINS; k += RBLOCK) s_tri[k] = tri[k];
-  __syncthreads();
-  const int64_t m = count_of(h, &h->n_surv);
-  const long long ox = h->poly.rox, oy = h->poly.roy;
-  const float oxf = (float)ox, oyf = (float)oy;
-  const int64_t stride = (int64_t)gridDim.x * RBLOCK;
-  // 4 independent loads in flight per thread; a warp handles 4 x 32
-  // consecutive survivors per round
-  for (int64_t j0 = (int64_t)blockIdx.x * RBLOCK * 4; j0 < m; j0 += 4 * stride) {
+  const int64_t nt = T.total(S, gstatus);
+  int cur = -1;
+  WsHeader* h = nullptr;
+  long long ox = 0, oy = 0;
+  float oxf = 0.0f, oyf = 0.0f;
+  int64_t m = 0;
+  const unsigned long long* kin = nullptr;
+  const uint32_t* vin = nullptr;
+  unsigned long long* kout = nullptr;
+  uint32_t* vout = nullptr;
+  for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int s = T.set_of(t);
+    if (s != cur) {
+      __syncthreads();
+      cur = s;
+      const int4* tri = tri_base + (size_t)s * 2 * REFINE_BINS;
+      for (int k = tid; k < 2 * REFINE_BINS; k += RBLOCK) s_tri[k] = tri[k];
+      h = S.h(s);
+      ox = h->poly.rox;
+      oy = h->poly.roy;
+      oxf = (float)ox;
+      oyf = (float)oy;
+      m = count_of(h, &h->n_surv);
+      const int64_t o = S.off_at(s);
+      kin = kin_base + o; vin = vin_base + o; kout = kout_base + o; vout = vout_base + o;
+      __syncthreads();
+    }
+    // 4 independent loads in flight per thread; a warp handles 4 x 32
+    // consecutive survivors
+    const int64_t j0 = (t - T.first(s)) * RT;
     unsigned long long kv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -170,17 +244,64 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(const unsigned long lo
   }
 }
 
+// Tile prefix over the sets' survivor counts (one block).
+__global__ void __launch_bounds__(1024) k_tile_prefix(Sets S, const uint32_t* gstatus, int which, int rt,
+                                                       int64_t* tp) {
+  __shared__ int64_t s_w[32];
+  __shared__ int64_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int s0 = 0; s0 < S.S; s0 += 1024) {
+    const int s = s0 + threadIdx.x;
+    int64_t v = 0;
+    if (s < S.S && !dead) {
+      const WsHeader* h = S.h(s);
+      const int64_t m = count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
+      v = (m + rt - 1) / rt;
+    }
+    int64_t incl = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int64_t u = __shfl_up_sync(FULL, incl, off);
+      if (lane >= off) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    int64_t wpre = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+      const int64_t x = s_w[w];
+      if (w < warp) wpre += x;
+      tot += x;
+    }
+    const int64_t carry = s_carry;
+    if (s < S.S) tp[s] = carry + wpre + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tp[S.S] = s_carry;
+}
+
 }  // namespace
 
-cudaError_t launch_refine(WsHeader* h, const unsigned long long* keys_in, const uint32_t* vals_in,
-                          unsigned long long* keys_out, uint32_t* vals_out, int4* tri, int64_t cap,
-                          cudaStream_t st) {
+cudaError_t launch_refine(const Sets& S, const uint32_t* gstatus, int64_t* tp, const unsigned long long* keys_in,
+                          const uint32_t* vals_in, unsigned long long* keys_out, uint32_t* vals_out, int4* tri,
+                          int64_t cap, cudaStream_t st) {
   const int sms = device_sm_count();
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + RBLOCK - 1) / RBLOCK, (int64_t)sms * 8));
-  k_refine_bins<<<g, RBLOCK, 0, st>>>(keys_in, h);
-  k_refine_links<<<1, REFINE_BINS, 0, st>>>(keys_in, h, tri);
-  k_refine_filter<<<g, RBLOCK, 0, st>>>(keys_in, vals_in, keys_out, vals_out, h, tri);
-  count_launches(3);
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + RT - 1) / RT, (int64_t)sms * 8));
+  Tiles T;
+  T.S = S.S;
+  T.tp = S.S > 1 ? tp : nullptr;
+  int k = 3;
+  if (T.tp) {
+    k_tile_prefix<<<1, 1024, 0, st>>>(S, gstatus, 0, RT, tp);
+    ++k;
+  }
+  k_refine_bins<<<g, RBLOCK, 0, st>>>(S, T, gstatus, keys_in);
+  k_refine_links<<<(unsigned)S.S, REFINE_BINS, 0, st>>>(S, gstatus, keys_in, tri);
+  k_refine_filter<<<g, RBLOCK, 0, st>>>(S, T, gstatus, keys_in, vals_in, keys_out, vals_out, tri);
+  count_launches(k);
   return cudaGetLastError();
 }
 

@@ -54,17 +54,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 }
 
 // Bounded wait for the phase with the given parity; false (and the timeout
-// bit set) when it does not complete within WAIT_LIMIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, WsHeader* h) {
+// bit set in *status) when it does not complete within WAIT_LIMIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait_status(unsigned long long* bar, unsigned parity, uint32_t* status) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
-      atomicOr(&h->status, HULL_DEVICE_TIMEOUT);
+      atomicOr(status, HULL_DEVICE_TIMEOUT);
       return false;
     }
   }
   return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, WsHeader* h) {
+  return mbar_wait_status(bar, parity, &h->status);
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
@@ -99,6 +103,80 @@ struct StreamRange {
     return (int)min((int64_t)CHUNK, p1 - f);
   }
 };
+
+// The segments of a block's share [v0, v1) of the virtual pair axis, one
+// per set it meets, in order (or in reverse): f(s, first local pair, pairs).
+// Producer and consumers walk the same sequence; each splits a segment into
+// chunks of CHUNK pairs anchored at the segment's first pair (chunk k of
+// nchunks(n), visited first-to-last or last-to-first).
+template <class F>
+__device__ __forceinline__ void walk_segments(const Sets& S, int64_t v0, int64_t v1, bool reverse, F&& f) {
+  if (v0 >= v1) return;
+  if (!reverse) {
+    int s = S.set_of_pair(v0);
+    int64_t p = v0;
+    for (;;) {
+      const int64_t a = S.pp_at(s);
+      const int64_t hi = min(v1, S.pp_at(s + 1));
+      f(s, p - a, (int)(hi - p));
+      p = hi;
+      if (p >= v1) break;
+      ++s;
+      while (S.pp_at(s + 1) <= p) ++s;  // skip sets without pairs
+    }
+  } else {
+    int s = S.set_of_pair(v1 - 1);
+    int64_t p = v1;
+    for (;;) {
+      const int64_t a = S.pp_at(s);
+      const int64_t lo = max(v0, a);
+      f(s, lo - a, (int)(p - lo));
+      p = lo;
+      if (p <= v0) break;
+      --s;
+      while (s > 0 && S.pp_at(s) >= p) --s;  // the set holding pair p - 1
+    }
+  }
+}
+
+__device__ __forceinline__ int nchunks(int n) { return (n + CHUNK - 1) / CHUNK; }
+// First pair (relative to the segment) and pair count of visit k.
+__device__ __forceinline__ int chunk_first(int k, int nck, bool reverse) {
+  return (reverse ? nck - 1 - k : k) * CHUNK;
+}
+
+// Named barrier of the consumer warps only (the producer warp runs ahead).
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(CONSUMERS) : "memory");
+}
+
+// Producer (lane 0 of the producer warp) over a walk of segments: every
+// chunk into the next stage, waiting for a free stage each time; then it
+// waits until the copies it issued have landed.
+template <class SS>
+__device__ __forceinline__ void stream_produce_sets(SS& SM, const Sets& S, int64_t v0, int64_t v1, bool reverse,
+                                                    uint32_t* status) {
+  constexpr int STAGES = SS::STAGES;
+  if ((threadIdx.x & 31) != 0) return;
+  int c = 0;
+  bool stop = false;
+  walk_segments(S, v0, v1, reverse, [&](int s, int64_t lo, int n) {
+    const float4* P = reinterpret_cast<const float4*>(S.xy_of(s) + 2 * S.head_of(s)) + lo;
+    const int nck = nchunks(n);
+    for (int k = 0; k < nck && !stop; ++k, ++c) {
+      const int st = c % STAGES;
+      const int ph = c / STAGES;
+      if (ph > 0 && !mbar_wait_status(&SM.empty[st], (unsigned)((ph - 1) & 1), status)) { stop = true; break; }
+      if (*reinterpret_cast<volatile uint32_t*>(status) & HULL_DEVICE_TIMEOUT) { stop = true; break; }
+      const int f = chunk_first(k, nck, reverse);
+      const unsigned bytes = (unsigned)min(CHUNK, n - f) * 16u;
+      mbar_arrive_tx(&SM.full[st], bytes);
+      bulk_g2s(&SM.stage[st][0], P + f, bytes, &SM.full[st]);
+    }
+  });
+  for (int d = c > STAGES ? c - STAGES : 0; d < c; ++d)
+    mbar_wait_status(&SM.full[d % STAGES], (unsigned)((d / STAGES) & 1), status);
+}
 
 template <class SS>
 __device__ __forceinline__ void stream_init(SS& S) {

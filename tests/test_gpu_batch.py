@@ -1,0 +1,118 @@
+"""Parity of hull_batch (through the C ABI) with the CPU oracle, set by set.
+
+Every set's hull (global indices, CCW from the lexicographic minimum) must
+equal the oracle's hull of that set alone, shifted by the set's offset.  The
+batches mix the three input shapes, empty and tiny sets, sets starting at
+odd rows (8-byte but not 16-byte aligned), sizes that span several blocks
+of the streaming passes, and a set whose survivors exceed the one-block
+hull's capacity (the cooperative large path).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def convex_ring(k, r=float(1 << 23)):
+    a = np.arange(k) * (2 * np.pi / k)
+    return np.stack([np.round(r * np.cos(a)), np.round(r * np.sin(a))], 1).astype(np.float32)
+
+
+def make_batch(sizes, seed, extra=None):
+    sets = []
+    for k, n in enumerate(sizes):
+        sets.append(synth.shape(k % 3, n, seed + k, 0))
+    if extra is not None:
+        sets.extend(extra)
+    offsets = np.zeros(len(sets) + 1, np.int64)
+    offsets[1:] = np.cumsum([len(s) for s in sets])
+    xy = np.concatenate(sets).astype(np.float32) if offsets[-1] else np.zeros((0, 2), np.float32)
+    return sets, offsets, xy
+
+
+def run_batch(cp, xy, offsets, opt):
+    import torch
+    d = torch.from_numpy(np.ascontiguousarray(xy)).cuda() if len(xy) else torch.zeros((0, 2), device="cuda")
+    o = torch.from_numpy(offsets).cuda()
+    out, hoff, ws = cp.batch(d, o, opt)
+    torch.cuda.synchronize()
+    hoff = hoff.cpu().numpy()
+    out = out.cpu().numpy()
+    return out, hoff, ws
+
+
+def check(cp, sets, offsets, xy, opt):
+    out, hoff, ws = run_batch(cp, xy, offsets, opt)
+    assert cp.device_status(ws) == (0, 0)
+    assert hoff[0] == 0
+    for s, pts in enumerate(sets):
+        got = out[hoff[s]:hoff[s + 1]]
+        want = oracle.cudapre(pts)["hull"].astype(np.int64) + offsets[s] if len(pts) else np.zeros(0, np.int64)
+        assert got.tolist() == want.tolist(), f"set {s} (n={len(pts)})"
+
+
+SIZES = [0, 1, 2, 3, 5, 17, 100, 1000, 4097, 50_001, 0, 300_000, 2, 123_457, 7]
+
+
+@pytest.mark.parametrize("angles,filt,refine", [(0, 1, 1), (0, 0, 1), (1, 1, 1), (0, 1, 0), (1, 0, 0)])
+def test_batch_mixed_sets(gpu_lib, angles, filt, refine):
+    sets, offsets, xy = make_batch(SIZES, 9100)
+    check(gpu_lib, sets, offsets, xy, gpu_lib.Options(angles=angles, filter=filt, refine=bool(refine)))
+
+
+def test_batch_large_path_set(gpu_lib):
+    # a set of 20,000 points in convex position plus a disk: more survivors
+    # than the one-block hull takes, between ordinary sets
+    ring = np.concatenate([synth.disk(3000, 5, 1 << 20), convex_ring(20_000)]).astype(np.float32)
+    sets, offsets, xy = make_batch([1000, 33, 70_000], 9200, extra=[ring, synth.square(999, 9201)])
+    check(gpu_lib, sets, offsets, xy, gpu_lib.Options())
+    check(gpu_lib, sets, offsets, xy, gpu_lib.Options(refine=False))
+
+
+def test_batch_many_small_sets(gpu_lib):
+    rng = np.random.default_rng(9300)
+    sizes = [int(v) for v in np.floor(np.exp(rng.uniform(np.log(1), np.log(3e4), 600)))]
+    sets, offsets, xy = make_batch(sizes, 9300)
+    check(gpu_lib, sets, offsets, xy, gpu_lib.Options())
+
+
+def test_batch_plan_sample(gpu_lib):
+    # the batch workload's own generator (log-uniform sizes, shape per set),
+    # on 48 sets with sizes from 1e3 to 2e5
+    S = 48
+    xy, offsets, _ = synth.batch(S, 9400, 1e3, 2e5)
+    sets = [xy[offsets[s]:offsets[s + 1]] for s in range(S)]
+    check(gpu_lib, sets, np.asarray(offsets, np.int64), xy, gpu_lib.Options())
+
+
+def test_batch_single_set_equals_hull_compute(gpu_lib):
+    import torch
+    cp = gpu_lib
+    pts = synth.disk(1 << 20, 9500)
+    out, hoff, _ = run_batch(cp, pts, np.array([0, len(pts)], np.int64), cp.Options())
+    d = torch.from_numpy(pts).cuda()
+    h, c, _ = cp.compute(d)
+    torch.cuda.synchronize()
+    assert out[hoff[0]:hoff[1]].tolist() == cp.as_index(h, int(c.item())).tolist()
+
+
+def test_batch_empty_and_zero_sets(gpu_lib):
+    cp = gpu_lib
+    sets, offsets, xy = make_batch([0, 0, 0], 9600)
+    out, hoff, ws = run_batch(cp, xy, offsets, cp.Options())
+    assert hoff.tolist() == [0, 0, 0, 0]
+    out, hoff, ws = run_batch(cp, np.zeros((0, 2), np.float32), np.array([0], np.int64), cp.Options())
+    assert hoff.tolist() == [0]
+
+
+def test_batch_bad_offsets_flagged(gpu_lib):
+    cp = gpu_lib
+    sets, offsets, xy = make_batch([100, 200, 300], 9700)
+    bad = offsets.copy()
+    bad[1], bad[2] = bad[2], bad[1]  # decreasing
+    out, hoff, ws = run_batch(cp, xy, bad, cp.Options())
+    assert cp.device_status(ws)[1] & cp.HULL_DEVICE_OFFSETS
+    assert hoff.tolist() == [0, 0, 0, 0]
