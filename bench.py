@@ -315,6 +315,44 @@ def run_ours(args):
     e2e = {"value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": d2h // e2e_steps}
 
+    # Batched workload: many independent sets in one hull_batch call.
+    batch = None
+    if args.batch_sets > 0:
+        del ws, out
+        torch.cuda.empty_cache()
+        bxy, boff, _ = synth.batch(args.batch_sets, SEED + 17 + rank)
+        nb = int(boff[-1])
+        db = torch.from_numpy(bxy).cuda()
+        do = torch.from_numpy(boff).cuda()
+        del bxy
+        bws_bytes = cp.hull_batch_workspace_bytes(nb, args.batch_sets)
+        bws = cp.workspace(bws_bytes)
+        bout = torch.empty(nb, dtype=torch.int64, device="cuda")
+        bhoff = torch.empty(args.batch_sets + 1, dtype=torch.int64, device="cuda")
+
+        def batch_step(opt):
+            code = cp.hull_batch(db.data_ptr(), do.data_ptr(), args.batch_sets, nb, bws.data_ptr(), bws_bytes,
+                                 bout.data_ptr(), bhoff.data_ptr(), opt, sh)
+            if code:
+                raise cp.HullError(code, "hull_batch")
+
+        for _ in range(2):
+            batch_step(fp32)
+        btimer = cp.StageTimer(max_calls=args.batch_steps)
+        ms_b = timed(batch_step, fp32, args.batch_steps, btimer)
+        bst, bcalls = btimer.read()
+        btimer.close()
+        code, bits = cp.device_status(bws)
+        batch = {"value": world * nb / (ms_b * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_b,
+                 "sets": args.batch_sets, "points": nb, "bytes": nb * 8,
+                 "hbm_GBps_two_reads": 16.0 * nb / (ms_b * 1e-3) / 1e9,
+                 "stages_ms": {k: v / max(bcalls, 1) for k, v in bst.items()},
+                 "hull_vertices": int(bhoff[-1].item()), "device_status": bits,
+                 "workload": "%d sets, sizes floor(exp(U(ln 1e3, ln 4e6))), shape per set from square "
+                             "(r 2^24), disk (r 2^24), Gaussian (sigma 2^22)" % args.batch_sets}
+        del db, do, bws, bout, bhoff
+        torch.cuda.empty_cache()
+
     cpu = None
     if world == 1 and rank == 0 and not args.no_cpu:
         ns = 1 << 25
@@ -332,7 +370,8 @@ def run_ours(args):
                        "parallelism": "independent set per GPU" if world > 1 else "single GPU"},
             "variants": {"plain_exact": {"value": world * n / (ms_exact * 1e-3) / 1e9, "ms_per_step": ms_exact},
                          "fp32_filtered": {"value": value, "ms_per_step": ms},
-                         "prefilter_only": prefilter},
+                         "prefilter_only": prefilter,
+                         "batch": batch},
             "stages_ms_per_step": stages_out,
             "survivors": n_surv, "escalations": n_esc, "refined_survivors": n_ref, "hull_vertices": n_hull,
             "roofline": roofline,
@@ -356,6 +395,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--batch-sets", type=int, default=4096, help="sets of the batched leg (0: skip it)")
+    ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

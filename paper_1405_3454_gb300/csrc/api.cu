@@ -122,6 +122,7 @@ BatchLayout batch_layout(int64_t n_total, int32_t S) {
 struct BatchWords {
   uint32_t status;
   uint32_t bar_count, bar_gen;
+  int njobs;  // sets that take the large-set hull path
 };
 
 hull_status check_opts(const hull_options* o) {
@@ -303,7 +304,7 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   J.out_idx = d_hull_idx;
   J.out_n = d_n_hull;
   J.cap = cap;
-  HULL_TRY(launch_large(nullptr, 1, J, &h->bar_count, &h->status, st));
+  HULL_TRY(launch_large(nullptr, nullptr, J, &h->bar_count, &h->status, st));
   mark(4, st);
   mark(5, st);
   return HULL_OK;
@@ -375,10 +376,10 @@ hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, i
   HULL_TRY(launch_small_hull(SS, bstatus, which, kin, vin, reinterpret_cast<SmallWs*>(ws + L.small), hstage, hcnt,
                              st));
   LargeJob* jobs = reinterpret_cast<LargeJob*>(ws + L.jobs);
-  HULL_TRY(launch_batch_jobs(SS, which, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt),
-                             reinterpret_cast<uint32_t*>(ws + L.cnt), hstage, hcnt, jobs, st));
+  HULL_TRY(launch_batch_jobs(SS, bstatus, which, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt),
+                             reinterpret_cast<uint32_t*>(ws + L.cnt), hstage, hcnt, jobs, &bw->njobs, st));
   LargeJob none{};
-  HULL_TRY(launch_large(jobs, S, none, &bw->bar_count, bstatus, st));
+  HULL_TRY(launch_large(jobs, &bw->njobs, none, &bw->bar_count, bstatus, st));
   mark(4, st);
   HULL_TRY(launch_batch_emit(SS, bstatus, hcnt, hstage, d_hull_offsets, d_hull_idx, st));
   mark(5, st);

@@ -61,6 +61,7 @@ struct Edge {
 // of the edges that some point of the cell may fail; 0 = every point of the
 // cell is strictly inside (discard without a test).
 constexpr int GRID_LOG = 7;
+constexpr int64_t GRID_MIN_POINTS = 1 << 16;  // smaller sets use one cell listing every edge
 constexpr int GRID = 1 << GRID_LOG;
 // Cell storage in the workspace: GRID*GRID uint16 edge masks, then GRID*GRID
 // byte codes (0: inside, k + 1: only edge k, CELL_MULTI: see the mask).
@@ -214,15 +215,16 @@ struct LargeJob {
   int64_t* out_n;
   int64_t cap;
 };
-// One cooperative launch over `table[0..njobs)` (or `single` when table is
-// null); bar = two zeroed words for the grid barrier, bar_status = where a
-// barrier timeout is recorded.
-cudaError_t launch_large(const LargeJob* table, int njobs, const LargeJob& single, uint32_t* bar,
+// One cooperative launch over `table[0 .. *njobs)` (njobs in device memory),
+// or over `single` when table is null; bar = two zeroed words for the grid
+// barrier, bar_status = where a barrier timeout is recorded.
+cudaError_t launch_large(const LargeJob* table, const int* njobs, const LargeJob& single, uint32_t* bar,
                          uint32_t* bar_status, cudaStream_t st);
 cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st);
 
 constexpr int REFINE_BINS = 1024;         // angular bins of the refinement round
 constexpr int SMALL_MAX = 8192;           // survivor sets up to this size: one-block hull
+constexpr int TINY_MAX = 1024;            // ... up to this size: one short kernel
 
 // The refinement round for every set; tp = S+1 work-tile prefix (batch).
 cudaError_t launch_refine(const Sets& S, const uint32_t* gstatus, int64_t* tp, const unsigned long long* keys_in,
@@ -265,9 +267,9 @@ int chain_levels(int64_t cap);
 
 // Batch-only steps (k_batch.cu).
 cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, uint32_t* bstatus, int64_t* pp, cudaStream_t st);
-cudaError_t launch_batch_jobs(const Sets& S, int which, unsigned long long* ka, uint32_t* va, unsigned long long* kb,
-                              uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out, int64_t* out_n,
-                              LargeJob* jobs, cudaStream_t st);
+cudaError_t launch_batch_jobs(const Sets& S, const uint32_t* bstatus, int which, unsigned long long* ka, uint32_t* va,
+                              unsigned long long* kb, uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out,
+                              int64_t* out_n, LargeJob* jobs, int* njobs, cudaStream_t st);
 cudaError_t launch_batch_emit(const Sets& S, uint32_t* bstatus, const int64_t* hcnt, const uint32_t* hstage,
                               int64_t* hull_offsets, int64_t* hull_idx, cudaStream_t st);
 

@@ -69,14 +69,18 @@ __global__ void __launch_bounds__(TB) k_batch_setup(Sets S, int64_t n_total, uin
   if (threadIdx.x == 0) pp[S.S] = total;
 }
 
-// Large-path job of every set: its survivors after the refinement round
-// (which = 1) or after Step 3 (which = 0).
-__global__ void k_batch_jobs(Sets S, int which, unsigned long long* ka, uint32_t* va, unsigned long long* kb,
-                             uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out, int64_t* out_n,
-                             LargeJob* jobs) {
+// Large-path jobs: the sets whose survivors after the refinement round
+// (which = 1) or after Step 3 (which = 0) exceed the one-block hull, listed
+// in jobs[0 .. *njobs) in any order.
+__global__ void k_batch_jobs(Sets S, const uint32_t* bstatus, int which, unsigned long long* ka, uint32_t* va,
+                             unsigned long long* kb, uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out,
+                             int64_t* out_n, LargeJob* jobs, int* njobs) {
+  if (*reinterpret_cast<const volatile uint32_t*>(bstatus)) return;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.S; s += gridDim.x * blockDim.x) {
     const int64_t o = S.off_at(s);
     WsHeader* h = S.h(s);
+    if (h->status) continue;
+    if ((which == 0 ? h->n_surv : h->n_surv2) <= (unsigned long long)SMALL_MAX) continue;
     LargeJob J;
     J.h = h;
     J.count = which == 0 ? &h->n_surv : &h->n_surv2;
@@ -86,7 +90,7 @@ __global__ void k_batch_jobs(Sets S, int which, unsigned long long* ka, uint32_t
     J.out_idx = out + o;
     J.out_n = out_n + s;
     J.cap = S.n_of(s) > 0 ? S.n_of(s) : 1;
-    jobs[s] = J;
+    jobs[atomicAdd(njobs, 1)] = J;
   }
 }
 
@@ -125,11 +129,11 @@ cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, uint32_t* bstatus
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_jobs(const Sets& S, int which, unsigned long long* ka, uint32_t* va, unsigned long long* kb,
-                              uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out, int64_t* out_n,
-                              LargeJob* jobs, cudaStream_t st) {
+cudaError_t launch_batch_jobs(const Sets& S, const uint32_t* bstatus, int which, unsigned long long* ka, uint32_t* va,
+                              unsigned long long* kb, uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out,
+                              int64_t* out_n, LargeJob* jobs, int* njobs, cudaStream_t st) {
   const unsigned g = (unsigned)std::min<int64_t>(((int64_t)S.S + 255) / 256, 1024);
-  k_batch_jobs<<<g, 256, 0, st>>>(S, which, ka, va, kb, vb, tilecnt, cnt, out, out_n, jobs);
+  k_batch_jobs<<<g, 256, 0, st>>>(S, bstatus, which, ka, va, kb, vb, tilecnt, cnt, out, out_n, jobs, njobs);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -172,7 +172,7 @@ __device__ __forceinline__ float4 lds_vol4(const float* p) {
 // Step 2: the convex polygon of the extremes (Andrew's monotone chain, one
 // warp), plus the per-edge records and the inner box used by Step 3.
 
-__device__ void build_edges_and_box(Poly* P, int m, int lane) {
+__device__ void build_edges_and_box(Poly* P, int m, int lane, bool grid_on) {
   if (lane < m) {
     const int j = (lane + 1) % m;
     const long long ax = P->vx[lane], ay = P->vy[lane];
@@ -300,11 +300,17 @@ __device__ void build_edges_and_box(Poly* P, int m, int lane) {
     P->ky = ky;
     P->gx0 = origin(xl, kx);
     P->gy0 = origin(yl, ky);
+    if (!grid_on) {
+      // no grid: every point of the domain falls in cell (0, 0), whose
+      // entry lists every edge
+      P->kx = P->ky = 30;
+      P->gx0 = P->gy0 = -(1 << 25);
+    }
   }
 }
 
 // ext: 16 extreme indices (NONE = absent) in shared memory; warp-wide.
-__device__ void hull16_warp(const float* xy, const uint32_t* ext, Poly* P) {
+__device__ void hull16_warp(const float* xy, const uint32_t* ext, Poly* P, bool grid_on) {
   __shared__ int s_x[NSLOT], s_y[NSLOT];
   __shared__ uint32_t s_i[NSLOT];
   __shared__ int s_hx[NSLOT + 1], s_hy[NSLOT + 1];
@@ -370,7 +376,7 @@ __device__ void hull16_warp(const float* xy, const uint32_t* ext, Poly* P) {
   }
   if (lane == 0) P->m = m;
   __syncwarp();
-  build_edges_and_box(P, m, lane);
+  build_edges_and_box(P, m, lane, grid_on);
 }
 
 // ----------------------------------------------------------------------------
@@ -669,13 +675,12 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(Sets S, int64_t ppb, const
 // 16 extremes, Step 2 (the polygon, its edge records and inner box) and the
 // cell grid of the inside test.
 
-constexpr int FIN_THREADS = 1024;
-
-template <int ANG>
-__global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(Sets S, int64_t ppb, const uint32_t* gstatus,
+template <int ANG, int FIN_THREADS>
+__global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb, const uint32_t* gstatus,
                                                                const BlockBest* bres, uint32_t* ext_out,
                                                                uint16_t* cells_base, uint32_t* surv_idx,
                                                                unsigned long long* surv_key) {
+  static_assert(FIN_THREADS % 32 == 0 && FIN_THREADS <= 1024, "one reduction entry per warp");
   constexpr int ND = Dirs<ANG>::ND;
   __shared__ uint32_t s_ext[NSLOT];
   __shared__ unsigned long long s_k[FIN_THREADS / 32][ND];
@@ -746,7 +751,10 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(Sets S, int64_t p
   if (warp == 0) {
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      ks[d] = s_k[lane][d]; bi[d] = s_i[lane][d];
+      // one entry per warp of the block (FIN_THREADS / 32 <= 32)
+      const bool have = lane < FIN_THREADS / 32;
+      ks[d] = have ? s_k[have ? lane : 0][d] : 0ull;
+      bi[d] = have ? s_i[have ? lane : 0][d] : NONE;
       butterfly(d);
       if (lane == 0) s_ext[d] = bi[d];
     }
@@ -764,9 +772,12 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(Sets S, int64_t p
     if (dead) for (int k = 0; k < NSLOT; ++k) s_ext[k] = NONE;
   }
   __syncthreads();
+  // Sets below GRID_MIN_POINTS get no cell grid (its construction would cost
+  // more than the cell lookups save).
+  const bool grid_on = n >= GRID_MIN_POINTS;
   if (warp == 0) {
     if (ext_out && lane < NSLOT) ext_out[(size_t)set * NSLOT + lane] = s_ext[lane];
-    hull16_warp(xy, s_ext, &h->poly);
+    hull16_warp(xy, s_ext, &h->poly, grid_on);
   }
   __syncthreads();
   // The loose points' inside test (Step 3): exact against every edge.
@@ -798,6 +809,13 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_ext_finish(Sets S, int64_t p
   const Poly& P = h->poly;
   const int m = P.m;
   if (dead || m < 3) return;
+  if (!grid_on) {
+    if (tid == 0) {
+      cells[0] = (uint16_t)((1u << m) - 1u);
+      reinterpret_cast<uint8_t*>(cells + GRID * GRID)[0] = (uint8_t)CELL_MULTI;
+    }
+    return;
+  }
   for (int t = tid; t < m * GRID; t += FIN_THREADS) {
     const int k = t / GRID, c = t % GRID;
     const Edge& e = P.e[k];
@@ -873,6 +891,17 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
     G = std::max<int64_t>(1, (npairs + ppb - 1) / ppb);
     return std::make_pair(G, ppb);
   };
+  // The finishing kernel: one block per set, 1024 threads for a single set
+  // (its cell grid in one pass), 256 for a batch (more sets resident).
+#define FIN(A)                                                                                           \
+  do {                                                                                                   \
+    if (S.S == 1)                                                                                        \
+      k_ext_finish<A, 1024><<<nsets, 1024, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, \
+                                                    surv_key);                                           \
+    else                                                                                                 \
+      k_ext_finish<A, 256><<<nsets, 256, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx,   \
+                                                  surv_key);                                             \
+  } while (0)
   if (filter == HULL_FILTER_FP32) {
     const size_t dsmem = sizeof(StreamSmemT<3>);
     static bool attr[64][2] = {};
@@ -893,22 +922,23 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
     const auto gp = shape(occ);
     if (angles == HULL_ANGLES_CUMULATIVE) {
       k_extremes32<0><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
-      k_ext_finish<0><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
+      FIN(0);
     } else {
       k_extremes32<1><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
-      k_ext_finish<1><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
+      FIN(1);
     }
   } else {
     const int occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes64<0>) : occupancy(k_extremes64<1>);
     const auto gp = shape(occ);
     if (angles == HULL_ANGLES_CUMULATIVE) {
       k_extremes64<0><<<(unsigned)gp.first, BLOCK, 0, st>>>(S, gp.second, gstatus, bres);
-      k_ext_finish<0><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
+      FIN(0);
     } else {
       k_extremes64<1><<<(unsigned)gp.first, BLOCK, 0, st>>>(S, gp.second, gstatus, bres);
-      k_ext_finish<1><<<nsets, FIN_THREADS, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, surv_key);
+      FIN(1);
     }
   }
+#undef FIN
   count_launches(2);
   return cudaGetLastError();
 }

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
   SmallWs* sw = sw_base + set;
   const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0;
   const int64_t m64 = dead ? 0 : count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
-  if (m64 > SMALL_MAX || m64 == 0) {  // the large path, or nothing to do
+  if (m64 > SMALL_MAX || m64 <= TINY_MAX) {  // the large path, the tiny kernel, or nothing to do
     if (tid == 0) {
       sw->active = 0;
       if (m64 == 0) *out_n = 0;
@@ -211,6 +211,93 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
   }
   if (tid == 0) { sw->u = u; sw->C = C; sw->active = 1; }
   STAMP(5);
+}
+
+// tiny: the whole hull of a set with at most TINY_MAX survivors in one
+// block: bitonic sort of (key, index) in shared memory, then the lower and
+// the upper monotone chain by one thread each (equal keys are adjacent and
+// the lowest index comes first, so later copies are skipped), then the
+// emission.
+constexpr int TB = 256;
+
+__global__ void __launch_bounds__(TB) k_small_tiny(Sets S, const uint32_t* gstatus, int which,
+                                                    const unsigned long long* __restrict__ kin_base,
+                                                    const uint32_t* __restrict__ vin_base,
+                                                    uint32_t* __restrict__ out_base, int64_t* out_n_base) {
+  __shared__ unsigned long long sk[TINY_MAX];
+  __shared__ uint32_t si[TINY_MAX];
+  __shared__ uint16_t st[2][TINY_MAX];
+  __shared__ unsigned long long stk[2][TINY_MAX];
+  __shared__ int s_n[2];
+  const int tid = threadIdx.x;
+  const int set = blockIdx.x;
+  const WsHeader* h = S.h(set);
+  if (*reinterpret_cast<const volatile uint32_t*>(gstatus)) return;
+  const int64_t m64 = count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
+  if (m64 == 0 || m64 > TINY_MAX) return;
+  const int m = (int)m64;
+  const int64_t o = S.off_at(set);
+  int P2 = 2;
+  while (P2 < m) P2 <<= 1;
+  for (int i = tid; i < P2; i += TB) {
+    sk[i] = i < m ? kin_base[o + i] : ~0ull;
+    si[i] = i < m ? vin_base[o + i] : ~0u;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < P2; i += TB) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long a = sk[i], b = sk[l];
+          const uint32_t ai = si[i], bi = si[l];
+          const bool gt = a > b || (a == b && ai > bi);
+          if (gt == ((i & k) == 0)) { sk[i] = b; sk[l] = a; si[i] = bi; si[l] = ai; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // lower chain (thread 0) and upper chain (thread 32): pop while the turn
+  // is not strictly left (lower) / not strictly right (upper)
+  if (tid == 0 || tid == 32) {
+    // the top two stack entries stay in registers (t1 top, t2 below it)
+    const int c = tid == 0 ? 0 : 1;
+    uint16_t* q = st[c];
+    unsigned long long* kq = stk[c];
+    int n = 0;
+    long long x1 = 0, y1 = 0, x2 = 0, y2 = 0;
+    unsigned long long prev = ~0ull;
+    for (int p = 0; p < m; ++p) {
+      const unsigned long long kp = sk[p];
+      if (kp == prev) continue;
+      prev = kp;
+      const long long px = key_x(kp), py = key_y(kp);
+      while (n >= 2) {
+        const long long cr2 = (x1 - x2) * (py - y2) - (y1 - y2) * (px - x2);
+        if (c == 0 ? cr2 > 0 : cr2 < 0) break;
+        --n;
+        x1 = x2; y1 = y2;
+        if (n >= 2) { const unsigned long long k2 = kq[n - 2]; x2 = key_x(k2); y2 = key_y(k2); }
+      }
+      q[n] = (uint16_t)p;
+      kq[n] = kp;
+      ++n;
+      x2 = x1; y2 = y1;
+      x1 = px; y1 = py;
+    }
+    s_n[c] = n;
+  }
+  __syncthreads();
+  uint32_t* out = out_base + o;
+  const int a = s_n[0], b = s_n[1];
+  if (a == 1) {  // every survivor has the same coordinates
+    if (tid == 0) { out[0] = si[st[0][0]]; out_n_base[set] = 1; }
+    return;
+  }
+  for (int k = tid; k < a - 1; k += TB) out[k] = si[st[0][k]];
+  for (int k = 1 + tid; k <= b - 1; k += TB) out[(a - 1) + (b - 1 - k)] = si[st[1][k]];
+  if (tid == 0) out_n_base[set] = (int64_t)(a - 1) + (b - 1);
 }
 
 // Unique points read through the read-only path.
@@ -364,12 +451,13 @@ cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which,
     attr_set[dev] = true;
   }
   const unsigned nsets = (unsigned)S.S;
+  k_small_tiny<<<nsets, TB, 0, st>>>(S, gstatus, which, keys, vals, out, out_n);
   k_small_prep<<<nsets, SB, smem, st>>>(S, gstatus, which, keys, vals, sw, out, out_n);
   // one set: a wide grid (one warp per candidate); a batch: a few blocks per set
   const unsigned px = S.S == 1 ? (unsigned)(2 * SMALL_MAX / 8) : 8u;
   k_small_prune<<<dim3(nsets, px), 256, 0, st>>>(sw);
   k_small_emit<<<nsets, SB, 0, st>>>(S, sw, out, out_n);
-  count_launches(3);
+  count_launches(4);
   return cudaGetLastError();
 }
 

@@ -313,9 +313,10 @@ __device__ void chain_emit(const uint32_t* Vs, const uint32_t* Vu, const uint32_
   if (gt == 0) *out_n = (a - 1) + (b - 1);
 }
 
-__global__ void __launch_bounds__(LBLOCK) k_large(const LargeJob* __restrict__ table, int njobs, LargeJob single,
-                                                   uint32_t* bar, uint32_t* bar_status) {
+__global__ void __launch_bounds__(LBLOCK) k_large(const LargeJob* __restrict__ table, const int* njobs_dev,
+                                                   LargeJob single, uint32_t* bar, uint32_t* bar_status) {
   __shared__ SortSmem S;
+  const int njobs = table ? *reinterpret_cast<const volatile int*>(njobs_dev) : 1;
   for (int jb = 0; jb < njobs; ++jb) {
     const LargeJob J = table ? table[jb] : single;
     if (*reinterpret_cast<const volatile uint32_t*>(&J.h->status)) continue;
@@ -367,7 +368,7 @@ int chain_levels(int64_t cap) {
   return levels;
 }
 
-cudaError_t launch_large(const LargeJob* table, int njobs, const LargeJob& single, uint32_t* bar,
+cudaError_t launch_large(const LargeJob* table, const int* njobs, const LargeJob& single, uint32_t* bar,
                          uint32_t* bar_status, cudaStream_t st) {
   static int occ_cache[64] = {};
   int dev = 0;
@@ -382,7 +383,7 @@ cudaError_t launch_large(const LargeJob* table, int njobs, const LargeJob& singl
   const unsigned G = (unsigned)(device_sm_count() * occ_cache[dev]);
   LargeJob one = single;
   const LargeJob* tab = table;
-  int nj = njobs;
+  const int* nj = njobs;
   uint32_t* b = bar;
   uint32_t* bs = bar_status;
   void* args[] = {(void*)&tab, (void*)&nj, (void*)&one, (void*)&b, (void*)&bs};

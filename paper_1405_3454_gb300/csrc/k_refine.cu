@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_bins(Sets S, Tiles T, const u
 __global__ void __launch_bounds__(REFINE_BINS) k_refine_links(Sets S, const uint32_t* gstatus,
                                                                const unsigned long long* __restrict__ keys_base,
                                                                int4* __restrict__ tri_base) {
-  __shared__ int s_x[REFINE_BINS], s_y[REFINE_BINS], s_has[REFINE_BINS];
+  __shared__ int s_x[REFINE_BINS], s_y[REFINE_BINS];
+  __shared__ unsigned s_mask[REFINE_BINS / 32];
   const int set = blockIdx.x;
   WsHeader* h = S.h(set);
   const unsigned long long* keys = keys_base + S.off_at(set);
@@ -128,20 +129,46 @@ __global__ void __launch_bounds__(REFINE_BINS) k_refine_links(Sets S, const uint
   const int b = threadIdx.x;
   const unsigned long long w = dead ? 0ull : h->rbin[b];
   const bool has = w != 0;
-  s_has[b] = has;
   if (has) {
     const unsigned long long k = keys[(uint32_t)w];
     s_x[b] = key_x(k);
     s_y[b] = key_y(k);
   }
-  __syncthreads();
-  int l = -1, r = -1;
-  for (int d = 1; d < REFINE_BINS; ++d) {
-    if (l < 0 && s_has[(b - d + REFINE_BINS) % REFINE_BINS]) l = (b - d + REFINE_BINS) % REFINE_BINS;
-    if (r < 0 && s_has[(b + d) % REFINE_BINS]) r = (b + d) % REFINE_BINS;
-    if (l >= 0 && r >= 0) break;
-  }
+  // nearest bins with a winner before and after b (cyclically), from the
+  // warps' ballots of "has a winner"
+  constexpr int NWARP = REFINE_BINS / 32;
+  const int lane = b & 31, wp = b >> 5;
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
+  if (lane == 0) s_mask[wp] = bal;
   const int nw = __syncthreads_count(has);
+  int l = -1, r = -1;
+  if (nw > 0) {
+    const unsigned below = bal & ((1u << lane) - 1u);
+    if (below) {
+      l = wp * 32 + 31 - __clz(below);
+    } else {
+      for (int d = 1; d <= NWARP; ++d) {
+        const int w = (wp - d + NWARP) % NWARP;
+        // last, the own warp's bins after b (reached after wrapping around)
+        const unsigned mk = s_mask[w] & (d == NWARP ? (lane == 31 ? 0u : ~((2u << lane) - 1u)) : 0xFFFFFFFFu);
+        if (mk) { l = w * 32 + 31 - __clz(mk); break; }
+      }
+    }
+    const unsigned above = lane == 31 ? 0u : bal & ~((2u << lane) - 1u);
+    if (above) {
+      r = wp * 32 + __ffs(above) - 1;
+    } else {
+      for (int d = 1; d <= NWARP; ++d) {
+        const int w = (wp + d) % NWARP;
+        // last, the own warp's bins before b
+        const unsigned mk = s_mask[w] & (d == NWARP ? ((1u << lane) - 1u) : 0xFFFFFFFFu);
+        if (mk) { r = w * 32 + __ffs(mk) - 1; break; }
+      }
+    }
+    // a lone winner is its own neighbour on both sides
+    if (l < 0 && has) l = b;
+    if (r < 0 && has) r = b;
+  }
   int4 a = make_int4(0, 0, 0, 0), c = make_int4(0, 0, 0, 0);
   int flags = 0;
   if (!dead && h->poly.refine_on && nw >= 2 && l >= 0 && r >= 0) {

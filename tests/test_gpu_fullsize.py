@@ -49,3 +49,31 @@ def test_disk_2p28_bit_exact(gpu_lib, disk_and_oracle, filt):
         del out, ws2
     # cumulative angles on a disk leave ~6.7 % outside the 12-gon
     assert 0.060 < ns / N < 0.072
+
+
+def test_batch_4096_sets_sampled(gpu_lib):
+    """The batched workload at full size (4096 sets, log-uniform sizes from
+    1e3 to 4e6, about 1.9e9 points) through hull_batch with the bench's
+    defaults; 16 sets, the largest among them, checked against the oracle
+    one by one, and every hull offset checked for consistency."""
+    import torch
+    cp = gpu_lib
+    S = 4096
+    xy, off, _ = synth.batch(S, SEED + 17)
+    n = int(off[-1])
+    d = torch.from_numpy(xy).cuda()
+    o = torch.from_numpy(off).cuda()
+    out, hoff, ws = cp.batch(d, o)
+    torch.cuda.synchronize()
+    assert cp.device_status(ws) == (0, 0)
+    hoff = hoff.cpu().numpy()
+    assert hoff[0] == 0 and np.all(np.diff(hoff) >= 3)
+    sizes = np.diff(off)
+    pick = sorted(set([int(np.argmax(sizes)), int(np.argmin(sizes))] +
+                      np.random.default_rng(17).choice(S, 14, replace=False).tolist()))
+    for s in pick:
+        got = out[hoff[s]:hoff[s + 1]].cpu().numpy()
+        want = oracle.cudapre(xy[off[s]:off[s + 1]])["hull"].astype(np.int64) + off[s]
+        assert got.tolist() == want.tolist(), s
+    del d, out, ws
+    assert n > 1_000_000_000
