@@ -353,6 +353,34 @@ def run_ours(args):
         del db, do, bws, bout, bhoff
         torch.cuda.empty_cache()
 
+    # Serving: open-loop Poisson arrivals over a resident pool, continuous
+    # batching (serve.py); latency = completion event - arrival.
+    serving = None
+    if args.serve_requests > 0:
+        from paper_1405_3454_gb300 import serve
+        pxy, pstarts, psizes, _ = synth.serving_pool(args.serve_per_decile, SEED + 29 + rank)
+        dpool = torch.from_numpy(pxy).cuda()
+        del pxy
+        server = serve.Server(dpool, max_points=256 << 20, max_sets=2048, slots=2, opt=fp32)
+        req_set, unit_arr = synth.serving_requests(args.serve_requests, len(psizes), SEED + 31 + rank)
+        mean_size = float(psizes[req_set].mean())
+        cap_gpts = batch["value"] / world if batch else value / world
+        warm = min(2000, args.serve_requests)
+        serve.simulate(server, pstarts, psizes, req_set[:warm], unit_arr[:warm] / (0.5 * cap_gpts * 1e9 / mean_size))
+        runs = {}
+        for frac in (0.8, 0.5):
+            lam = frac * cap_gpts * 1e9 / mean_size
+            res = serve.simulate(server, pstarts, psizes, req_set, unit_arr / lam)
+            runs["load_%.1f" % frac] = dict(res.summary(), arrival_rate_per_s=lam)
+        serving = {"requests": args.serve_requests, "mean_points": mean_size,
+                   "pool": "%d sets (%d per size decile of [1e4, 1.6e7), log-uniform), %d points resident"
+                           % (len(psizes), args.serve_per_decile, int(psizes.sum())),
+                   "capacity_gpoints_per_s": cap_gpts, "slots": 2, "max_batch_points": 256 << 20,
+                   "max_batch_sets": 2048, "memory_budget": "64 GiB", "ingestion": "excluded (pool resident)",
+                   **runs}
+        del server, dpool
+        torch.cuda.empty_cache()
+
     cpu = None
     if world == 1 and rank == 0 and not args.no_cpu:
         ns = 1 << 25
@@ -371,7 +399,8 @@ def run_ours(args):
             "variants": {"plain_exact": {"value": world * n / (ms_exact * 1e-3) / 1e9, "ms_per_step": ms_exact},
                          "fp32_filtered": {"value": value, "ms_per_step": ms},
                          "prefilter_only": prefilter,
-                         "batch": batch},
+                         "batch": batch,
+                         "serving": serving},
             "stages_ms_per_step": stages_out,
             "survivors": n_surv, "escalations": n_esc, "refined_survivors": n_ref, "hull_vertices": n_hull,
             "roofline": roofline,
@@ -397,6 +426,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--batch-sets", type=int, default=4096, help="sets of the batched leg (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--serve-requests", type=int, default=100_000, help="requests of the serving leg (0: skip it)")
+    ap.add_argument("--serve-per-decile", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

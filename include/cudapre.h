@@ -95,7 +95,8 @@ typedef struct hull_options {
 #define HULL_DEVICE_DOMAIN 1u   /* validate found a coordinate outside the domain */
 #define HULL_DEVICE_TIMEOUT 2u  /* a bounded wait expired */
 #define HULL_DEVICE_OVERFLOW 4u /* an internal capacity was exceeded */
-#define HULL_DEVICE_OFFSETS 8u  /* hull_batch: offsets[0] != 0, decreasing, or offsets[S] != n_total */
+#define HULL_DEVICE_OFFSETS 8u  /* hull_batch: offsets[0] != 0, decreasing, offsets[S] != n_total,
+                                   a set of 2^32 points or more, or a range beyond the pool */
 
 /* Fills *opt with the defaults (cumulative angles, FP32 filter, no validation,
  * tuned launch shapes, refinement on). */
@@ -133,7 +134,7 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
                          const hull_options* opt, void* stream);
 
 /* Bytes of workspace needed by hull_batch for S sets of n_total points in
- * all: about 28 bytes per point plus about 1.2 MB per set. */
+ * all: about 28 bytes per point plus about 0.25 MB per set. */
 size_t hull_batch_workspace_bytes(int64_t n_total, int32_t S, const hull_options* opt);
 
 /* The whole method (as hull_compute) on each of S point sets in one call.
@@ -160,6 +161,20 @@ size_t hull_batch_workspace_bytes(int64_t n_total, int32_t S, const hull_options
 hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, int64_t n_total, void* d_ws,
                        size_t ws_bytes, int64_t* d_hull_idx, int64_t* d_hull_offsets,
                        const hull_options* opt, void* stream);
+
+/* hull_batch on sets taken anywhere in a pool of points: set s is the
+ * offsets[s+1] - offsets[s] points of d_xy starting at row d_starts[s]
+ * (sets may overlap, repeat or come in any order; a set may start at any
+ * row).  offsets (S+1, from 0 to n_total) then only give the sizes and the
+ * order of the output; the workspace is hull_batch_workspace_bytes(n_total,
+ * S).  Hull indices are rows of d_xy (d_starts[s] + the index within the
+ * set).  d_starts (S int64, device) is checked on the device: a set beyond
+ * the n_xy points records HULL_DEVICE_OFFSETS.  The paper has no
+ * counterpart: it lets a server batch requests that point into a resident
+ * pool without copying their points. */
+hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_starts, const int64_t* d_offsets,
+                              int32_t S, int64_t n_total, void* d_ws, size_t ws_bytes, int64_t* d_hull_idx,
+                              int64_t* d_hull_offsets, const hull_options* opt, void* stream);
 
 /* hull_compute without a caller workspace; the paper has no counterpart (it
  * is a library convenience, not a step of the method).  The workspace is a

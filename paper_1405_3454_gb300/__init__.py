@@ -37,7 +37,7 @@ ABI_SYMBOLS = (
     "hull_prefilter", "hull_compute", "hull_read_counters", "hull_read_polygon",
     "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version", "hull_read_stats",
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
-    "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes",
+    "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes", "hull_batch_ranges",
 )
 HULL_STAGES = 5
 STAGE_NAMES = ("validate", "extremes", "filter", "sort", "chain")
@@ -116,6 +116,8 @@ def load(path: str | None = None):
     lib.hull_batch_workspace_bytes.restype = sz
     lib.hull_batch.argtypes = [P, P, ctypes.c_int32, i64, P, sz, P, P, OP, P]
     lib.hull_batch.restype = st
+    lib.hull_batch_ranges.argtypes = [P, i64, P, P, ctypes.c_int32, i64, P, sz, P, P, OP, P]
+    lib.hull_batch_ranges.restype = st
     _lib = lib
     return lib
 
@@ -279,6 +281,36 @@ def batch(xy, offsets, opt: Options | None = None, ws=None, stream=None):
     hoff = torch.empty(S + 1, dtype=torch.int64, device=xy.device)
     _check(hull_batch(_ptr(xy), _ptr(offsets), S, n_total, _ptr(ws), ws.numel(), _ptr(out), _ptr(hoff), opt,
                       _stream_handle(stream)), "hull_batch")
+    return out, hoff, ws
+
+
+def hull_batch_ranges(d_xy: int, n_xy: int, d_starts: int, d_offsets: int, S: int, n_total: int, d_ws: int,
+                      ws_bytes: int, d_hull_idx: int, d_hull_offsets: int, opt: Options | None, stream: int) -> int:
+    o = (opt or Options()).c()
+    return load().hull_batch_ranges(d_xy or None, n_xy, d_starts or None, d_offsets, S, n_total, d_ws, ws_bytes,
+                                    d_hull_idx or None, d_hull_offsets, ctypes.byref(o), stream or None)
+
+
+def batch_ranges(pool, starts, sizes, opt: Options | None = None, ws=None, stream=None):
+    """hull_batch_ranges on a resident pool: set s = pool rows starts[s] ..
+    starts[s] + sizes[s].  pool float32 [n_xy, 2], starts / sizes int64 [S]
+    on the pool's device.  Returns (hull_idx int64 (pool rows), hull_offsets
+    int64 [S+1], ws)."""
+    import torch
+    n_xy = _check_points(pool)
+    S = starts.numel()
+    offsets = torch.zeros(S + 1, dtype=torch.int64, device=pool.device)
+    if S:
+        torch.cumsum(sizes, 0, out=offsets[1:])
+    n_total = int(offsets[-1].item()) if S else 0
+    opt = opt or Options()
+    need = hull_batch_workspace_bytes(n_total, S, opt)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, pool.device)
+    out = torch.empty(max(n_total, 1), dtype=torch.int64, device=pool.device)
+    hoff = torch.empty(S + 1, dtype=torch.int64, device=pool.device)
+    _check(hull_batch_ranges(_ptr(pool), n_xy, _ptr(starts), _ptr(offsets), S, n_total, _ptr(ws), ws.numel(),
+                             _ptr(out), _ptr(hoff), opt, _stream_handle(stream)), "hull_batch_ranges")
     return out, hoff, ws
 
 

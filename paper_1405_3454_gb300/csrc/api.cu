@@ -153,6 +153,7 @@ Sets single_set(const float* d_xy, int64_t n, char* ws) {
   Sets S;
   S.xy = d_xy;
   S.off = nullptr;
+  S.start = nullptr;
   S.pp = nullptr;
   S.n1 = n;
   S.S = 1;
@@ -318,10 +319,18 @@ size_t hull_batch_workspace_bytes(int64_t n_total, int32_t S, const hull_options
 hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, int64_t n_total, void* d_ws,
                        size_t ws_bytes, int64_t* d_hull_idx, int64_t* d_hull_offsets, const hull_options* opt,
                        void* stream) {
-  if (S < 0 || n_total < 0 || n_total > ((int64_t)1 << 40)) return HULL_ERR_INVALID_ARG;
+  return hull_batch_ranges(d_xy, n_total, nullptr, d_offsets, S, n_total, d_ws, ws_bytes, d_hull_idx,
+                           d_hull_offsets, opt, stream);
+}
+
+hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_starts, const int64_t* d_offsets,
+                              int32_t S, int64_t n_total, void* d_ws, size_t ws_bytes, int64_t* d_hull_idx,
+                              int64_t* d_hull_offsets, const hull_options* opt, void* stream) {
+  if (S < 0 || n_total < 0 || n_total > ((int64_t)1 << 40) || n_xy < 0) return HULL_ERR_INVALID_ARG;
   if (!d_offsets || !d_hull_offsets || !d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u))
     return HULL_ERR_INVALID_ARG;
   if (n_total > 0 && (!d_xy || (reinterpret_cast<uintptr_t>(d_xy) & 7u) || !d_hull_idx)) return HULL_ERR_INVALID_ARG;
+  if (!d_starts && n_xy != n_total) return HULL_ERR_INVALID_ARG;
   hull_status s;
   if ((s = check_opts(opt)) != HULL_OK) return s;
   const BatchLayout L = batch_layout(n_total, S);
@@ -339,6 +348,7 @@ hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, i
   Sets SS;
   SS.xy = d_xy;
   SS.off = d_offsets;
+  SS.start = d_starts;
   SS.pp = reinterpret_cast<const int64_t*>(ws + L.pp);
   SS.n1 = 0;
   SS.S = S;
@@ -352,8 +362,8 @@ hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, i
   auto* hcnt = reinterpret_cast<int64_t*>(ws + L.hcnt);
   uint16_t* cells = reinterpret_cast<uint16_t*>(ws + L.cells);
   mark(0, st);
-  if (o.validate) HULL_TRY(launch_validate(d_xy, n_total, bstatus, st));
-  HULL_TRY(launch_batch_setup(SS, n_total, bstatus, reinterpret_cast<int64_t*>(ws + L.pp), st));
+  if (o.validate) HULL_TRY(launch_validate(d_xy, n_xy, bstatus, st));
+  HULL_TRY(launch_batch_setup(SS, n_total, n_xy, bstatus, reinterpret_cast<int64_t*>(ws + L.pp), st));
   mark(1, st);
   const int64_t pairs_bound = n_total / 2;
   HULL_TRY(launch_extremes(SS, pairs_bound, o.angles, o.filter, bstatus, ws + L.blockres, cells, o.grid, nullptr, va,

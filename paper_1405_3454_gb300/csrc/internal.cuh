@@ -144,14 +144,18 @@ __host__ __device__ inline int32_t key_y(unsigned long long k) {
 // split evenly over their blocks.
 struct Sets {
   const float* xy;
-  const int64_t* off;  // S+1 element offsets, or null: one set of n1 points
-  const int64_t* pp;   // S+1 prefix of the sets' pair counts, or null
+  const int64_t* off;    // S+1 element offsets, or null: one set of n1 points
+  const int64_t* start;  // S first rows of the sets in xy, or null: off
+  const int64_t* pp;     // S+1 prefix of the sets' pair counts, or null
   int64_t n1;
   int S;
-  char* hdr;           // S headers, HEADER_BYTES apart
+  char* hdr;             // S headers, HEADER_BYTES apart
 
+  // off(s): where set s's part of every per-point workspace array begins
+  // (the prefix of the set sizes); start(s): its first point in xy.
   __host__ __device__ int64_t off_at(int s) const { return off ? off[s] : (s == 0 ? 0 : n1); }
-  __host__ __device__ const float* xy_of(int s) const { return xy + 2 * off_at(s); }
+  __host__ __device__ int64_t start_at(int s) const { return start ? start[s] : off_at(s); }
+  __host__ __device__ const float* xy_of(int s) const { return xy + 2 * start_at(s); }
   __host__ __device__ int64_t n_of(int s) const { return off_at(s + 1) - off_at(s); }
   __host__ __device__ int head_of(int s) const {
     return (n_of(s) > 0 && (reinterpret_cast<uintptr_t>(xy_of(s)) & 15u)) ? 1 : 0;
@@ -266,7 +270,8 @@ __host__ __device__ inline size_t chains_at(int64_t off, int s) { return 4 * (si
 int chain_levels(int64_t cap);
 
 // Batch-only steps (k_batch.cu).
-cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, uint32_t* bstatus, int64_t* pp, cudaStream_t st);
+cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, int64_t n_xy, uint32_t* bstatus, int64_t* pp,
+                               cudaStream_t st);
 cudaError_t launch_batch_jobs(const Sets& S, const uint32_t* bstatus, int which, unsigned long long* ka, uint32_t* va,
                               unsigned long long* kb, uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out,
                               int64_t* out_n, LargeJob* jobs, int* njobs, cudaStream_t st);

@@ -49,15 +49,21 @@ __device__ int64_t block_prefix(int n, Get get, Put put) {
   return total;
 }
 
-// Offsets check (off[0] == 0, non-decreasing, off[S] == n_total) and the
-// prefix of the sets' 16-byte pair counts.  Bad offsets set
-// HULL_DEVICE_OFFSETS in the batch status and every later step skips.
-__global__ void __launch_bounds__(TB) k_batch_setup(Sets S, int64_t n_total, uint32_t* bstatus, int64_t* pp) {
+// Offsets check (off[0] == 0, non-decreasing, off[S] == n_total; with
+// start rows, every set within the n_xy points) and the prefix of the sets'
+// 16-byte pair counts.  Bad offsets set HULL_DEVICE_OFFSETS in the batch
+// status and every later step skips.
+__global__ void __launch_bounds__(TB) k_batch_setup(Sets S, int64_t n_total, int64_t n_xy, uint32_t* bstatus,
+                                                    int64_t* pp) {
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = (S.off[0] != 0 || S.off[S.S] != n_total) ? 1 : 0;
   __syncthreads();
   bool bad = false;
-  for (int s = threadIdx.x; s < S.S; s += TB) bad |= S.off[s + 1] < S.off[s];
+  for (int s = threadIdx.x; s < S.S; s += TB) {
+    const int64_t n = S.off[s + 1] - S.off[s];
+    bad |= n < 0 || n > 0xFFFFFFFFll;
+    if (S.start) bad |= S.start[s] < 0 || S.start[s] > n_xy - n;
+  }
   if (bad) atomicOr(&s_bad, 1);
   __syncthreads();
   const bool ok = s_bad == 0;
@@ -113,18 +119,19 @@ __global__ void __launch_bounds__(TB) k_batch_offsets(Sets S, uint32_t* bstatus,
 }
 
 // Global indices: hull vertex k of set s goes to hull_idx[hoff[s] + k] as
-// off[s] + (its index within the set).
+// start(s) + (its index within the set).
 __global__ void k_batch_gather(Sets S, const uint32_t* hstage, const int64_t* hoff, int64_t* hull_idx) {
   for (int s = blockIdx.x; s < S.S; s += gridDim.x) {
-    const int64_t b = hoff[s], c = hoff[s + 1] - b, o = S.off_at(s);
-    for (int64_t k = threadIdx.x; k < c; k += blockDim.x) hull_idx[b + k] = o + (int64_t)hstage[o + k];
+    const int64_t b = hoff[s], c = hoff[s + 1] - b, o = S.off_at(s), g = S.start_at(s);
+    for (int64_t k = threadIdx.x; k < c; k += blockDim.x) hull_idx[b + k] = g + (int64_t)hstage[o + k];
   }
 }
 
 }  // namespace
 
-cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, uint32_t* bstatus, int64_t* pp, cudaStream_t st) {
-  k_batch_setup<<<1, TB, 0, st>>>(S, n_total, bstatus, pp);
+cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, int64_t n_xy, uint32_t* bstatus, int64_t* pp,
+                               cudaStream_t st) {
+  k_batch_setup<<<1, TB, 0, st>>>(S, n_total, n_xy, bstatus, pp);
   count_launches(1);
   return cudaGetLastError();
 }

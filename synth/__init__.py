@@ -174,3 +174,40 @@ def mix64(z: int) -> int:
 
 def draw(seed: int, stream: int, i: int, k: int) -> int:
     return int(_get().synth_draw(seed, stream, i, k))
+
+
+def _unit(seed: int, stream: int, i: int, k: int) -> float:
+    """U(0, 1) from one counter-based draw (53 bits, never 0)."""
+    return ((draw(seed, stream, i, k) >> 11) + 0.5) * 2.0 ** -53
+
+
+def serving_pool(per_decile: int, seed: int = BASE_SEED, lo: float = 1e4, hi: float = 1.6e7):
+    """The dataset pool of the serving workload: per_decile sets in each of
+    the 10 log-size deciles of [lo, hi) (size floor(exp(U)) within its
+    decile, shape drawn per set as in the batched workload), concatenated.
+    Returns (xy [N, 2] float32, starts [K] int64, sizes [K] int64, shapes [K])."""
+    k_sets = 10 * per_decile
+    a, b = np.log(lo), np.log(hi)
+    sizes = np.empty(k_sets, np.int64)
+    shapes = np.empty(k_sets, np.int32)
+    for j in range(k_sets):
+        d = j // per_decile
+        u = _unit(seed, 60, j, 0)
+        sizes[j] = int(np.floor(np.exp(a + (b - a) * (d + u) / 10.0)))
+        shapes[j] = int(draw(seed, 61, j, 0) % 3)
+    starts = np.zeros(k_sets, np.int64)
+    np.cumsum(sizes[:-1], out=starts[1:])
+    xy = _out(int(sizes.sum()))
+    for j in range(k_sets):
+        shape(int(shapes[j]), int(sizes[j]), seed, 2000 + j, out=xy[starts[j]:starts[j] + sizes[j]])
+    return xy, starts, sizes, shapes
+
+
+def serving_requests(n: int, k_sets: int, seed: int = BASE_SEED):
+    """n requests over a pool of k_sets sets: the set of each request
+    (uniform, so request sizes follow the pool's log-uniform deciles) and
+    unit-rate Poisson arrival times (divide by the rate to scale).
+    Returns (set index [n] int64, arrival [n] float64)."""
+    sets = np.fromiter((draw(seed, 62, r, 0) % k_sets for r in range(n)), dtype=np.int64, count=n)
+    gaps = np.fromiter((-np.log(_unit(seed, 63, r, 0)) for r in range(n)), dtype=np.float64, count=n)
+    return sets, np.cumsum(gaps)

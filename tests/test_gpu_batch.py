@@ -116,3 +116,69 @@ def test_batch_bad_offsets_flagged(gpu_lib):
     out, hoff, ws = run_batch(cp, xy, bad, cp.Options())
     assert cp.device_status(ws)[1] & cp.HULL_DEVICE_OFFSETS
     assert hoff.tolist() == [0, 0, 0, 0]
+
+
+def test_batch_ranges_in_a_pool(gpu_lib):
+    # sets taken anywhere in a resident pool: overlapping, repeated, empty,
+    # out of order, starting at odd rows
+    import torch
+    cp = gpu_lib
+    pool = np.concatenate([synth.disk(300_000, 9800), synth.square(200_001, 9801),
+                           synth.gaussian(150_000, 9802)]).astype(np.float32)
+    rng = np.random.default_rng(9803)
+    ranges = [(0, 300_000), (300_000, 200_001), (500_001, 150_000), (12_345, 0), (7, 99_999), (7, 99_999),
+              (640_000, 10_001), (123_457, 3), (1, 1)]
+    for _ in range(40):
+        a = int(rng.integers(0, len(pool)))
+        b = int(rng.integers(0, min(60_000, len(pool) - a) + 1))
+        ranges.append((a, b))
+    d = torch.from_numpy(pool).cuda()
+    starts = torch.tensor([r[0] for r in ranges], dtype=torch.int64, device="cuda")
+    sizes = torch.tensor([r[1] for r in ranges], dtype=torch.int64, device="cuda")
+    out, hoff, ws = cp.batch_ranges(d, starts, sizes)
+    torch.cuda.synchronize()
+    assert cp.device_status(ws) == (0, 0)
+    out, hoff = out.cpu().numpy(), hoff.cpu().numpy()
+    for s, (a, b) in enumerate(ranges):
+        got = out[hoff[s]:hoff[s + 1]]
+        want = (oracle.cudapre(pool[a:a + b])["hull"].astype(np.int64) + a) if b else np.zeros(0, np.int64)
+        assert got.tolist() == want.tolist(), (s, a, b)
+
+
+def test_batch_range_beyond_the_pool_flagged(gpu_lib):
+    import torch
+    cp = gpu_lib
+    pool = torch.from_numpy(synth.disk(1000, 9804)).cuda()
+    starts = torch.tensor([0, 900], dtype=torch.int64, device="cuda")
+    sizes = torch.tensor([500, 200], dtype=torch.int64, device="cuda")
+    out, hoff, ws = cp.batch_ranges(pool, starts, sizes)
+    torch.cuda.synchronize()
+    assert cp.device_status(ws)[1] & cp.HULL_DEVICE_OFFSETS
+    assert hoff.cpu().tolist() == [0, 0, 0]
+
+
+def test_server_slots_match_oracle_and_simulation_completes(gpu_lib):
+    import torch
+    from paper_1405_3454_gb300 import serve
+    cp = gpu_lib
+    pxy, starts, sizes, _ = synth.serving_pool(1, 9900, 1e3, 2e5)
+    pool = torch.from_numpy(pxy).cuda()
+    server = serve.Server(pool, max_points=1 << 20, max_sets=64, slots=2)
+    picks = [[0, 3, 5, 9, 9], [1, 2, 4, 6, 7, 8]]
+    slots = []
+    for k, p in enumerate(picks):
+        slot = server.free_slot()
+        server.launch(slot, starts[p], sizes[p], k)
+        slots.append(slot)
+    torch.cuda.synchronize()
+    done = server.poll()
+    assert sorted(t for _, t in done) == [0, 1] and server.free_slot() is not None
+    for slot, p in zip(slots, picks):
+        out, hoff = slot["out"].cpu().numpy(), slot["hoff"][:len(p) + 1].cpu().numpy()
+        for s, j in enumerate(p):
+            want = oracle.cudapre(pxy[starts[j]:starts[j] + sizes[j]])["hull"].astype(np.int64) + starts[j]
+            assert out[hoff[s]:hoff[s + 1]].tolist() == want.tolist()
+    req_set, unit = synth.serving_requests(500, len(sizes), 9901)
+    res = serve.simulate(server, starts, sizes, req_set, unit / 20000.0)
+    assert np.all(np.isfinite(res.completion_s)) and np.all(res.latency_s > 0)
+    assert res.points == int(sizes[req_set].sum())
