@@ -132,6 +132,23 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest of every rank's x (each rank passes its own); x itself on
+    one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput in units per second: every rank processes its own
+    units (weak scaling) and the job takes the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def cpu_oracle_sample(n_sample: int, seed: int):
     """The CPU oracle (as it stands, single-threaded) on the first n_sample
     points of the workload's generator stream: (Gpoints/s, seconds)."""
@@ -217,13 +234,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     def timed(fn, opt, steps, timer=None):
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -236,7 +246,7 @@ def run_ours(args):
         if timer:
             timer.detach()
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / steps)
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dist)
 
     for _ in range(args.warmup):
         step(fp32)
@@ -255,7 +265,7 @@ def run_ours(args):
     stats = cp.read_stats(ws)
     n_surv, n_esc, n_ref = stats["n_survivors"], stats["n_escalated"], stats["n_refined"]
     n_hull = int(cnt.item())
-    value = world * n / (ms * 1e-3) / 1e9
+    value = job_rate(world, n, ms * 1e-3) / 1e9
 
     # Plain exact method (binary64 projections, int64 orientation for every edge).
     for _ in range(2):
@@ -311,7 +321,7 @@ def run_ours(args):
         k, _ = e2e_step()
         d2h += 8 + 4 * k
     barrier()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist)
     e2e = {"value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": d2h // e2e_steps}
 

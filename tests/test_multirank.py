@@ -1,0 +1,53 @@
+"""The multi-process path of bench.py on CPU: two gloo ranks, each with its
+own set of points (weak scaling, no data-path collective), the job time is
+the slowest rank's and the throughput counts every rank's points."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ws, r, local = bench.dist_info()
+    local_ms = 10.0 + 5.0 * rank  # rank 1 is the slow one
+    ms = bench.max_over_ranks(local_ms, dist, "cpu")
+    rate = bench.job_rate(ws, 1000, ms * 1e-3)
+    q.put((r, ws, local, ms, rate))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_rank_and_sum_the_units():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, (rank, ws, local, ms, rate) in enumerate(got):
+        assert (rank, ws, local) == (r, 2, r)
+        assert ms == 15.0                      # the slowest rank's time on every rank
+        assert rate == pytest.approx(2 * 1000 / 0.015)
+
+
+def test_single_process_defaults():
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.job_rate(1, 10, 2.0) == 5.0
