@@ -104,7 +104,7 @@ struct WsHeader {
   uint32_t bar_count, bar_gen;  // grid barrier of the cooperative large-set kernel
   uint32_t hist[8][256];  // radix-sort digit histograms (all passes)
   unsigned long long n_surv2;  // survivors left by the refinement round
-  unsigned long long pad1_;
+  uint32_t n_lower, n_upper;   // small-set hull: vertices of the lower / upper chain
   Poly poly;
   unsigned long long rbin[1024];  // refinement: per angular bin, packed farthest survivor
 };
@@ -247,11 +247,9 @@ struct SmallWs {
   uint32_t uid[SMALL_MAX];
   uint16_t chain[2][SMALL_MAX];
   uint8_t keep[2][SMALL_MAX];
+  uint8_t flag[SMALL_MAX];  // whole-GPU path: bit 0 lower-chain vertex, bit 1 upper
 };
 
-// The one-block hull of every set with 1..SMALL_MAX survivors (which = 0:
-// after Step 3, 1: after the refinement round); sets without survivors get
-// count 0.  out / out_n: per-set hull (set-local indices) and count.
 cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which, const unsigned long long* keys,
                               const uint32_t* vals, SmallWs* sw, uint32_t* out, int64_t* out_n, cudaStream_t st);
 

@@ -675,16 +675,20 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(Sets S, int64_t ppb, const
 // 16 extremes, Step 2 (the polygon, its edge records and inner box) and the
 // cell grid of the inside test.
 
+// Phase hooks of the finishing kernel (no code unless a timing build
+// defines FSTAMP).
+#ifndef FSTAMP
+#define FSTAMP(i) ((void)0)
+#endif
+
 template <int ANG, int FIN_THREADS>
 __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb, const uint32_t* gstatus,
                                                                const BlockBest* bres, uint32_t* ext_out,
                                                                uint16_t* cells_base, uint32_t* surv_idx,
                                                                unsigned long long* surv_key) {
-  static_assert(FIN_THREADS % 32 == 0 && FIN_THREADS <= 1024, "one reduction entry per warp");
+  static_assert(FIN_THREADS % 32 == 0 && FIN_THREADS <= 1024, "whole warps");
   constexpr int ND = Dirs<ANG>::ND;
   __shared__ uint32_t s_ext[NSLOT];
-  __shared__ unsigned long long s_k[FIN_THREADS / 32][ND];
-  __shared__ uint32_t s_i[FIN_THREADS / 32][ND];
   __shared__ long long s_ax[MAXV][GRID], s_by[MAXV][GRID];  // per edge: min of A x per column, B y per row
   __shared__ long long s_c[MAXV], s_span[MAXV];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -706,60 +710,35 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
   // points outside the 16-byte pairs: the head point and an odd last point
   const bool lead = !dead && head == 1;
   const bool trail = !dead && n > head && ((n - head) & 1);
-  // every direction at once: per thread over its strided entries, then a
-  // warp butterfly and a cross-warp pass (all exact)
-  unsigned long long ks[ND];
-  uint32_t bi[ND];
-#pragma unroll
-  for (int d = 0; d < ND; ++d) { ks[d] = 0; bi[d] = NONE; }
-  auto take = [&](int d, unsigned long long k, uint32_t i) {
-    return i != NONE && (bi[d] == NONE || k > ks[d] || (k == ks[d] && i < bi[d]));
-  };
-  for (int64_t e = e0 + tid; e < e1; e += FIN_THREADS) {
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
+  FSTAMP(0);
+  // One warp per direction: its lanes take the set's block results (and the
+  // loose points) in turn, then an exact butterfly by (score key, index).
+  for (int d = warp; d < ND; d += FIN_THREADS / 32) {
+    unsigned long long ks = 0;
+    uint32_t bi = NONE;
+    auto take = [&](unsigned long long k, uint32_t i) {
+      return i != NONE && (bi == NONE || k > ks || (k == ks && i < bi));
+    };
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
       const BlockBest b = bres[e * ND + d];
       const unsigned long long k = dkey(b.s);
-      if (take(d, k, b.idx)) { ks[d] = k; bi[d] = b.idx; }
+      if (take(k, b.idx)) { ks = k; bi = b.idx; }
     }
-  }
-  if (tid == FIN_THREADS - 1) {
-    for (int r = 0; r < 2; ++r) {
-      if (!(r == 0 ? lead : trail)) continue;
-      const uint32_t i = r == 0 ? 0u : (uint32_t)(n - 1);
+    if (lane < 2 && (lane == 0 ? lead : trail)) {
+      const uint32_t i = lane == 0 ? 0u : (uint32_t)(n - 1);
       const float2 p = load_point(xy, i);
-#pragma unroll
-      for (int d = 0; d < ND; ++d) {
-        const unsigned long long k = dkey(score64(ANG, d, p.x, p.y));
-        if (take(d, k, i)) { ks[d] = k; bi[d] = i; }
-      }
+      const unsigned long long k = dkey(score64(ANG, d, p.x, p.y));
+      if (take(k, i)) { ks = k; bi = i; }
     }
-  }
-  auto butterfly = [&](int d) {
     for (int off = 16; off; off >>= 1) {
-      const uint32_t io = __shfl_xor_sync(FULL, bi[d], off);
-      const unsigned long long ko = __shfl_xor_sync(FULL, ks[d], off);
-      if (take(d, ko, io)) { ks[d] = ko; bi[d] = io; }
+      const uint32_t io = __shfl_xor_sync(FULL, bi, off);
+      const unsigned long long ko = __shfl_xor_sync(FULL, ks, off);
+      if (take(ko, io)) { ks = ko; bi = io; }
     }
-  };
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    butterfly(d);
-    if (lane == 0) { s_k[warp][d] = ks[d]; s_i[warp][d] = bi[d]; }
+    if (lane == 0) s_ext[d] = bi;
   }
   __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      // one entry per warp of the block (FIN_THREADS / 32 <= 32)
-      const bool have = lane < FIN_THREADS / 32;
-      ks[d] = have ? s_k[have ? lane : 0][d] : 0ull;
-      bi[d] = have ? s_i[have ? lane : 0][d] : NONE;
-      butterfly(d);
-      if (lane == 0) s_ext[d] = bi[d];
-    }
-  }
-  __syncthreads();
+  FSTAMP(1);
   if (tid == 0) {
     if (ANG == 0) {
       // 120 degrees from 30 degrees: with the correctly rounded constants,
@@ -780,6 +759,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
     hull16_warp(xy, s_ext, &h->poly, grid_on);
   }
   __syncthreads();
+  FSTAMP(2);
   // The loose points' inside test (Step 3): exact against every edge.
   if (!dead && tid == 0) {
     const int mm = h->poly.m;
@@ -806,6 +786,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
   // maximum.  Bit k of a cell's mask: some point of the cell may fail edge
   // k; a cell entirely outside edge k keeps only bit k.  Byte code: 0 inside,
   // k + 1 only edge k, CELL_MULTI several edges.
+  FSTAMP(3);
   const Poly& P = h->poly;
   const int m = P.m;
   if (dead || m < 3) return;
@@ -831,6 +812,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
     }
   }
   __syncthreads();
+  FSTAMP(4);
   uint8_t* code8 = reinterpret_cast<uint8_t*>(cells + GRID * GRID);
   for (int c = tid; c < GRID * GRID; c += FIN_THREADS) {
     const int cx = c & (GRID - 1), cy = c >> GRID_LOG;
@@ -843,6 +825,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
     cells[c] = (uint16_t)mask;
     code8[c] = mask == 0 ? 0 : ((mask & (mask - 1)) == 0 ? (uint8_t)__ffs(mask) : (uint8_t)CELL_MULTI);
   }
+  FSTAMP(5);
 }
 
 // Domain check (finite, integer-valued, |v| <= 2^24).

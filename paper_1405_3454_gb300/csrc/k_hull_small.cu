@@ -1,22 +1,32 @@
-// k_hull_small.cu -- Andrew's monotone chain for a small survivor set (up to
-// SMALL_MAX points): the final step of the method, the hull of the points
-// that remain (section 3, case (2)).  Three launches:
+// k_hull_small.cu -- the hull of a survivor set of at most SMALL_MAX points:
+// the final step of the method, the hull of the points that remain (section
+// 3, case (2)).
 //
-// prep  (one block) Load the survivors into shared memory and bitonic-sort
-//       them by (x, y, index); keep the first of each run of equal
-//       coordinates, which has the lowest index.  Split the sorted points
-//       into 32 chunks; one lane per chunk runs the lower and one the upper
-//       monotone chain of its chunk.
-// prune (whole grid, one warp per chunk-chain vertex) A vertex v is a vertex
-//       of the whole lower hull iff every earlier point a and later point b
-//       make a strict left turn a -> v -> b: the most counter-clockwise
-//       incoming direction v - a turns strictly left into the most clockwise
-//       outgoing direction b - v.  Over one chunk's convex chain these
-//       extremes are unimodal, so lane c finds chunk c's by binary search and
-//       a warp reduction combines the 32 chunks.  The upper hull is the same
-//       test with the orientation sign flipped.
-// emit  (one block) Write the lower hull left to right, then the upper hull
-//       right to left.
+// tiny     (one block per set, at most TINY_MAX points) bitonic sort in
+//          shared memory, then Andrew's lower and upper monotone chains.
+// One set of more points uses the whole GPU, without sorting:
+// classify (one warp per survivor v) v is a vertex of the lower chain iff
+//          no point with equal coordinates has a lower index, and either v is
+//          the lexicographically smallest or largest point, or the most
+//          counter-clockwise incoming direction v - a over every point a
+//          before v (in (x, y) order) turns strictly left into the most
+//          clockwise outgoing direction b - v over every point b after v;
+//          the upper chain is the same with the turns mirrored.  The
+//          directions of each reduction lie in a half-plane, so the cross
+//          product orders them.
+// rank     (one warp per vertex) its position: how many vertices of its chain
+//          come before it in (x, y) order.
+// A batch gives each set one block (many sets at once):
+// prep     sort the survivors by (x, y, index) in registers and shared
+//          memory, keep the first of each run of equal coordinates (the
+//          lowest index), split them into 32 chunks and run the lower and
+//          upper chain of each chunk;
+// prune    (one warp per chunk-chain vertex) the test of classify over the
+//          32 chunk chains, each by binary search (the extremes over one
+//          convex chain are unimodal);
+// emit     the lower hull left to right, then the upper hull right to left.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace cudapre {
@@ -68,18 +78,25 @@ struct Pts {
 
 // Chain of chunk c (positions into the unique arrays) for sign S (+1 lower,
 // -1 upper), computed by one thread, in place from `base`.
-template <int S>
-__device__ int chunk_chain(Pts P, int lo, int hi, uint16_t* st) {
+// Chain of chunk [lo, hi) (positions into the unique arrays) for sign sg
+// (+1 lower, -1 upper), computed by one thread into st; the top two stack
+// points stay in registers.  Lower and upper chains of one chunk run in two
+// lanes of one warp on the same instruction stream.
+__device__ int chunk_chain(Pts P, int lo, int hi, uint16_t* st, long long sg) {
   int n = 0;
+  long long x1 = 0, y1 = 0, x2 = 0, y2 = 0;
   for (int p = lo; p < hi; ++p) {
     const long long px = P.x[p], py = P.y[p];
     while (n >= 2) {
-      const int a = st[n - 2], b = st[n - 1];
-      const long long c = S * cr(P.x[b] - (long long)P.x[a], P.y[b] - (long long)P.y[a], px - P.x[a], py - P.y[a]);
+      const long long c = sg * cr(x1 - x2, y1 - y2, px - x2, py - y2);
       if (c > 0) break;
       --n;
+      x1 = x2; y1 = y2;
+      if (n >= 2) { const int a = st[n - 2]; x2 = P.x[a]; y2 = P.y[a]; }
     }
     st[n++] = (uint16_t)p;
+    x2 = x1; y2 = y1;
+    x1 = px; y1 = py;
   }
   return n;
 }
@@ -123,26 +140,81 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
   unsigned long long* sk = reinterpret_cast<unsigned long long*>(sm);
   uint32_t* si = reinterpret_cast<uint32_t*>(sk + SMALL_MAX);
   uint16_t* chain = reinterpret_cast<uint16_t*>(si + SMALL_MAX);  // [2][SMALL_MAX]
-  for (int i = tid; i < P2; i += SB) {
-    sk[i] = i < m ? kin[i] : ~0ull;
-    si[i] = i < m ? vin[i] : ~0u;
-  }
-  __syncthreads();
-  STAMP(1);
-  // bitonic sort by (key, index)
-  for (int k = 2; k <= P2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < P2; i += SB) {
-        const int l = i ^ j;
-        if (l > i) {
-          const unsigned long long a = sk[i], b = sk[l];
-          const uint32_t ai = si[i], bi = si[l];
-          const bool gt = a > b || (a == b && ai > bi);
-          if (gt == ((i & k) == 0)) { sk[i] = b; sk[l] = a; si[i] = bi; si[l] = ai; }
-        }
-      }
-      __syncthreads();
+  // Bitonic sort by (key, index) of P2 = 2^p elements (2048..8192), element
+  // i = r * SB + tid held in registers by thread tid (r < P2 / SB): partner
+  // distances below 32 are exchanged by warp shuffles, distances of SB and
+  // more stay in the thread, only 32..SB/2 go through shared memory.
+  {
+    constexpr int EMAX = SMALL_MAX / SB;
+    const int NE = P2 / SB;
+    unsigned long long qk[EMAX];
+    uint32_t qv[EMAX];
+#pragma unroll
+    for (int r = 0; r < EMAX; ++r) {
+      const int i = r * SB + tid;
+      qk[r] = (r < NE && i < m) ? kin[i] : ~0ull;
+      qv[r] = (r < NE && i < m) ? vin[i] : ~0u;
     }
+    STAMP(1);
+    for (int k = 2; k <= P2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        if (j >= SB) {  // partner in the same thread: element r ^ (j / SB)
+          auto in_thread = [&](auto JR) {
+            constexpr int jr = decltype(JR)::value;
+#pragma unroll
+            for (int r = 0; r < EMAX; ++r) {
+              const int l = r ^ jr;
+              if (l > r && l < EMAX && r < NE) {
+                const int i = r * SB + tid;
+                const bool asc = (i & k) == 0;
+                const bool gt = qk[r] > qk[l] || (qk[r] == qk[l] && qv[r] > qv[l]);
+                if (gt == asc) {
+                  const unsigned long long tk = qk[r]; qk[r] = qk[l]; qk[l] = tk;
+                  const uint32_t tv = qv[r]; qv[r] = qv[l]; qv[l] = tv;
+                }
+              }
+            }
+          };
+          const int jr = j / SB;  // 1, 2 or 4
+          if (jr == 1) in_thread(std::integral_constant<int, 1>{});
+          else if (jr == 2) in_thread(std::integral_constant<int, 2>{});
+          else in_thread(std::integral_constant<int, 4>{});
+          continue;
+        }
+        if (j >= 32) {  // through shared memory
+#pragma unroll
+          for (int r = 0; r < EMAX; ++r)
+            if (r < NE) { sk[r * SB + tid] = qk[r]; si[r * SB + tid] = qv[r]; }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < EMAX; ++r) {
+          if (r < NE) {
+            const int i = r * SB + tid;
+            unsigned long long pk;
+            uint32_t pv;
+            if (j >= 32) {
+              pk = sk[i ^ j];
+              pv = si[i ^ j];
+            } else {
+              pk = __shfl_xor_sync(FULL, qk[r], j);
+              pv = __shfl_xor_sync(FULL, qv[r], j);
+            }
+            const bool asc = (i & k) == 0;
+            const bool lower = (i & j) == 0;  // the smaller index of the pair
+            const bool pgt = pk > qk[r] || (pk == qk[r] && pv > qv[r]);  // partner is larger
+            // the lower element keeps the minimum when ascending
+            const bool take = lower == asc ? !pgt : pgt;
+            if (take) { qk[r] = pk; qv[r] = pv; }
+          }
+        }
+        if (j >= 32) __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < EMAX; ++r)
+      if (r < NE) { sk[r * SB + tid] = qk[r]; si[r * SB + tid] = qv[r]; }
+    __syncthreads();
   }
   STAMP(2);
   // dedupe: first of each run of equal keys (lowest index) -> unique arrays
@@ -186,8 +258,7 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
   {
     const int w = tid >> 5, lane = tid & 31;
     const int lo = min(w * C, u), hi = min(lo + C, u);
-    if (lane == 0) s_cnt[0][w] = chunk_chain<1>(P, lo, hi, chain + w * C);
-    if (lane == 1) s_cnt[1][w] = chunk_chain<-1>(P, lo, hi, chain + SMALL_MAX + w * C);
+    if (lane < 2) s_cnt[lane][w] = chunk_chain(P, lo, hi, chain + lane * SMALL_MAX + w * C, lane == 0 ? 1 : -1);
   }
   __syncthreads();
   STAMP(4);
@@ -232,9 +303,13 @@ __global__ void __launch_bounds__(TB) k_small_tiny(Sets S, const uint32_t* gstat
   const int tid = threadIdx.x;
   const int set = blockIdx.x;
   const WsHeader* h = S.h(set);
-  if (*reinterpret_cast<const volatile uint32_t*>(gstatus)) return;
-  const int64_t m64 = count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
-  if (m64 == 0 || m64 > TINY_MAX) return;
+  const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0;
+  const int64_t m64 = dead ? 0 : count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
+  if (m64 == 0) {  // nothing survives (or the call is dead): an empty hull
+    if (tid == 0) out_n_base[set] = 0;
+    return;
+  }
+  if (m64 > TINY_MAX) return;
   const int m = (int)m64;
   const int64_t o = S.off_at(set);
   int P2 = 2;
@@ -433,6 +508,135 @@ __global__ void __launch_bounds__(SB, 1) k_small_emit(Sets S, const SmallWs* sw_
   }
 }
 
+// Cross product of two directions given by 32-bit components (each product
+// is one widening multiply).
+__device__ __forceinline__ long long crs(int bx, int by, int dx, int dy) {
+  return (long long)bx * dy - (long long)by * dx;
+}
+
+constexpr int CW = 8;  // warps per block of classify and rank
+
+__global__ void __launch_bounds__(CW * 32) k_small_classify(Sets S, const uint32_t* gstatus, int which,
+                                                             const unsigned long long* __restrict__ kin_base,
+                                                             const uint32_t* __restrict__ vin_base,
+                                                             SmallWs* sw_base) {
+  const int set = blockIdx.x;
+  WsHeader* h = S.h(set);
+  if (*reinterpret_cast<const volatile uint32_t*>(gstatus)) return;
+  const int64_t m64 = count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
+  if (m64 <= TINY_MAX || m64 > SMALL_MAX) return;
+  const int m = (int)m64;
+  const int64_t o = S.off_at(set);
+  const unsigned long long* K = kin_base + o;
+  const uint32_t* V = vin_base + o;
+  SmallWs* sw = sw_base + set;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.y * CW;
+  for (int v = blockIdx.y * CW + (threadIdx.x >> 5); v < m; v += warps) {
+    const unsigned long long kv = __ldg(K + v);
+    const uint32_t iv = __ldg(V + v);
+    const int vx = key_x(kv), vy = key_y(kv);
+    // per lane: best incoming (lower: most CCW, upper: most CW) and best
+    // outgoing (lower: most CW, upper: most CCW) directions
+    int lix = 0, liy = 0, lox = 0, loy = 0, uix = 0, uiy = 0, uox = 0, uoy = 0;
+    bool hin = false, hout = false, dup = false;
+    for (int a = lane; a < m; a += 32) {
+      const unsigned long long ka = __ldg(K + a);
+      if (ka == kv) {
+        dup |= __ldg(V + a) < iv;
+        continue;
+      }
+      const int ax = key_x(ka), ay = key_y(ka);
+      if (ka < kv) {  // incoming v - a
+        const int dx = vx - ax, dy = vy - ay;
+        if (!hin) { lix = uix = dx; liy = uiy = dy; hin = true; continue; }
+        if (crs(lix, liy, dx, dy) > 0) { lix = dx; liy = dy; }
+        if (crs(uix, uiy, dx, dy) < 0) { uix = dx; uiy = dy; }
+      } else {        // outgoing a - v
+        const int dx = ax - vx, dy = ay - vy;
+        if (!hout) { lox = uox = dx; loy = uoy = dy; hout = true; continue; }
+        if (crs(lox, loy, dx, dy) < 0) { lox = dx; loy = dy; }
+        if (crs(uox, uoy, dx, dy) > 0) { uox = dx; uoy = dy; }
+      }
+    }
+    for (int off = 16; off; off >>= 1) {
+      const bool oin = __shfl_xor_sync(FULL, hin, off), oout = __shfl_xor_sync(FULL, hout, off);
+      int x1 = __shfl_xor_sync(FULL, lix, off), y1 = __shfl_xor_sync(FULL, liy, off);
+      int x2 = __shfl_xor_sync(FULL, uix, off), y2 = __shfl_xor_sync(FULL, uiy, off);
+      if (oin) {
+        if (!hin || crs(lix, liy, x1, y1) > 0) { lix = x1; liy = y1; }
+        if (!hin || crs(uix, uiy, x2, y2) < 0) { uix = x2; uiy = y2; }
+      }
+      x1 = __shfl_xor_sync(FULL, lox, off); y1 = __shfl_xor_sync(FULL, loy, off);
+      x2 = __shfl_xor_sync(FULL, uox, off); y2 = __shfl_xor_sync(FULL, uoy, off);
+      if (oout) {
+        if (!hout || crs(lox, loy, x1, y1) < 0) { lox = x1; loy = y1; }
+        if (!hout || crs(uox, uoy, x2, y2) > 0) { uox = x2; uoy = y2; }
+      }
+      hin |= oin;
+      hout |= oout;
+      dup |= __shfl_xor_sync(FULL, dup, off);
+    }
+    if (lane == 0) {
+      uint8_t f = 0;
+      if (!dup) {
+        const bool end = !hin || !hout;
+        if (end || crs(lix, liy, lox, loy) > 0) f |= 1;
+        if (end || crs(uix, uiy, uox, uoy) < 0) f |= 2;
+      }
+      sw->flag[v] = f;
+      if (f & 1) atomicAdd(&h->n_lower, 1u);
+      if (f & 2) atomicAdd(&h->n_upper, 1u);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CW * 32) k_small_rank(Sets S, const uint32_t* gstatus, int which,
+                                                         const unsigned long long* __restrict__ kin_base,
+                                                         const uint32_t* __restrict__ vin_base,
+                                                         const SmallWs* sw_base, uint32_t* __restrict__ out_base,
+                                                         int64_t* out_n_base) {
+  const int set = blockIdx.x;
+  const WsHeader* h = S.h(set);
+  if (*reinterpret_cast<const volatile uint32_t*>(gstatus)) return;
+  const int64_t m64 = count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
+  if (m64 <= TINY_MAX || m64 > SMALL_MAX) return;
+  const int m = (int)m64;
+  const int64_t o = S.off_at(set);
+  const unsigned long long* K = kin_base + o;
+  const uint32_t* V = vin_base + o;
+  const uint8_t* F = sw_base[set].flag;
+  uint32_t* out = out_base + o;
+  const int la = (int)h->n_lower, lb = (int)h->n_upper;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.y * CW;
+  if (blockIdx.y == 0 && threadIdx.x == 0) out_n_base[set] = la <= 1 ? 1 : (int64_t)(la - 1) + (lb - 1);
+  for (int v = blockIdx.y * CW + (threadIdx.x >> 5); v < m; v += warps) {
+    const uint8_t f = F[v];
+    if (!f) continue;
+    const unsigned long long kv = __ldg(K + v);
+    int rl = 0, ru = 0;
+    for (int a = lane; a < m; a += 32) {
+      const uint8_t fa = F[a];
+      const unsigned long long ka = __ldg(K + a);
+      if (fa && ka < kv) { rl += fa & 1; ru += fa >> 1; }
+    }
+    for (int off = 16; off; off >>= 1) {
+      rl += __shfl_xor_sync(FULL, rl, off);
+      ru += __shfl_xor_sync(FULL, ru, off);
+    }
+    if (lane == 0) {
+      const uint32_t iv = __ldg(V + v);
+      if (la <= 1) {  // every survivor has the same coordinates
+        out[0] = iv;
+      } else {
+        if ((f & 1) && rl < la - 1) out[rl] = iv;
+        if ((f & 2) && ru >= 1) out[(la - 1) + (lb - 1 - ru)] = iv;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 size_t small_hull_smem() {
@@ -441,6 +645,15 @@ size_t small_hull_smem() {
 
 cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which, const unsigned long long* keys,
                               const uint32_t* vals, SmallWs* sw, uint32_t* out, int64_t* out_n, cudaStream_t st) {
+  const unsigned nsets = (unsigned)S.S;
+  k_small_tiny<<<nsets, TB, 0, st>>>(S, gstatus, which, keys, vals, out, out_n);
+  if (S.S == 1) {  // the whole GPU on one set: a warp for every possible survivor
+    const unsigned gy = (unsigned)(SMALL_MAX / CW);
+    k_small_classify<<<dim3(1, gy), CW * 32, 0, st>>>(S, gstatus, which, keys, vals, sw);
+    k_small_rank<<<dim3(1, gy), CW * 32, 0, st>>>(S, gstatus, which, keys, vals, sw, out, out_n);
+    count_launches(3);
+    return cudaGetLastError();
+  }
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -450,12 +663,8 @@ cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which,
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  const unsigned nsets = (unsigned)S.S;
-  k_small_tiny<<<nsets, TB, 0, st>>>(S, gstatus, which, keys, vals, out, out_n);
   k_small_prep<<<nsets, SB, smem, st>>>(S, gstatus, which, keys, vals, sw, out, out_n);
-  // one set: a wide grid (one warp per candidate); a batch: a few blocks per set
-  const unsigned px = S.S == 1 ? (unsigned)(2 * SMALL_MAX / 8) : 8u;
-  k_small_prune<<<dim3(nsets, px), 256, 0, st>>>(sw);
+  k_small_prune<<<dim3(nsets, 8), 256, 0, st>>>(sw);
   k_small_emit<<<nsets, SB, 0, st>>>(S, sw, out, out_n);
   count_launches(4);
   return cudaGetLastError();

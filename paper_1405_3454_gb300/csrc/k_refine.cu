@@ -315,8 +315,22 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(Sets S, const uint32_t* gs
 cudaError_t launch_refine(const Sets& S, const uint32_t* gstatus, int64_t* tp, const unsigned long long* keys_in,
                           const uint32_t* vals_in, unsigned long long* keys_out, uint32_t* vals_out, int4* tri,
                           int64_t cap, cudaStream_t st) {
+  // one wave of resident blocks (the filter's triangle table limits it)
   const int sms = device_sm_count();
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + RT - 1) / RT, (int64_t)sms * 8));
+  static int occ_cache[64][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!occ_cache[dev][0]) {
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_refine_bins, RBLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_refine_filter, RBLOCK, 0);
+    occ_cache[dev][0] = std::max(a, 1);
+    occ_cache[dev][1] = std::max(b, 1);
+  }
+  const int64_t tiles = (cap + RT - 1) / RT;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * occ_cache[dev][0]));
+  const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * occ_cache[dev][1]));
   Tiles T;
   T.S = S.S;
   T.tp = S.S > 1 ? tp : nullptr;
@@ -327,7 +341,7 @@ cudaError_t launch_refine(const Sets& S, const uint32_t* gstatus, int64_t* tp, c
   }
   k_refine_bins<<<g, RBLOCK, 0, st>>>(S, T, gstatus, keys_in);
   k_refine_links<<<(unsigned)S.S, REFINE_BINS, 0, st>>>(S, gstatus, keys_in, tri);
-  k_refine_filter<<<g, RBLOCK, 0, st>>>(S, T, gstatus, keys_in, vals_in, keys_out, vals_out, tri);
+  k_refine_filter<<<gf, RBLOCK, 0, st>>>(S, T, gstatus, keys_in, vals_in, keys_out, vals_out, tri);
   count_launches(k);
   return cudaGetLastError();
 }
