@@ -482,6 +482,45 @@ __device__ __forceinline__ void ext_seed(const float* tmin, const float* tmax, f
   __syncwarp();
 }
 
+// A block's result for one set (consumer warps): the binary64 score of every
+// warp's candidate (one lane per direction), then an exact (score, index)
+// reduction over the warps, into out[0 .. ND).  Out of line: it runs once per
+// set and block, and keeps its registers out of the streaming loop.
+template <int ANG>
+__device__ __noinline__ void ext_block_result(const float* xy, const uint32_t* w_bidx, double* w_s64,
+                                              BlockBest* out) {
+  constexpr int ND = Dirs<ANG>::ND;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  consumers_sync();
+  if (lane < ND) {
+    const uint32_t i = w_bidx[warp * ND + lane];
+    double sc = -DBL_MAX;
+    if (i != NONE) {
+      const float2 p = load_point(xy, i);
+      sc = score64(ANG, lane, p.x, p.y);
+    }
+    w_s64[warp * ND + lane] = sc;
+  }
+  consumers_sync();
+  if (tid < ND) {
+    double bs = -DBL_MAX;
+    unsigned long long bk = 0;
+    uint32_t bi = NONE;
+    for (int w = 0; w < CONSUMERS / 32; ++w) {
+      const uint32_t i = w_bidx[w * ND + tid];
+      const double sc = w_s64[w * ND + tid];
+      const unsigned long long kk = dkey(sc);
+      if (i != NONE && (bi == NONE || kk > bk || (kk == bk && i < bi))) { bs = sc; bk = kk; bi = i; }
+    }
+    BlockBest r;
+    r.s = bs;
+    r.idx = bi;
+    r.pad_ = 0;
+    out[tid] = r;
+  }
+  consumers_sync();
+}
+
 // Blocks per SM the streaming search is compiled for (registers per thread).
 #ifndef EXT_MIN_BLOCKS
 #define EXT_MIN_BLOCKS 3
@@ -555,37 +594,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(S
         }
       }
     }
-    // this block's result for set s: the binary64 score of every warp's
-    // candidate (one lane per direction), then an exact (score, index)
-    // reduction over the warps, into slot (block + set)
-    consumers_sync();
-    if (lane < ND) {
-      const uint32_t i = w_bidx[warp][lane];
-      double sc = -DBL_MAX;
-      if (i != NONE) {
-        const float2 p = load_point(xy, i);
-        sc = score64(ANG, lane, p.x, p.y);
-      }
-      w_s64[warp][lane] = sc;
-    }
-    consumers_sync();
-    if (tid < ND) {
-      double bs = -DBL_MAX;
-      unsigned long long bk = 0;
-      uint32_t bi = NONE;
-      for (int w = 0; w < CONSUMERS / 32; ++w) {
-        const uint32_t i = w_bidx[w][tid];
-        const double sc = w_s64[w][tid];
-        const unsigned long long kk = dkey(sc);
-        if (i != NONE && (bi == NONE || kk > bk || (kk == bk && i < bi))) { bs = sc; bk = kk; bi = i; }
-      }
-      BlockBest r;
-      r.s = bs;
-      r.idx = bi;
-      r.pad_ = 0;
-      bres[((size_t)blockIdx.x + s) * ND + tid] = r;
-    }
-    consumers_sync();
+    ext_block_result<ANG>(xy, &w_bidx[0][0], &w_s64[0][0], bres + ((size_t)blockIdx.x + s) * ND);
   });
 }
 

@@ -126,7 +126,7 @@ struct WarpOut {
 // No point is read from memory twice.
 
 using FilterStream = StreamSmemT<2>;
-constexpr int QCAP = 288;  // >= 31 left over + 8 * 32 pushed per chunk
+constexpr int QCAP = 288;  // >= 31 left over + 8 * 32 pushed per chunk (a per-warp stack)
 
 struct Cells {
   const uint8_t* code8;    // GRID*GRID byte codes (global memory, L1-cached)
@@ -146,20 +146,28 @@ struct Cells {
   }
 };
 
+// Rare outcomes of the full test, out of line: a cell listing several edges,
+// or a float32 single-edge test inside its error bound (exact int64).
+__device__ __noinline__ unsigned full_test_rare(const Edge* E, const uint16_t* mask16, uint32_t code, int cell,
+                                                float x, float y) {
+  if (code == CELL_MULTI) return fails_any(E, __ldg(mask16 + cell), x, y);
+  const Edge& e = E[code - 1];
+  return 2 + (exact_left(e, __float2int_rn(x), __float2int_rn(y)) ? 0u : 1u);
+}
+
 // Full inside test of one point: cell lookup, float32 edge test(s), exact
-// escalation.  Returns 2 * escalations + (survives ? 1 : 0).
+// escalation.  Returns 2 * escalations + (survives ? 1 : 0).  The common
+// outcomes (inside cell, outside the grid, one edge decided in float32) take
+// no branch.
 __device__ __forceinline__ unsigned full_test(const Edge* E, const Cells& C, float x, float y) {
   int cell;
   const uint32_t code = C.code(x, y, cell);
-  if (code == 0) return 0;
-  if (code == 256) return 1;
-  if (code == CELL_MULTI) return fails_any(E, __ldg(C.mask16 + cell), x, y);
-  const int k = (int)code - 1;
-  const float4 c = *reinterpret_cast<const float4*>(&E[k].A);
-  const float s = fmaf(c.x, x, fmaf(c.y, y, c.z));
-  if (s > c.w) return 0;
-  if (s < -c.w) return 1;
-  return 2 + (exact_left(E[k], __float2int_rn(x), __float2int_rn(y)) ? 0u : 1u);
+  const float4 c = *reinterpret_cast<const float4*>(&E[(code - 1) & (MAXV - 1)].A);
+  const float sv = fmaf(c.x, x, fmaf(c.y, y, c.z));
+  const bool single = code - 1u < (uint32_t)(CELL_MULTI - 1);  // 1 .. 254
+  const bool undecided = single && !(sv > c.w) && !(sv < -c.w);
+  if (code == CELL_MULTI || undecided) return full_test_rare(E, C.mask16, code, cell, x, y);
+  return (code == 256u || (single && sv < -c.w)) ? 1u : 0u;
 }
 
 template <bool KEYS>
@@ -195,15 +203,14 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(Sets S, int64_t 
   O.count = 0;
   float2* qxy = s_qxy[warp];
   uint32_t* qi = s_qi[warp];
-  int qhead = 0, qtail = 0, qn = 0;  // warp-uniform ring state
+  int qn = 0;  // warp-uniform fill of the queue (used as a stack)
   unsigned esc = 0;
   bool all_survive = true;
   Cells C;
-  // Full test of `count` (<= 32) queued points, one per lane.
+  // Full test of the `count` (<= 32) most recently queued points, one per lane.
   auto drain = [&](int count) {
     const bool mine = lane < count;
-    int slot = qhead + lane;
-    if (slot >= QCAP) slot -= QCAP;
+    const int slot = qn - count + lane;
     float2 p = make_float2(0.0f, 0.0f);
     uint32_t i = 0;
     bool keep = false;
@@ -218,8 +225,6 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(Sets S, int64_t 
         keep = r & 1;
       }
     }
-    qhead += count;
-    if (qhead >= QCAP) qhead -= QCAP;
     qn -= count;
     O.push(keep, i, p.x, p.y);
   };
@@ -273,18 +278,12 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(Sets S, int64_t 
         const float dx = x - ccx, dy = y - ccy;
         const bool need = (j >> 1) * CONSUMERS < lim && !(fmaf(dx, dx, dy * dy) < cr2);
         const unsigned bal = __ballot_sync(FULL, need);
-        if (bal) {
-          if (need) {
-            int slot = qtail + __popc(bal & lt);
-            if (slot >= QCAP) slot -= QCAP;
-            qxy[slot] = make_float2(x, y);
-            qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
-          }
-          const int kq = __popc(bal);
-          qtail += kq;
-          if (qtail >= QCAP) qtail -= QCAP;
-          qn += kq;
+        const int slot = qn + __popc(bal & lt);
+        if (need) {
+          qxy[slot] = make_float2(x, y);
+          qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
         }
+        qn += __popc(bal);
       }
       __syncwarp();
       while (qn >= 32) drain(32);

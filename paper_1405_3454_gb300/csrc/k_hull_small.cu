@@ -41,8 +41,10 @@ constexpr int SB = 1024;      // threads
 constexpr int NCH = SMALL_NCH;  // chunks (one warp each)
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-__device__ __forceinline__ long long cr(long long ax, long long ay, long long bx, long long by) {
-  return ax * by - ay * bx;
+// Cross product of two difference vectors of lattice points within +-2^24
+// (32-bit components; one widening multiply per product).
+__device__ __forceinline__ long long cr(int ax, int ay, int bx, int by) {
+  return (long long)ax * by - (long long)ay * bx;
 }
 
 // Exclusive block scan of one int per thread; writes the total to *tot.
@@ -84,9 +86,9 @@ struct Pts {
 // lanes of one warp on the same instruction stream.
 __device__ int chunk_chain(Pts P, int lo, int hi, uint16_t* st, long long sg) {
   int n = 0;
-  long long x1 = 0, y1 = 0, x2 = 0, y2 = 0;
+  int x1 = 0, y1 = 0, x2 = 0, y2 = 0;
   for (int p = lo; p < hi; ++p) {
-    const long long px = P.x[p], py = P.y[p];
+    const int px = P.x[p], py = P.y[p];
     while (n >= 2) {
       const long long c = sg * cr(x1 - x2, y1 - y2, px - x2, py - y2);
       if (c > 0) break;

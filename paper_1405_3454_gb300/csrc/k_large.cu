@@ -65,9 +65,9 @@ __device__ __forceinline__ uint32_t digit(unsigned long long k, int pass) {
 }
 
 __device__ __forceinline__ long long cross_k(unsigned long long o, unsigned long long a, unsigned long long b) {
-  const long long ox = key_x(o), oy = key_y(o);
-  return ((long long)key_x(a) - ox) * ((long long)key_y(b) - oy) -
-         ((long long)key_y(a) - oy) * ((long long)key_x(b) - ox);
+  // differences of lattice coordinates within +-2^24 fit in 32 bits
+  const int ox = key_x(o), oy = key_y(o);
+  return (long long)(key_x(a) - ox) * (key_y(b) - oy) - (long long)(key_y(a) - oy) * (key_x(b) - ox);
 }
 
 // One monotone chain kept as an in-place stack K[base..base+n), V likewise.

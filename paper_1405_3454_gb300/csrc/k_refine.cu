@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(REFINE_BINS) k_refine_links(Sets S, const uint
   tri[2 * b + 1] = c;
 }
 
-__device__ __forceinline__ long long orient_ll(long long ax, long long ay, long long bx, long long by,
-                                               long long px, long long py) {
-  return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+// Exact orientation of (a, b, p) for lattice points within +-2^24: every
+// difference fits in 32 bits, every product is one widening multiply.
+__device__ __forceinline__ long long orient_ll(int ax, int ay, int bx, int by, int px, int py) {
+  return (long long)(bx - ax) * (py - ay) - (long long)(by - ay) * (px - ax);
 }
 
 // Pass 2: keep the survivors not strictly inside their bin's triangles;
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const
   const int64_t nt = T.total(S, gstatus);
   int cur = -1;
   WsHeader* h = nullptr;
-  long long ox = 0, oy = 0;
+  int ox = 0, oy = 0;
   float oxf = 0.0f, oyf = 0.0f;
   int64_t m = 0;
   const unsigned long long* kin = nullptr;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const
       bool keep = false;
       if (j < m) {
         const unsigned long long key = kv[u];
-        const long long px = key_x(key), py = key_y(key);
+        const int px = key_x(key), py = key_y(key);
         keep = true;
         const int b = bin_of((float)px - oxf, (float)py - oyf);
         const int4 a = s_tri[2 * b], c = s_tri[2 * b + 1];
