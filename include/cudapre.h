@@ -241,10 +241,11 @@ int32_t hull_abi_version(void);
 
 /* ---- Instrumentation (not part of the method) -------------------------- */
 
-/* Stages of one call, in launch order: domain check, extremes + polygon
- * (Steps 1-2), inside test + compaction (Step 3), sort of the survivors,
- * monotone chain of the survivors. */
-#define HULL_STAGES 5
+/* Stages of one call, in launch order: domain check (and batch set-up),
+ * the streaming extreme search (Step 1), the polygon of the extremes and
+ * its cell grid (Step 2), inside test + compaction (Step 3), the
+ * refinement round and the small-set hull, the large-set hull. */
+#define HULL_STAGES 6
 
 /* Opaque stage timer: CUDA events recorded on the call's stream at every
  * stage boundary (host objects; no device memory). */

@@ -39,8 +39,8 @@ ABI_SYMBOLS = (
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
     "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes", "hull_batch_ranges",
 )
-HULL_STAGES = 5
-STAGE_NAMES = ("validate", "extremes", "filter", "sort", "chain")
+HULL_STAGES = 6
+STAGE_NAMES = ("validate", "extremes", "polygon", "filter", "hull", "final")
 
 
 class HullOptions(ctypes.Structure):

@@ -43,13 +43,19 @@ namespace cudapre {
 namespace {
 thread_local hull_timer* g_timer = nullptr;
 
+}  // namespace
+
 // Marks boundary `b` (0..HULL_STAGES) of the current call.
-void mark(int b, cudaStream_t st) {
+void stage_mark(int b, cudaStream_t st) {
   hull_timer* t = g_timer;
   if (!t || t->calls >= t->cap) return;
   cudaEventRecord(t->ev[(size_t)t->calls * (HULL_STAGES + 1) + b], st);
   if (b == HULL_STAGES) ++t->calls;
 }
+
+namespace {
+
+void mark(int b, cudaStream_t st) { stage_mark(b, st); }
 
 constexpr int64_t MAX_N = 0xFFFFFFFFll;  // indices are uint32
 constexpr int64_t MAX_BLOCKS = 4096;     // per-block partials of the extreme search
@@ -174,10 +180,10 @@ hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& 
   const int64_t npairs = S.npairs_of(0);
   uint16_t* cells = reinterpret_cast<uint16_t*>(ws + L.cells);
   HULL_TRY(launch_extremes(S, npairs, o.angles, o.filter, &h->status, ws + L.blockres, cells, o.grid, ext_out,
-                           surv_idx, surv_key, st));
-  mark(2, st);
-  HULL_TRY(launch_filter(S, npairs, o.filter, &h->status, cells, surv_idx, surv_key, o.grid, st));
+                           surv_idx, surv_key, st));  // marks boundary 2 between its two kernels
   mark(3, st);
+  HULL_TRY(launch_filter(S, npairs, o.filter, &h->status, cells, surv_idx, surv_key, o.grid, st));
+  mark(4, st);
   return HULL_OK;
 }
 
@@ -252,8 +258,8 @@ hull_status hull_prefilter(const float* d_xy, int64_t n, void* d_ws, size_t ws_b
   s = run_prefilter(d_xy, n, ws, L, d_survivor_idx, nullptr, d_extreme_idx, o, st);
   if (s != HULL_OK) return s;
   s = cuda_status(launch_copy_count(reinterpret_cast<WsHeader*>(ws), d_n_survivors, st));
-  mark(4, st);
   mark(5, st);
+  mark(6, st);
   return s;
 }
 
@@ -305,9 +311,9 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   J.out_idx = d_hull_idx;
   J.out_n = d_n_hull;
   J.cap = cap;
-  HULL_TRY(launch_large(nullptr, nullptr, J, &h->bar_count, &h->status, st));
-  mark(4, st);
   mark(5, st);
+  HULL_TRY(launch_large(nullptr, nullptr, J, &h->bar_count, &h->status, st));
+  mark(6, st);
   return HULL_OK;
 }
 
@@ -367,10 +373,10 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
   mark(1, st);
   const int64_t pairs_bound = n_total / 2;
   HULL_TRY(launch_extremes(SS, pairs_bound, o.angles, o.filter, bstatus, ws + L.blockres, cells, o.grid, nullptr, va,
-                           ka, st));
-  mark(2, st);
-  HULL_TRY(launch_filter(SS, pairs_bound, o.filter, bstatus, cells, va, ka, o.grid, st));
+                           ka, st));  // marks boundary 2 between its two kernels
   mark(3, st);
+  HULL_TRY(launch_filter(SS, pairs_bound, o.filter, bstatus, cells, va, ka, o.grid, st));
+  mark(4, st);
   const int64_t cap = std::max<int64_t>(n_total, 1);
   const bool refine = o.refine != 0;
   unsigned long long* kin = ka;
@@ -388,11 +394,11 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
   LargeJob* jobs = reinterpret_cast<LargeJob*>(ws + L.jobs);
   HULL_TRY(launch_batch_jobs(SS, bstatus, which, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt),
                              reinterpret_cast<uint32_t*>(ws + L.cnt), hstage, hcnt, jobs, &bw->njobs, st));
+  mark(5, st);
   LargeJob none{};
   HULL_TRY(launch_large(jobs, &bw->njobs, none, &bw->bar_count, bstatus, st));
-  mark(4, st);
   HULL_TRY(launch_batch_emit(SS, bstatus, hcnt, hstage, d_hull_offsets, d_hull_idx, st));
-  mark(5, st);
+  mark(6, st);
   return HULL_OK;
 }
 

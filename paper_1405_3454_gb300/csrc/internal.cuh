@@ -187,6 +187,9 @@ int device_sm_count();
 
 // Process-wide count of kernels enqueued by this library (instrumentation).
 void count_launches(int k);
+// Stage boundary b of the current call for an attached stage timer
+// (instrumentation; nothing when no timer is attached).
+void stage_mark(int b, cudaStream_t st);
 
 // Launchers (one per translation unit); all enqueue on `st`.  `gstatus` is
 // the status word every step checks first (the header's for one set, the

@@ -521,9 +521,13 @@ __device__ __noinline__ void ext_block_result(const float* xy, const uint32_t* w
   consumers_sync();
 }
 
-// Blocks per SM the streaming search is compiled for (registers per thread).
+// Blocks per SM the streaming search is compiled for (registers per thread)
+// and the stages of its shared-memory ring.
 #ifndef EXT_MIN_BLOCKS
-#define EXT_MIN_BLOCKS 3
+#define EXT_MIN_BLOCKS 2
+#endif
+#ifndef EXT_STAGES
+#define EXT_STAGES 6
 #endif
 
 template <int ANG>
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(S
                                                                    BlockBest* bres) {
   constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
   extern __shared__ __align__(128) unsigned char dsm[];
-  using SS = StreamSmemT<3>;
+  using SS = StreamSmemT<EXT_STAGES>;
   SS& SM = *reinterpret_cast<SS*>(dsm);
   __shared__ __align__(16) float thr[ND];  // trigger thresholds in value space
   __shared__ float w_best[CONSUMERS / 32][ND];   // per-warp running best (score space)
@@ -895,7 +899,7 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
                                                   surv_key);                                             \
   } while (0)
   if (filter == HULL_FILTER_FP32) {
-    const size_t dsmem = sizeof(StreamSmemT<3>);
+    const size_t dsmem = sizeof(StreamSmemT<EXT_STAGES>);
     static bool attr[64][2] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -914,9 +918,11 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
     const auto gp = shape(occ);
     if (angles == HULL_ANGLES_CUMULATIVE) {
       k_extremes32<0><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
+      stage_mark(2, st);
       FIN(0);
     } else {
       k_extremes32<1><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
+      stage_mark(2, st);
       FIN(1);
     }
   } else {
@@ -924,9 +930,11 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
     const auto gp = shape(occ);
     if (angles == HULL_ANGLES_CUMULATIVE) {
       k_extremes64<0><<<(unsigned)gp.first, BLOCK, 0, st>>>(S, gp.second, gstatus, bres);
+      stage_mark(2, st);
       FIN(0);
     } else {
       k_extremes64<1><<<(unsigned)gp.first, BLOCK, 0, st>>>(S, gp.second, gstatus, bres);
+      stage_mark(2, st);
       FIN(1);
     }
   }

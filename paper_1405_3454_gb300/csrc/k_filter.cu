@@ -125,7 +125,14 @@ struct WarpOut {
 // test: cell lookup, then the float32 edge test(s) with exact escalation.
 // No point is read from memory twice.
 
-using FilterStream = StreamSmemT<2>;
+// Blocks per SM the inside test is compiled for, and its ring's stages.
+#ifndef FLT_MIN_BLOCKS
+#define FLT_MIN_BLOCKS 3
+#endif
+#ifndef FLT_STAGES
+#define FLT_STAGES 2
+#endif
+using FilterStream = StreamSmemT<FLT_STAGES>;
 constexpr int QCAP = 288;  // >= 31 left over + 8 * 32 pushed per chunk (a per-warp stack)
 
 struct Cells {
@@ -171,7 +178,7 @@ __device__ __forceinline__ unsigned full_test(const Edge* E, const Cells& C, flo
 }
 
 template <bool KEYS>
-__global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter32(Sets S, int64_t ppb, uint32_t* gstatus,
+__global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Sets S, int64_t ppb, uint32_t* gstatus,
                                                                  const uint16_t* __restrict__ cells_base,
                                                                  uint32_t* __restrict__ surv_idx,
                                                                  unsigned long long* __restrict__ surv_key) {
