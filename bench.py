@@ -271,6 +271,11 @@ def run_ours(args):
     for _ in range(2):
         step(exact)
     ms_exact = timed(step, exact, max(3, args.steps // 4))
+    # The paper's comparison (section 3, case (1) against case (2)): the same
+    # hull without the preprocessing (every point sorted and chained).
+    noprefilter = cp.Options(filter=cp.HULL_FILTER_FP32, no_prefilter=True)
+    step(noprefilter)
+    ms_np = timed(step, noprefilter, max(3, args.steps // 10))
     # Prefilter alone (Steps 1-3), both forms.
     for _ in range(2):
         prefilter_step(fp32)
@@ -408,6 +413,8 @@ def run_ours(args):
                        "parallelism": "independent set per GPU" if world > 1 else "single GPU"},
             "variants": {"plain_exact": {"value": world * n / (ms_exact * 1e-3) / 1e9, "ms_per_step": ms_exact},
                          "fp32_filtered": {"value": value, "ms_per_step": ms},
+                         "no_prefilter": {"value": job_rate(world, n, ms_np * 1e-3) / 1e9, "ms_per_step": ms_np,
+                                          "cudapre_speedup": ms_np / ms},
                          "prefilter_only": prefilter,
                          "batch": batch,
                          "serving": serving},

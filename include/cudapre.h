@@ -88,7 +88,11 @@ typedef struct hull_options {
   int32_t refine;        /* hull_compute: 1 (default) = a second, finer discard
                             round on the survivors before the final hull (same
                             result, less work); 0 = sort and chain every survivor */
-  int32_t reserved[10];  /* must be zero */
+  int32_t no_prefilter;  /* hull_compute: 0 (default) = the method; 1 = the hull of
+                            all points without Steps 1-3 (the paper's case (1),
+                            for comparison; same result).  Not for hull_prefilter
+                            or a batch (HULL_ERR_UNSUPPORTED). */
+  int32_t reserved[9];   /* must be zero */
 } hull_options;
 
 /* Device-side condition bits (hull_get_device_status). */

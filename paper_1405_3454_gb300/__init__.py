@@ -46,7 +46,7 @@ STAGE_NAMES = ("validate", "extremes", "polygon", "filter", "hull", "final")
 class HullOptions(ctypes.Structure):
     _fields_ = [("angles", ctypes.c_int32), ("filter", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("refine", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("no_prefilter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class HullStats(ctypes.Structure):
@@ -142,12 +142,14 @@ class Options:
     block: int = 0
     grid: int = 0
     refine: bool = True
+    no_prefilter: bool = False
 
     def c(self) -> HullOptions:
         o = HullOptions()
         load().hull_default_options(ctypes.byref(o))
         o.angles, o.filter, o.validate = int(self.angles), int(self.filter), int(bool(self.validate))
         o.block, o.grid, o.refine = int(self.block), int(self.grid), int(bool(self.refine))
+        o.no_prefilter = int(bool(self.no_prefilter))
         return o
 
 

@@ -137,7 +137,8 @@ hull_status check_opts(const hull_options* o) {
   if (o->filter != HULL_FILTER_EXACT && o->filter != HULL_FILTER_FP32) return HULL_ERR_UNSUPPORTED;
   if (o->block < 0 || o->grid < 0 || o->grid > MAX_BLOCKS) return HULL_ERR_INVALID_ARG;
   if (o->refine != 0 && o->refine != 1) return HULL_ERR_UNSUPPORTED;
-  for (int k = 0; k < 10; ++k) if (o->reserved[k] != 0) return HULL_ERR_UNSUPPORTED;
+  if (o->no_prefilter != 0 && o->no_prefilter != 1) return HULL_ERR_UNSUPPORTED;
+  for (int k = 0; k < 9; ++k) if (o->reserved[k] != 0) return HULL_ERR_UNSUPPORTED;
   return HULL_OK;
 }
 
@@ -250,6 +251,7 @@ hull_status hull_prefilter(const float* d_xy, int64_t n, void* d_ws, size_t ws_b
   if (s != HULL_OK) return s;
   if ((s = check_opts(opt)) != HULL_OK) return s;
   if (!d_n_survivors || (n > 0 && !d_survivor_idx)) return HULL_ERR_INVALID_ARG;
+  if (opt && opt->no_prefilter) return HULL_ERR_UNSUPPORTED;
   const Layout L = layout(n, false);
   if (ws_bytes < L.total) return HULL_ERR_WORKSPACE;
   const hull_options o = opts_or_default(opt);
@@ -280,15 +282,27 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   auto* va = reinterpret_cast<uint32_t*>(ws + L.vals_a);
   auto* kb = reinterpret_cast<unsigned long long*>(ws + L.keys_b);
   auto* vb = reinterpret_cast<uint32_t*>(ws + L.vals_b);
-  s = run_prefilter(d_xy, n, ws, L, va, ka, nullptr, o, st);
-  if (s != HULL_OK) return s;
+  if (o.no_prefilter) {
+    // the paper's case (1): every point goes to the hull stage
+    mark(0, st);
+    HULL_TRY(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
+    if (o.validate) HULL_TRY(launch_validate(d_xy, n, &h->status, st));
+    mark(1, st);
+    mark(2, st);
+    mark(3, st);
+    HULL_TRY(launch_all_keys(d_xy, n, h, ka, va, st));
+    mark(4, st);
+  } else {
+    s = run_prefilter(d_xy, n, ws, L, va, ka, nullptr, o, st);
+    if (s != HULL_OK) return s;
+  }
   const int64_t cap = std::max<int64_t>(n, 1);
   // The hull of the survivors.  With refinement the survivors in (ka, va)
   // are thinned into (kb, vb) first.  Sets up to SMALL_MAX points take the
   // one-block path; larger ones one cooperative launch of the device radix
   // sort (7 passes, ending in the other buffer) and the chunked chain (its
   // upper chains in the input).
-  const bool refine = o.refine != 0;
+  const bool refine = o.refine != 0 && !o.no_prefilter;
   const Sets S = single_set(d_xy, n, ws);
   unsigned long long* kin = ka;
   uint32_t* vin = va;
@@ -339,6 +353,7 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
   if (!d_starts && n_xy != n_total) return HULL_ERR_INVALID_ARG;
   hull_status s;
   if ((s = check_opts(opt)) != HULL_OK) return s;
+  if (opt && opt->no_prefilter) return HULL_ERR_UNSUPPORTED;
   const BatchLayout L = batch_layout(n_total, S);
   if (ws_bytes < L.total) return HULL_ERR_WORKSPACE;
   const hull_options o = opts_or_default(opt);

@@ -228,6 +228,10 @@ struct LargeJob {
 cudaError_t launch_large(const LargeJob* table, const int* njobs, const LargeJob& single, uint32_t* bar,
                          uint32_t* bar_status, cudaStream_t st);
 cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st);
+// Every point as a survivor (the paper's case (1), no preprocessing): its
+// key and index, and the count n.
+cudaError_t launch_all_keys(const float* xy, int64_t n, WsHeader* h, unsigned long long* keys, uint32_t* vals,
+                            cudaStream_t st);
 
 constexpr int REFINE_BINS = 1024;         // angular bins of the refinement round
 constexpr int SMALL_MAX = 8192;           // survivor sets up to this size: one-block hull

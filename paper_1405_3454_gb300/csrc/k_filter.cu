@@ -376,6 +376,18 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(Sets S, int6
   });
 }
 
+__global__ void k_all_keys(const float* __restrict__ xy, int64_t n, WsHeader* h, unsigned long long* __restrict__ keys,
+                           uint32_t* __restrict__ vals) {
+  if (*reinterpret_cast<volatile uint32_t*>(&h->status) != 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float2 p = __ldcs(reinterpret_cast<const float2*>(xy) + i);
+    keys[i] = point_key(__float2int_rn(p.x), __float2int_rn(p.y));
+    vals[i] = (uint32_t)i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) h->n_surv = (unsigned long long)n;
+}
+
 __global__ void k_copy_count(const WsHeader* h, int64_t* out) {
   *out = h->status ? 0 : (int64_t)h->n_surv;
 }
@@ -431,6 +443,14 @@ cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32
       k_filter_exact<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, surv_idx, surv_key);
     }
   }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_all_keys(const float* xy, int64_t n, WsHeader* h, unsigned long long* keys, uint32_t* vals,
+                            cudaStream_t st) {
+  const int64_t g = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 8));
+  k_all_keys<<<(unsigned)g, 256, 0, st>>>(xy, n, h, keys, vals);
   count_launches(1);
   return cudaGetLastError();
 }

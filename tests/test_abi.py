@@ -83,3 +83,6 @@ def test_argument_errors_without_gpu(lib):
     assert cp.hull_compute(P, 1000, P, 16, P, P, None, 0) == 3               # workspace too small
     o = cp.Options(angles=7)
     assert cp.hull_compute(P, 10, P, 1 << 30, P, P, o, 0) == 7               # unsupported option
+    # the no-prefilter comparator is for hull_compute only
+    assert cp.hull_prefilter(P, 10, P, 1 << 30, P, P, 0, cp.Options(no_prefilter=True), 0) == 7
+    assert cp.hull_batch(P, P, 1, 10, P, 1 << 30, P, P, cp.Options(no_prefilter=True), 0) == 7

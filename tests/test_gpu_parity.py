@@ -213,3 +213,20 @@ def test_workspace_reuse_back_to_back(gpu_lib):
         out, cnt, _ = gpu_lib.compute(to_dev(xy), gpu_lib.Options(refine=False), ws=ws)
         torch.cuda.synchronize()
         assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()
+
+
+@pytest.mark.parametrize("name,n", [("empty", 0), ("one", 1), ("tiny_square", 700), ("small_disk", 5000),
+                                    ("disk_100k", 100_000), ("square_1m", 1_000_000)])
+def test_no_prefilter_hull_equals_the_method(gpu_lib, name, n):
+    # the paper's case (1): the hull of all points with no preprocessing
+    # (every point goes to the small-set or the large-set hull) gives the
+    # same hull as the method
+    import torch
+    cp = gpu_lib
+    xy = synth.square(n, 31, 1 << 20) if "square" in name else synth.disk(n, 32)
+    d = torch.from_numpy(np.ascontiguousarray(xy)).cuda() if n else torch.zeros((0, 2), device="cuda")
+    out, cnt, _ = cp.compute(d, cp.Options(no_prefilter=True))
+    torch.cuda.synchronize()
+    got = cp.as_index(out, int(cnt.item())).tolist()
+    want = oracle.cudapre(xy)["hull"].tolist() if n else []
+    assert got == want
