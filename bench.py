@@ -149,12 +149,14 @@ def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def cpu_oracle_sample(n_sample: int, seed: int):
+def cpu_oracle_sample(n_sample: int, seed: int, xy=None):
     """The CPU oracle (as it stands, single-threaded) on the first n_sample
-    points of the workload's generator stream: (Gpoints/s, seconds)."""
+    points of the workload's generator stream (or on xy when given):
+    (Gpoints/s, seconds)."""
     import oracle
     import synth
-    xy = synth.disk(n_sample, seed)
+    if xy is None:
+        xy = synth.disk(n_sample, seed)
     oracle.cudapre(xy[:1024])  # load the library outside the timing
     t0 = time.perf_counter()
     oracle.cudapre(xy)
@@ -276,6 +278,40 @@ def run_ours(args):
     noprefilter = cp.Options(filter=cp.HULL_FILTER_FP32, no_prefilter=True)
     step(noprefilter)
     ms_np = timed(step, noprefilter, max(3, args.steps // 10))
+    # The float32-escalation workload: half Gaussian, half on or one unit
+    # inside the Gaussian half's polygon (its polygon from this library's own
+    # hull_prefilter, which the parity tests check against the oracle).
+    def gpu_polygon(g):
+        dg = torch.from_numpy(np.ascontiguousarray(g)).cuda()
+        _, _, _, pws = cp.prefilter(dg, fp32)
+        m, pxy, _ = cp.read_polygon(pws)
+        del dg, pws
+        return np.array(pxy, dtype=np.int64).reshape(-1, 2)[:m]
+
+    ne_host, _ = synth.near_edge_mix(n, SEED + 41 + rank, gpu_polygon)
+    ne_dev = torch.from_numpy(ne_host).cuda()
+    ne_out = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def ne_step(opt):
+        code = cp.hull_compute(ne_dev.data_ptr(), n, ws.data_ptr(), ws_bytes, ne_out.data_ptr(), cnt.data_ptr(), opt,
+                               sh)
+        if code:
+            raise cp.HullError(code, "hull_compute")
+
+    ne_step(fp32)
+    ms_ne = timed(ne_step, fp32, max(3, args.steps // 4))
+    ne_stats = cp.read_stats(ws)
+    ne_hull32 = ne_out[:int(cnt.item())].clone()
+    ne_step(exact)
+    ms_ne_exact = timed(ne_step, exact, 3)
+    ne_hull64 = ne_out[:int(cnt.item())].clone()
+    near_edge = {"value": job_rate(world, n, ms_ne * 1e-3) / 1e9, "ms_per_step": ms_ne,
+                 "exact_value": job_rate(world, n, ms_ne_exact * 1e-3) / 1e9, "exact_ms_per_step": ms_ne_exact,
+                 "escalations": ne_stats["n_escalated"], "escalation_rate": ne_stats["n_escalated"] / n,
+                 "survivors": ne_stats["n_survivors"], "hull_identical_to_exact": bool(torch.equal(ne_hull32, ne_hull64)),
+                 "workload": "2^28 points: 2^27 Gaussian (sigma 2^22, clipped to +-2^24) interleaved with 2^27 on or "
+                             "one unit inside the edges of the Gaussian half's polygon"}
+    del ne_dev, ne_out, ne_hull32, ne_hull64, ne_host
     # Prefilter alone (Steps 1-3), both forms.
     for _ in range(2):
         prefilter_step(fp32)
@@ -398,10 +434,9 @@ def run_ours(args):
 
     cpu = None
     if world == 1 and rank == 0 and not args.no_cpu:
-        ns = 1 << 25
-        v, dt = cpu_oracle_sample(ns, SEED)
+        v, dt = cpu_oracle_sample(n, SEED, host)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first 2^25 points of the same disk generator stream (%.1f s, single thread)" % dt}
+               "sample": "the whole workload: all %d points of the same disk (%.1f s, single thread)" % (n, dt)}
 
     if rank == 0:
         line = {
@@ -416,6 +451,7 @@ def run_ours(args):
                          "no_prefilter": {"value": job_rate(world, n, ms_np * 1e-3) / 1e9, "ms_per_step": ms_np,
                                           "cudapre_speedup": ms_np / ms},
                          "prefilter_only": prefilter,
+                         "near_edge": near_edge,
                          "batch": batch,
                          "serving": serving},
             "stages_ms_per_step": stages_out,
