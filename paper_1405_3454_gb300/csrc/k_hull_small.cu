@@ -539,46 +539,50 @@ __global__ void __launch_bounds__(CW * 32) k_small_classify(Sets S, const uint32
     const uint32_t iv = __ldg(V + v);
     const int vx = key_x(kv), vy = key_y(kv);
     // per lane: best incoming (lower: most CCW, upper: most CW) and best
-    // outgoing (lower: most CW, upper: most CCW) directions
-    int lix = 0, liy = 0, lox = 0, loy = 0, uix = 0, uiy = 0, uox = 0, uoy = 0;
-    bool hin = false, hout = false, dup = false;
+    // outgoing (lower: most CW, upper: most CCW) directions.  They start at
+    // unreachable directions that every real one beats (real components are
+    // within 2^25): (1, -2^26) is clockwise, (-1, 2^26) counter-clockwise of
+    // every direction of the half-plane; no branch depends on the lane.
+    constexpr int BIG = 1 << 26;
+    int lix = 1, liy = -BIG, uix = -1, uiy = BIG;  // incoming
+    int lox = -1, loy = BIG, uox = 1, uoy = -BIG;  // outgoing
+    bool dup = false;
     for (int a = lane; a < m; a += 32) {
       const unsigned long long ka = __ldg(K + a);
-      if (ka == kv) {
+      if (ka == kv) {  // equal coordinates (rare): the lowest index stands for them
         dup |= __ldg(V + a) < iv;
         continue;
       }
+      const bool before = ka < kv;
       const int ax = key_x(ka), ay = key_y(ka);
-      if (ka < kv) {  // incoming v - a
-        const int dx = vx - ax, dy = vy - ay;
-        if (!hin) { lix = uix = dx; liy = uiy = dy; hin = true; continue; }
-        if (crs(lix, liy, dx, dy) > 0) { lix = dx; liy = dy; }
-        if (crs(uix, uiy, dx, dy) < 0) { uix = dx; uiy = dy; }
-      } else {        // outgoing a - v
-        const int dx = ax - vx, dy = ay - vy;
-        if (!hout) { lox = uox = dx; loy = uoy = dy; hout = true; continue; }
-        if (crs(lox, loy, dx, dy) < 0) { lox = dx; loy = dy; }
-        if (crs(uox, uoy, dx, dy) > 0) { uox = dx; uoy = dy; }
+      // incoming v - a (a before v) or outgoing a - v (a after v)
+      const int dx = before ? vx - ax : ax - vx, dy = before ? vy - ay : ay - vy;
+      const int bl_x = before ? lix : lox, bl_y = before ? liy : loy;
+      const int bu_x = before ? uix : uox, bu_y = before ? uiy : uoy;
+      // lower: incoming keeps the most CCW, outgoing the most CW (upper: mirrored)
+      const long long cl = crs(bl_x, bl_y, dx, dy), cu = crs(bu_x, bu_y, dx, dy);
+      const bool tl = before ? cl > 0 : cl < 0, tu = before ? cu < 0 : cu > 0;
+      if (before) {
+        lix = tl ? dx : lix; liy = tl ? dy : liy;
+        uix = tu ? dx : uix; uiy = tu ? dy : uiy;
+      } else {
+        lox = tl ? dx : lox; loy = tl ? dy : loy;
+        uox = tu ? dx : uox; uoy = tu ? dy : uoy;
       }
     }
     for (int off = 16; off; off >>= 1) {
-      const bool oin = __shfl_xor_sync(FULL, hin, off), oout = __shfl_xor_sync(FULL, hout, off);
       int x1 = __shfl_xor_sync(FULL, lix, off), y1 = __shfl_xor_sync(FULL, liy, off);
-      int x2 = __shfl_xor_sync(FULL, uix, off), y2 = __shfl_xor_sync(FULL, uiy, off);
-      if (oin) {
-        if (!hin || crs(lix, liy, x1, y1) > 0) { lix = x1; liy = y1; }
-        if (!hin || crs(uix, uiy, x2, y2) < 0) { uix = x2; uiy = y2; }
-      }
+      if (crs(lix, liy, x1, y1) > 0) { lix = x1; liy = y1; }
+      x1 = __shfl_xor_sync(FULL, uix, off); y1 = __shfl_xor_sync(FULL, uiy, off);
+      if (crs(uix, uiy, x1, y1) < 0) { uix = x1; uiy = y1; }
       x1 = __shfl_xor_sync(FULL, lox, off); y1 = __shfl_xor_sync(FULL, loy, off);
-      x2 = __shfl_xor_sync(FULL, uox, off); y2 = __shfl_xor_sync(FULL, uoy, off);
-      if (oout) {
-        if (!hout || crs(lox, loy, x1, y1) < 0) { lox = x1; loy = y1; }
-        if (!hout || crs(uox, uoy, x2, y2) > 0) { uox = x2; uoy = y2; }
-      }
-      hin |= oin;
-      hout |= oout;
+      if (crs(lox, loy, x1, y1) < 0) { lox = x1; loy = y1; }
+      x1 = __shfl_xor_sync(FULL, uox, off); y1 = __shfl_xor_sync(FULL, uoy, off);
+      if (crs(uox, uoy, x1, y1) > 0) { uox = x1; uoy = y1; }
       dup |= __shfl_xor_sync(FULL, dup, off);
     }
+    // no point before (after) v: the incoming (outgoing) best is still its start
+    const bool hin = !(lix == 1 && liy == -BIG), hout = !(lox == -1 && loy == BIG);
     if (lane == 0) {
       uint8_t f = 0;
       if (!dup) {

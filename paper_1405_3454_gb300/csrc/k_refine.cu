@@ -238,24 +238,22 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const
       const int64_t j = j0 + u * RBLOCK + tid;
       bool keep = false;
       if (j < m) {
+        // One triangle (O, A, B) per bin and side, chosen without branching:
+        // with a winner W, (O, L, W) on the L side of the ray O->W and
+        // (O, W, R) on the other; without one, (O, L, R).  p is dropped iff
+        // it is strictly inside (all three orientations positive); a point
+        // on the ray O->W has a zero orientation and stays.
         const unsigned long long key = kv[u];
         const int px = key_x(key), py = key_y(key);
-        keep = true;
         const int b = bin_of((float)px - oxf, (float)py - oyf);
         const int4 a = s_tri[2 * b], c = s_tri[2 * b + 1];
-        if (c.z & 1) {
-          if (c.z & 2) {
-            const long long ow = orient_ll(ox, oy, a.z, a.w, px, py);
-            if (ow < 0) {  // the L side of ray O->W: triangle (O, L, W)
-              keep = !(orient_ll(ox, oy, a.x, a.y, px, py) > 0 && orient_ll(a.x, a.y, a.z, a.w, px, py) > 0);
-            } else if (ow > 0) {  // triangle (O, W, R)
-              keep = !(orient_ll(a.z, a.w, c.x, c.y, px, py) > 0 && orient_ll(c.x, c.y, ox, oy, px, py) > 0);
-            }
-          } else {  // empty bin: triangle (O, L, R)
-            keep = !(orient_ll(ox, oy, a.x, a.y, px, py) > 0 && orient_ll(a.x, a.y, c.x, c.y, px, py) > 0 &&
-                     orient_ll(c.x, c.y, ox, oy, px, py) > 0);
-          }
-        }
+        const bool has_w = (c.z & 2) != 0;
+        const bool l_side = has_w && orient_ll(ox, oy, a.z, a.w, px, py) < 0;
+        const int ax_ = has_w && !l_side ? a.z : a.x, ay_ = has_w && !l_side ? a.w : a.y;
+        const int bx_ = has_w && l_side ? a.z : c.x, by_ = has_w && l_side ? a.w : c.y;
+        const bool inside = orient_ll(ox, oy, ax_, ay_, px, py) > 0 && orient_ll(ax_, ay_, bx_, by_, px, py) > 0 &&
+                            orient_ll(bx_, by_, ox, oy, px, py) > 0;
+        keep = !((c.z & 1) && inside);
       }
       const unsigned bal = __ballot_sync(FULL, keep);
       if (bal) {
