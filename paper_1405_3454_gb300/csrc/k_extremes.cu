@@ -879,7 +879,9 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
   // blocks and pairs per block: at most one wave of resident blocks, each
   // share a whole number of chunks
   auto shape = [&](int occ) {
-    int64_t G = grid > 0 ? grid : (int64_t)device_sm_count() * std::max(occ, 1);
+    const int64_t resident = (int64_t)device_sm_count() * std::max(occ, 1);
+    int64_t G = grid > 0 ? grid : resident * stream_waves(S.S, npairs, resident);
+    G = std::min<int64_t>(G, MAX_STREAM_BLOCKS);
     G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
     int64_t ppb = (npairs + G - 1) / G;
     ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;

@@ -196,7 +196,9 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
   const bool dead = *reinterpret_cast<volatile uint32_t*>(gstatus) != 0;
   stream_init(SM);
   const int64_t P = S.pp_at(S.S);
-  const int64_t v0 = (int64_t)blockIdx.x * ppb;
+  // blocks take their shares last-to-first: the first ones to run read what
+  // the extreme search read last (still in L2)
+  const int64_t v0 = (int64_t)(gridDim.x - 1 - blockIdx.x) * ppb;
   const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
   // Chunks run last-to-first: the extreme search streamed each block's range
   // first-to-last, so the tail of every range is still in L2.
@@ -321,7 +323,9 @@ __global__ void __launch_bounds__(STREAM_THREADS, 3) k_filter_exact(Sets S, int6
   const bool dead = *reinterpret_cast<volatile uint32_t*>(gstatus) != 0;
   stream_init(SM);
   const int64_t P = S.pp_at(S.S);
-  const int64_t v0 = (int64_t)blockIdx.x * ppb;
+  // blocks take their shares last-to-first: the first ones to run read what
+  // the extreme search read last (still in L2)
+  const int64_t v0 = (int64_t)(gridDim.x - 1 - blockIdx.x) * ppb;
   const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
   if (warp == PRODUCER_WARP) {
     stream_produce_sets(SM, S, v0, v1, true, gstatus);
@@ -393,7 +397,7 @@ __global__ void k_copy_count(const WsHeader* h, int64_t* out) {
 }
 
 template <class K>
-cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npairs, int grid, int64_t& G,
+cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npairs, int grid, int sets, int64_t& G,
                           int64_t& ppb) {
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
@@ -403,7 +407,9 @@ cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npair
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, STREAM_THREADS, dsmem);
   occ = std::max(occ, 1);
-  G = grid > 0 ? grid : (int64_t)device_sm_count() * occ;
+  const int64_t resident = (int64_t)device_sm_count() * occ;
+  G = grid > 0 ? grid : resident * stream_waves(sets, npairs, resident);
+  G = std::min<int64_t>(G, MAX_STREAM_BLOCKS);
   G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
   ppb = (npairs + G - 1) / G;
   ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;
@@ -428,18 +434,18 @@ cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32
   const size_t ds = sizeof(FilterStream);
   if (filter == HULL_FILTER_FP32) {
     if (keys) {
-      if ((e = stream_launch(k_filter32<true>, attr[dev][0], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      if ((e = stream_launch(k_filter32<true>, attr[dev][0], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess) return e;
       k_filter32<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key);
     } else {
-      if ((e = stream_launch(k_filter32<false>, attr[dev][1], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      if ((e = stream_launch(k_filter32<false>, attr[dev][1], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess) return e;
       k_filter32<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key);
     }
   } else {
     if (keys) {
-      if ((e = stream_launch(k_filter_exact<true>, attr[dev][2], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      if ((e = stream_launch(k_filter_exact<true>, attr[dev][2], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess) return e;
       k_filter_exact<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, surv_idx, surv_key);
     } else {
-      if ((e = stream_launch(k_filter_exact<false>, attr[dev][3], ds, npairs, grid, G, ppb)) != cudaSuccess) return e;
+      if ((e = stream_launch(k_filter_exact<false>, attr[dev][3], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess) return e;
       k_filter_exact<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, surv_idx, surv_key);
     }
   }

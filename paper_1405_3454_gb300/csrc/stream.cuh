@@ -10,6 +10,8 @@
 // timeout the kernel records HULL_DEVICE_TIMEOUT and stops streaming.
 #pragma once
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace cudapre {
@@ -19,6 +21,19 @@ constexpr int PRODUCER_WARP = CONSUMERS / 32;
 constexpr int STREAM_THREADS = CONSUMERS + 32;
 constexpr int CHUNK = 4 * CONSUMERS;         // pairs per stage (4 per consumer thread)
 constexpr long long WAIT_LIMIT_CYCLES = 1ll << 31;  // about one second
+// A large batch's streaming passes launch up to BATCH_WAVES waves of resident
+// blocks: the block scheduler then hands the shares out as SMs free up, which
+// evens out sets of unequal cost per point.  Every block keeps at least
+// WAVE_MIN_CHUNKS chunks; one set takes one wave (equal cost per point).
+constexpr int BATCH_WAVES = 4;
+constexpr int64_t WAVE_MIN_CHUNKS = 32;
+constexpr int64_t MAX_STREAM_BLOCKS = 4096;  // partial-result slots per call
+
+inline int stream_waves(int sets, int64_t npairs, int64_t resident_blocks) {
+  if (sets <= 1) return 1;
+  const int64_t w = npairs / (resident_blocks * WAVE_MIN_CHUNKS * CHUNK);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(BATCH_WAVES, w));
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
