@@ -702,8 +702,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
   static_assert(FIN_THREADS % 32 == 0 && FIN_THREADS <= 1024, "whole warps");
   constexpr int ND = Dirs<ANG>::ND;
   __shared__ uint32_t s_ext[NSLOT];
-  __shared__ long long s_ax[MAXV][GRID], s_by[MAXV][GRID];  // per edge: min of A x per column, B y per row
-  __shared__ long long s_c[MAXV], s_span[MAXV];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int set = blockIdx.x;
   WsHeader* h = S.h(set);
@@ -793,52 +791,106 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
       }
     }
   }
-  // The cell grid.  For edge k the orientation is A x + B y + C (exact
-  // int64); its minimum over a cell is the minimum of A x over the cell's
-  // columns plus that of B y over its rows plus C (corners), likewise the
-  // maximum.  Bit k of a cell's mask: some point of the cell may fail edge
-  // k; a cell entirely outside edge k keeps only bit k.  Byte code: 0 inside,
-  // k + 1 only edge k, CELL_MULTI several edges.
   FSTAMP(3);
-  const Poly& P = h->poly;
-  const int m = P.m;
+  // Sets below GRID_MIN_POINTS use one cell listing every edge (the cell
+  // grid of larger sets is built by k_cells).
+  const int m = h->poly.m;
   if (dead || m < 3) return;
-  if (!grid_on) {
-    if (tid == 0) {
-      cells[0] = (uint16_t)((1u << m) - 1u);
-      reinterpret_cast<uint8_t*>(cells + GRID * GRID)[0] = (uint8_t)CELL_MULTI;
-    }
-    return;
-  }
-  for (int t = tid; t < m * GRID; t += FIN_THREADS) {
-    const int k = t / GRID, c = t % GRID;
-    const Edge& e = P.e[k];
-    const long long A = -(long long)e.dy, B = e.dx;
-    const long long xa = (long long)P.gx0 + ((long long)c << P.kx), xb = xa + (1ll << P.kx) - 1;
-    const long long ya = (long long)P.gy0 + ((long long)c << P.ky), yb = ya + (1ll << P.ky) - 1;
-    s_ax[k][c] = min(A * xa, A * xb);
-    s_by[k][c] = min(B * ya, B * yb);
-    if (c == 0) {
-      s_c[k] = (long long)e.dy * e.ax - (long long)e.dx * e.ay;
-      // max - min over a cell: |A| (2^kx - 1) + |B| (2^ky - 1)
-      s_span[k] = (A < 0 ? -A : A) * ((1ll << P.kx) - 1) + (B < 0 ? -B : B) * ((1ll << P.ky) - 1);
-    }
-  }
-  __syncthreads();
-  FSTAMP(4);
-  uint8_t* code8 = reinterpret_cast<uint8_t*>(cells + GRID * GRID);
-  for (int c = tid; c < GRID * GRID; c += FIN_THREADS) {
-    const int cx = c & (GRID - 1), cy = c >> GRID_LOG;
-    uint32_t mask = 0;
-    for (int k = 0; k < m; ++k) {
-      const long long mn = s_ax[k][cx] + s_by[k][cy] + s_c[k];
-      if (mn + s_span[k] <= 0) { mask = 1u << k; break; }  // the cell's maximum
-      if (mn <= 0) mask |= 1u << k;
-    }
-    cells[c] = (uint16_t)mask;
-    code8[c] = mask == 0 ? 0 : ((mask & (mask - 1)) == 0 ? (uint8_t)__ffs(mask) : (uint8_t)CELL_MULTI);
+  if (!grid_on && tid == 0) {
+    cells[0] = (uint16_t)((1u << m) - 1u);
+    reinterpret_cast<uint8_t*>(cells + GRID * GRID)[0] = (uint8_t)CELL_MULTI;
   }
   FSTAMP(5);
+}
+
+// ----------------------------------------------------------------------------
+// The cell grid of the inside test, in groups of CELL_ROWS rows spread over
+// the blocks of a set.  For edge k the orientation is A x + B y + C (exact
+// int64); its minimum over a cell is the minimum of A x over the cell's
+// columns plus that of B y over its rows plus C (corners), likewise the
+// maximum.  Bit k of a cell's mask: some point of the cell may fail edge k;
+// a cell entirely outside edge k keeps only bit k.  Byte code: 0 inside,
+// k + 1 only edge k, CELL_MULTI several edges.
+constexpr int CELL_ROW_BLOCKS = 16;
+constexpr int CELL_ROWS = GRID / CELL_ROW_BLOCKS;
+constexpr int CELL_THREADS = 256;
+
+__global__ void __launch_bounds__(CELL_THREADS) k_cells(Sets S, const uint32_t* gstatus, uint16_t* cells_base) {
+  // blockIdx.y takes every gridDim.y-th group of CELL_ROWS rows
+  __shared__ long long s_ax[MAXV][GRID];       // per edge: min of A x per column
+  __shared__ long long s_by[MAXV][CELL_ROWS];  // per edge: min of B y per row (this block's rows)
+  __shared__ long long s_c[MAXV], s_span[MAXV];
+  __shared__ int s_ra[CELL_ROWS], s_rb[CELL_ROWS];  // per row: columns inside every edge
+  const int set = blockIdx.x, tid = threadIdx.x;
+  const WsHeader* h = S.h(set);
+  if (*reinterpret_cast<const volatile uint32_t*>(gstatus) || h->status) return;
+  if (S.n_of(set) < GRID_MIN_POINTS) return;  // one cell listing every edge (finishing kernel)
+  const Poly& P = h->poly;
+  const int m = P.m;
+  if (m < 3) return;
+  uint16_t* cells = cells_base + (size_t)set * (CELL_BYTES / 2);
+  const int kx = P.kx, ky = P.ky;
+  for (int t = tid; t < m * GRID; t += CELL_THREADS) {
+    const int k = t / GRID, c = t % GRID;
+    const Edge& e = P.e[k];
+    const long long A = -(long long)e.dy;
+    const long long xa = (long long)P.gx0 + ((long long)c << kx), xb = xa + (1ll << kx) - 1;
+    s_ax[k][c] = min(A * xa, A * xb);
+    if (c == 0) {
+      const long long B = e.dx;
+      s_c[k] = (long long)e.dy * e.ax - (long long)e.dx * e.ay;
+      // max - min over a cell: |A| (2^kx - 1) + |B| (2^ky - 1)
+      s_span[k] = (A < 0 ? -A : A) * ((1ll << kx) - 1) + (B < 0 ? -B : B) * ((1ll << ky) - 1);
+    }
+  }
+  for (int r0 = blockIdx.y * CELL_ROWS; r0 < GRID; r0 += gridDim.y * CELL_ROWS) {
+    __syncthreads();
+    for (int t = tid; t < m * CELL_ROWS; t += CELL_THREADS) {
+      const int k = t / CELL_ROWS, row = t % CELL_ROWS;
+      const long long B = P.e[k].dx;
+      const long long ya = (long long)P.gy0 + ((long long)(r0 + row) << ky), yb = ya + (1ll << ky) - 1;
+      s_by[k][row] = min(B * ya, B * yb);
+    }
+    if (tid < CELL_ROWS) { s_ra[tid] = 0; s_rb[tid] = GRID - 1; }
+    __syncthreads();
+    // Per row, the columns whose cells lie strictly inside every edge: the row
+    // term is fixed and the column term min(A x) is monotone in the column
+    // (increasing for A > 0, decreasing for A < 0), so "inside edge k" is a
+    // half-line of columns, found by binary search; the row's interval is
+    // their intersection.  Cells in it get code 0 at once.
+    for (int t = tid; t < m * CELL_ROWS; t += CELL_THREADS) {
+      const int k = t / CELL_ROWS, row = t % CELL_ROWS;
+      const long long A = -(long long)P.e[k].dy;
+      const long long rb = s_by[k][row] + s_c[k];
+      if (A == 0) {
+        if (s_ax[k][0] + rb <= 0) atomicMax(&s_ra[row], GRID);  // the whole row may fail edge k
+      } else if (A > 0) {  // inside for columns >= the first passing one
+        int lo = 0, hi = GRID;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (s_ax[k][mid] + rb > 0) hi = mid; else lo = mid + 1; }
+        atomicMax(&s_ra[row], lo);
+      } else {             // inside for columns <= the last passing one
+        int lo = -1, hi = GRID - 1;
+        while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (s_ax[k][mid] + rb > 0) lo = mid; else hi = mid - 1; }
+        atomicMin(&s_rb[row], lo);
+      }
+    }
+    __syncthreads();
+    uint8_t* code8 = reinterpret_cast<uint8_t*>(cells + GRID * GRID);
+    for (int t = tid; t < CELL_ROWS * GRID; t += CELL_THREADS) {
+      const int cx = t & (GRID - 1), row = t >> GRID_LOG;
+      const int c = (r0 + row) * GRID + cx;
+      uint32_t mask = 0;
+      if (cx < s_ra[row] || cx > s_rb[row]) {
+        for (int k = 0; k < m; ++k) {
+          const long long mn = s_ax[k][cx] + s_by[k][row] + s_c[k];
+          if (mn + s_span[k] <= 0) { mask = 1u << k; break; }  // the cell's maximum
+          if (mn <= 0) mask |= 1u << k;
+        }
+      }
+      cells[c] = (uint16_t)mask;
+      code8[c] = mask == 0 ? 0 : ((mask & (mask - 1)) == 0 ? (uint8_t)__ffs(mask) : (uint8_t)CELL_MULTI);
+    }
+  }
 }
 
 // Domain check (finite, integer-valued, |v| <= 2^24).
@@ -941,7 +993,9 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
     }
   }
 #undef FIN
-  count_launches(2);
+  // one set: its rows over CELL_ROW_BLOCKS blocks; a batch: one block per set
+  k_cells<<<dim3(nsets, S.S == 1 ? CELL_ROW_BLOCKS : 1), CELL_THREADS, 0, st>>>(S, gstatus, cells);
+  count_launches(3);
   return cudaGetLastError();
 }
 
