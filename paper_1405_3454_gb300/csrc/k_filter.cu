@@ -76,7 +76,10 @@ struct Tester<HULL_FILTER_EXACT> {
 // memory, filled while the point's coordinates are still in registers; a full
 // buffer is flushed by its warp with one global atomic and coalesced stores.
 // No block-wide barrier in the streaming loop.
-constexpr int WBUF = 128;
+#ifndef FLT_WBUF
+#define FLT_WBUF 256
+#endif
+constexpr int WBUF = FLT_WBUF;
 
 template <bool KEYS>
 struct WarpOut {
@@ -133,7 +136,11 @@ struct WarpOut {
 #define FLT_STAGES 2
 #endif
 using FilterStream = StreamSmemT<FLT_STAGES>;
-constexpr int QCAP = 288;  // >= 31 left over + 8 * 32 pushed per chunk (a per-warp stack)
+// Points per thread between two drains of the queue (8 = once per chunk).
+#ifndef FLT_DRAIN_POINTS
+#define FLT_DRAIN_POINTS 4
+#endif
+constexpr int QCAP = 31 + 32 * FLT_DRAIN_POINTS;  // left over + pushed between drains (a per-warp stack)
 
 struct Cells {
   const uint8_t* code8;    // GRID*GRID byte codes (global memory, L1-cached)
@@ -282,20 +289,23 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
       const uint32_t i0 = ibase + 2u * (uint32_t)f;
       const int lim = cnt - tid;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
-        const float dx = x - ccx, dy = y - ccy;
-        const bool need = (j >> 1) * CONSUMERS < lim && !(fmaf(dx, dx, dy * dy) < cr2);
-        const unsigned bal = __ballot_sync(FULL, need);
-        const int slot = qn + __popc(bal & lt);
-        if (need) {
-          qxy[slot] = make_float2(x, y);
-          qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+      for (int j0 = 0; j0 < 8; j0 += FLT_DRAIN_POINTS) {
+#pragma unroll
+        for (int j = j0; j < j0 + FLT_DRAIN_POINTS; ++j) {
+          const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
+          const float dx = x - ccx, dy = y - ccy;
+          const bool need = (j >> 1) * CONSUMERS < lim && !(fmaf(dx, dx, dy * dy) < cr2);
+          const unsigned bal = __ballot_sync(FULL, need);
+          const int slot = qn + __popc(bal & lt);
+          if (need) {
+            qxy[slot] = make_float2(x, y);
+            qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+          }
+          qn += __popc(bal);
         }
-        qn += __popc(bal);
+        __syncwarp();
+        while (qn >= 32) drain(32);
       }
-      __syncwarp();
-      while (qn >= 32) drain(32);
     }
     // finish the set: queued points, buffered survivors, counters
     __syncwarp();
