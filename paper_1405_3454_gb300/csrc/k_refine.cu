@@ -35,7 +35,8 @@ __device__ __forceinline__ int bin_of(float qx, float qy) {
   return min(max(b, 0), REFINE_BINS - 1);
 }
 
-constexpr int RT = 4 * RBLOCK;  // survivors per work tile (4 per thread)
+constexpr int RU = 8;            // survivors per thread per work tile
+constexpr int RT = RU * RBLOCK;  // survivors per work tile
 
 // Work tiles over the sets' survivor counts: tile t of set s covers its
 // survivors [(t - tp[s]) RT, ...).  One set: tp == null and the tiles of set
@@ -97,11 +98,11 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_bins(Sets S, Tiles T, const u
     }
     if (!on) continue;
     const int64_t j0 = (t - T.first(s)) * RT + threadIdx.x;
-    unsigned long long kv[4];
+    unsigned long long kv[RU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) kv[u] = j0 + u * RBLOCK < m ? keys[j0 + u * RBLOCK] : 0ull;
+    for (int u = 0; u < RU; ++u) kv[u] = j0 + u * RBLOCK < m ? keys[j0 + u * RBLOCK] : 0ull;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < RU; ++u) {
       const int64_t j = j0 + u * RBLOCK;
       if (j < m) {
         const float qx = (float)key_x(kv[u]) - ox, qy = (float)key_y(kv[u]) - oy;
@@ -227,14 +228,14 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const
     // 4 independent loads in flight per thread; a warp handles 4 x 32
     // consecutive survivors
     const int64_t j0 = (t - T.first(s)) * RT;
-    unsigned long long kv[4];
+    unsigned long long kv[RU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < RU; ++u) {
       const int64_t j = j0 + u * RBLOCK + tid;
       kv[u] = j < m ? kin[j] : 0ull;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < RU; ++u) {
       const int64_t j = j0 + u * RBLOCK + tid;
       bool keep = false;
       if (j < m) {
