@@ -272,6 +272,14 @@ hull_status hull_timer_read(hull_timer* t, float* h_ms, int32_t* h_calls);
 /* Number of kernels this library has enqueued in this process so far. */
 int64_t hull_launch_count(void);
 
+/* Test of the timeout path (no counterpart in the paper): one kernel waits,
+ * with a limit of limit_cycles GPU cycles (1 .. 2^31), on a barrier that
+ * nothing releases; the wait gives up, records HULL_DEVICE_TIMEOUT in d_ws's
+ * status word (cleared first) and the kernel returns.  The context stays
+ * usable; hull_get_device_status then reports HULL_ERR_TIMEOUT.  d_ws: any
+ * workspace (256-byte aligned). */
+hull_status hull_selftest_wait(void* d_ws, int64_t limit_cycles, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,7 @@ ABI_SYMBOLS = (
     "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version", "hull_read_stats",
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
     "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes", "hull_batch_ranges",
+    "hull_selftest_wait",
 )
 HULL_STAGES = 6
 STAGE_NAMES = ("validate", "extremes", "polygon", "filter", "hull", "final")
@@ -118,6 +119,8 @@ def load(path: str | None = None):
     lib.hull_batch.restype = st
     lib.hull_batch_ranges.argtypes = [P, i64, P, P, ctypes.c_int32, i64, P, sz, P, P, OP, P]
     lib.hull_batch_ranges.restype = st
+    lib.hull_selftest_wait.argtypes = [P, i64, P]
+    lib.hull_selftest_wait.restype = st
     _lib = lib
     return lib
 
@@ -345,6 +348,12 @@ def device_status(ws, stream=None):
     bits = ctypes.c_uint32(0)
     code = load().hull_get_device_status(_ptr(ws), ctypes.byref(bits), _stream_handle(stream))
     return int(code), int(bits.value)
+
+
+def selftest_wait(ws, limit_cycles: int = 1 << 20, stream=None):
+    """Run one bounded device wait that nothing releases (a test of the
+    timeout path); the workspace's status then reads HULL_ERR_TIMEOUT."""
+    _check(load().hull_selftest_wait(_ptr(ws), int(limit_cycles), _stream_handle(stream)), "hull_selftest_wait")
 
 
 def constants():

@@ -417,6 +417,16 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
   return HULL_OK;
 }
 
+hull_status hull_selftest_wait(void* d_ws, int64_t limit_cycles, void* stream) {
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return HULL_ERR_INVALID_ARG;
+  if (limit_cycles < 1 || limit_cycles > ((int64_t)1 << 31)) return HULL_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t* status = reinterpret_cast<uint32_t*>(d_ws);  // the first word of every workspace
+  HULL_TRY(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
+  HULL_TRY(launch_wait_selftest(status, limit_cycles, st));
+  return HULL_OK;
+}
+
 hull_status hull_read_counters(const void* d_ws, int64_t* h_n_survivors, int64_t* h_n_escalated,
                                void* stream) {
   if (!d_ws) return HULL_ERR_INVALID_ARG;

@@ -274,6 +274,9 @@ __host__ __device__ inline size_t tiles_at(int64_t off, int s) { return 256 * (s
 __host__ __device__ inline size_t chains_at(int64_t off, int s) { return 4 * (size_t)(off / CHAIN_C0 + s); }
 int chain_levels(int64_t cap);
 
+// Instrumentation: one bounded wait that runs out (k_selftest.cu).
+cudaError_t launch_wait_selftest(uint32_t* status, long long limit, cudaStream_t st);
+
 // Batch-only steps (k_batch.cu).
 cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, int64_t n_xy, uint32_t* bstatus, int64_t* pp,
                                cudaStream_t st);

@@ -69,17 +69,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 }
 
 // Bounded wait for the phase with the given parity; false (and the timeout
-// bit set in *status) when it does not complete within WAIT_LIMIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait_status(unsigned long long* bar, unsigned parity, uint32_t* status) {
+// bit set in *status) when it does not complete within `limit` cycles.
+__device__ __forceinline__ bool mbar_wait_limit(unsigned long long* bar, unsigned parity, uint32_t* status,
+                                                long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       atomicOr(status, HULL_DEVICE_TIMEOUT);
       return false;
     }
   }
   return true;
+}
+
+__device__ __forceinline__ bool mbar_wait_status(unsigned long long* bar, unsigned parity, uint32_t* status) {
+  return mbar_wait_limit(bar, parity, status, WAIT_LIMIT_CYCLES);
 }
 
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, WsHeader* h) {

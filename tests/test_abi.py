@@ -86,3 +86,9 @@ def test_argument_errors_without_gpu(lib):
     # the no-prefilter comparator is for hull_compute only
     assert cp.hull_prefilter(P, 10, P, 1 << 30, P, P, 0, cp.Options(no_prefilter=True), 0) == 7
     assert cp.hull_batch(P, P, 1, 10, P, 1 << 30, P, P, cp.Options(no_prefilter=True), 0) == 7
+    # the timeout self-test checks its workspace and its limit first
+    lib_ = cp.load()
+    assert lib_.hull_selftest_wait(0, 1000, 0) == 1
+    assert lib_.hull_selftest_wait(P + 16, 1000, 0) == 1
+    assert lib_.hull_selftest_wait(P, 0, 0) == 1
+    assert lib_.hull_selftest_wait(P, (1 << 31) + 1, 0) == 1

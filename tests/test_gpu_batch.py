@@ -182,3 +182,40 @@ def test_server_slots_match_oracle_and_simulation_completes(gpu_lib):
     res = serve.simulate(server, starts, sizes, req_set, unit / 20000.0)
     assert np.all(np.isfinite(res.completion_s)) and np.all(res.latency_s > 0)
     assert res.points == int(sizes[req_set].sum())
+
+
+def test_set_alone_equals_in_batch_equals_in_serving_mix(gpu_lib):
+    # One set's hull computed alone (hull_compute on its rows), inside a
+    # batch of other sets (hull_batch_ranges) and inside a serving slot's
+    # mix (Server.launch) is the same list of global indices.
+    import torch
+    from paper_1405_3454_gb300 import serve
+    cp = gpu_lib
+    pxy, starts, sizes, _ = synth.serving_pool(1, 9950, 1e3, 3e5)
+    pool = torch.from_numpy(pxy).cuda()
+    server = serve.Server(pool, max_points=1 << 22, max_sets=32, slots=1)
+    rng = np.random.default_rng(9951)
+    for j in range(len(sizes)):
+        a, b = int(starts[j]), int(sizes[j])
+        h, c, _ = cp.compute(pool[a:a + b])
+        torch.cuda.synchronize()
+        alone = (cp.as_index(h, int(c.item())) + a).tolist()
+        others = rng.choice(len(sizes), 6, replace=True).tolist()
+        mix = others[:3] + [j] + others[3:]
+        out, hoff, ws = cp.batch_ranges(pool, torch.tensor(starts[mix], device="cuda"),
+                                        torch.tensor(sizes[mix], device="cuda"))
+        torch.cuda.synchronize()
+        assert cp.device_status(ws) == (0, 0)
+        hoff = hoff.cpu().numpy()
+        in_batch = out[hoff[3]:hoff[4]].cpu().tolist()
+        slot = server.free_slot()
+        server.launch(slot, starts[mix[::-1]], sizes[mix[::-1]], j)
+        torch.cuda.synchronize()
+        assert [t for _, t in server.poll()] == [j]
+        so = slot["hoff"][:len(mix) + 1].cpu().numpy()
+        k = len(mix) - 1 - 3
+        in_serving = slot["out"][so[k]:so[k + 1]].cpu().tolist()
+        assert alone == in_batch == in_serving, j
+    want = oracle.cudapre(pxy[starts[0]:starts[0] + sizes[0]])["hull"].astype(np.int64) + starts[0]
+    h, c, _ = cp.compute(pool[int(starts[0]):int(starts[0] + sizes[0])])
+    assert (cp.as_index(h, int(c.item())) + starts[0]).tolist() == want.tolist()

@@ -77,3 +77,53 @@ def test_batch_4096_sets_sampled(gpu_lib):
         assert got.tolist() == want.tolist(), s
     del d, out, ws
     assert n > 1_000_000_000
+
+
+def test_near_edge_2p28_fp32_decisions_match_exact(gpu_lib):
+    """The FP32 filter's error bound at scale: 2^28 points, half of them
+    (1.3e8) on or within one unit inside the polygon's edges, where float32
+    cannot decide and the bound must send the test to int64.  The survivor
+    set, the polygon and the hull must equal the oracle's (exact integer
+    arithmetic); a wrong bound would keep or drop some near-edge point."""
+    import torch
+    cp = gpu_lib
+    xy, poly = synth.near_edge_mix(N, SEED + 41, lambda g: oracle.hull16(g, oracle.extremes(g))[1])
+    _, opoly = oracle.hull16(xy, oracle.extremes(xy))
+    assert opoly.tolist() == poly.tolist()
+    osurv = oracle.prefilter(xy, opoly)
+    d = torch.from_numpy(xy).cuda()
+    surv, cnt, ext, ws = cp.prefilter(d)
+    torch.cuda.synchronize()
+    assert cp.read_polygon(ws)[1] == opoly.tolist()
+    ns, nesc = cp.read_counters(ws)
+    assert nesc > N // 8, nesc
+    assert np.array_equal(np.sort(cp.as_index(surv, int(cnt.item()))), osurv)
+    del surv, ws
+    out, hcnt, _ = cp.compute(d)
+    torch.cuda.synchronize()
+    assert cp.as_index(out, int(hcnt.item())).tolist() == oracle.hull(xy, osurv).tolist()
+
+
+def test_time_grows_linearly_with_n(gpu_lib):
+    """Linear time: on the disk workload, 4x the points costs between 2.5x
+    and 5x the device time of hull_compute (below 4x while fixed costs still
+    weigh), median of 7 timed calls after 3 warm-up calls each."""
+    import torch
+    cp = gpu_lib
+    ms = {}
+    for n in (1 << 26, 1 << 28):
+        d = torch.from_numpy(synth.disk(n, SEED)).cuda()
+        ws = cp.workspace(cp.hull_workspace_bytes(n))
+        t = []
+        for k in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            cp.compute(d, ws=ws)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= 3:
+                t.append(a.elapsed_time(b))
+        ms[n] = float(np.median(t))
+        del d, ws
+    r = ms[1 << 28] / ms[1 << 26]
+    assert 2.5 < r < 5.0, ms

@@ -230,3 +230,37 @@ def test_no_prefilter_hull_equals_the_method(gpu_lib, name, n):
     got = cp.as_index(out, int(cnt.item())).tolist()
     want = oracle.cudapre(xy)["hull"].tolist() if n else []
     assert got == want
+
+
+def test_bounded_wait_timeout_reports_and_context_survives(gpu_lib):
+    # A bounded device wait that nothing releases gives up, records the
+    # timeout in the workspace status and returns; the context stays usable
+    # and the next call on the same workspace clears the status.
+    import torch
+    cp = gpu_lib
+    xy = synth.disk(100_000, 41)
+    ws = cp.workspace(cp.hull_workspace_bytes(len(xy)))
+    for limit in (1, 1 << 12, 1 << 20):
+        cp.selftest_wait(ws, limit)
+        torch.cuda.synchronize()
+        assert cp.device_status(ws) == (5, cp.HULL_DEVICE_TIMEOUT)
+    out, cnt, _ = cp.compute(to_dev(xy), ws=ws)
+    torch.cuda.synchronize()
+    assert cp.device_status(ws) == (0, 0)
+    assert cp.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()
+
+
+@pytest.mark.parametrize("name,lo,hi", [("square", 5e-5, 2e-3), ("disk", 0.060, 0.072),
+                                        ("gaussian", 2e-5, 2e-3)])
+def test_survivor_fraction_bands(gpu_lib, name, lo, hi):
+    # Fraction of points left after Step 3 with cumulative angles: in a
+    # square the corners are among the 16 extremes and only thin slivers
+    # along the sides remain, a disk keeps the circular segments outside the
+    # inscribed polygon, a Gaussian cloud only its sparse outer tail.
+    import torch
+    n = 1 << 24
+    xy = {"square": lambda: synth.square(n, 51, 1 << 24), "disk": lambda: synth.disk(n, 52),
+          "gaussian": lambda: synth.gaussian(n, 53)}[name]()
+    surv, cnt, _, ws = gpu_lib.prefilter(to_dev(xy))
+    torch.cuda.synchronize()
+    assert lo <= int(cnt.item()) / n <= hi
