@@ -98,7 +98,7 @@ struct BlockBest {
 // Workspace header (offset 0 of every workspace); zeroed by each call.
 struct WsHeader {
   uint32_t status;        // HULL_DEVICE_* bits
-  uint32_t done_blocks;   // last-block-done counter of the extreme search
+  uint32_t next_group[2];  // dynamic shares of one set: chunk-group counters of Step 1 and Step 3
   unsigned long long n_surv;      // survivors written by the inside test
   unsigned long long n_escalated; // float32 decisions escalated to int64
   uint32_t bar_count, bar_gen;  // grid barrier of the cooperative large-set kernel

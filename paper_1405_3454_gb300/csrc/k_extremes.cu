@@ -395,10 +395,11 @@ __device__ void hull16_warp(const float* xy, const uint32_t* ext, Poly* P, bool 
 // block's best for value k (min if lo, max if hi).  Each lane picks its best
 // tile point, a butterfly of exact comparisons picks the warp's, and lane 0
 // merges it into the warp's running best (shared memory) and lowers the
-// block threshold.  The tile is re-read from global memory (an L2 hit);
-// f = first pair of the chunk, cnt = its pairs.
+// block threshold.  The tile is re-read from the stage in shared memory (the
+// warp releases the stage only after this); f = first pair of the chunk in
+// the set, cnt = its pairs.
 template <int ANG>
-__device__ __noinline__ void ext_slow(int k, bool lo, bool hi, int64_t f, int cnt, const float4* P, int head,
+__device__ __noinline__ void ext_slow(int k, bool lo, bool hi, int64_t f, int cnt, const float4* SP, int head,
                                       float* thr, float* wbest, uint32_t* widx, const float* xy) {
   const int tid = threadIdx.x, lane = tid & 31;
   float s_lo = -FLT_MAX, s_hi = -FLT_MAX;
@@ -407,8 +408,9 @@ __device__ __noinline__ void ext_slow(int k, bool lo, bool hi, int64_t f, int cn
   const float t_hi = *reinterpret_cast<volatile float*>(&thr[2 * k + 1]);
   for (int j = 0; j < 8; ++j) {
     const int o = (j >> 1) * CONSUMERS + tid;
-    const int64_t q = f + (o < cnt ? o : 0);  // out of range: repeat a real point
-    const float4 v = __ldg(P + q);
+    const int oo = o < cnt ? o : 0;  // out of range: repeat a real point
+    const int64_t q = f + oo;
+    const float4 v = SP[oo];
     const float x = (j & 1) ? v.z : v.x, y = (j & 1) ? v.w : v.y;
     const uint32_t i = (uint32_t)(head + 2 * q) + (j & 1);
     const float val = value32<ANG>(k, x, y);
@@ -544,11 +546,72 @@ __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(S
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool dead = *reinterpret_cast<volatile uint32_t*>(gstatus) != 0;
   stream_init(SM);
+  // one set: dynamic shares; a batch: the block's static share of the
+  // virtual pair axis, set by set
+  const bool dyn = S.S == 1;
   const int64_t P = S.pp_at(S.S);
   const int64_t v0 = (int64_t)blockIdx.x * ppb;
   const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
   if (warp == PRODUCER_WARP) {
-    stream_produce_sets(SM, S, v0, v1, false, gstatus);
+    if (dyn)
+      stream_produce_dynamic(SM, reinterpret_cast<const float4*>(S.xy_of(0) + 2 * S.head_of(0)), S.npairs_of(0),
+                             &S.h(0)->next_group[0], false, gstatus);
+    else
+      stream_produce_sets(SM, S, v0, v1, false, gstatus);
+    return;
+  }
+  // a new set: clear the running bests and thresholds
+  auto begin_set = [&]() {
+    if (tid < CONSUMERS / 32 * ND) {
+      (&w_best[0][0])[tid] = -FLT_MAX;
+      (&w_bidx[0][0])[tid] = NONE;
+    }
+    if (tid < ND) thr[tid] = (tid & 1) ? -FLT_MAX : FLT_MAX;
+    consumers_sync();
+  };
+  // one chunk in stage st: cnt pairs from pair f of the set (first: the
+  // warp's first chunk of the set seeds the thresholds); the stage is
+  // released after the rare path, which re-reads it
+  auto chunk = [&](int st, int64_t f, int cnt, bool first, const float* xy, int head) {
+    const float4* sp = SM.stage[st];
+    const float4 a = sp[tid < cnt ? tid : 0];
+    const float4 b = sp[tid + CONSUMERS < cnt ? tid + CONSUMERS : 0];
+    const float4 cc = sp[tid + 2 * CONSUMERS < cnt ? tid + 2 * CONSUMERS : 0];
+    const float4 d = sp[tid + 3 * CONSUMERS < cnt ? tid + 3 * CONSUMERS : 0];
+    float tmin[NV], tmax[NV];
+    ext_minmax<ANG>(a, b, cc, d, tmin, tmax);
+    if (first) ext_seed<ANG>(tmin, tmax, thr);
+    float t[ND];
+#pragma unroll
+    for (int q = 0; q < ND / 4; ++q) {
+      const float4 v4 = lds_vol4(&thr[4 * q]);
+      t[4 * q] = v4.x; t[4 * q + 1] = v4.y; t[4 * q + 2] = v4.z; t[4 * q + 3] = v4.w;
+    }
+    bool any = false;
+#pragma unroll
+    for (int kk = 0; kk < NV; ++kk) any |= (tmin[kk] <= t[2 * kk]) | (tmax[kk] >= t[2 * kk + 1]);
+    if (__any_sync(FULL, any)) {  // rare: some lane's tile may improve a best
+#pragma unroll
+      for (int kk = 0; kk < NV; ++kk) {
+        const bool lo2 = __any_sync(FULL, tmin[kk] <= t[2 * kk]), hi2 = __any_sync(FULL, tmax[kk] >= t[2 * kk + 1]);
+        if (lo2 || hi2) ext_slow<ANG>(kk, lo2, hi2, f, cnt, sp, head, thr, w_best[warp], w_bidx[warp], xy);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&SM.empty[st]);
+  };
+  if (dyn) {
+    const float* xy = S.xy_of(0);
+    const int head = S.head_of(0);
+    const int64_t np = S.npairs_of(0);
+    begin_set();
+    for (int c = 0;; ++c) {
+      const int id = stream_next_chunk(SM, c, gstatus);
+      if (id < 0) break;
+      const int64_t f = (int64_t)id * CHUNK;
+      chunk(c % SS::STAGES, f, (int)min((int64_t)CHUNK, np - f), c == 0, xy, head);
+    }
+    ext_block_result<ANG>(xy, &w_bidx[0][0], &w_s64[0][0], bres + (size_t)blockIdx.x * ND);
     return;
   }
   int c = 0;
@@ -556,47 +619,14 @@ __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(S
   walk_segments(S, v0, v1, false, [&](int s, int64_t lo, int n) {
     const float* xy = S.xy_of(s);
     const int head = S.head_of(s);
-    const float4* Pp = reinterpret_cast<const float4*>(xy + 2 * head);
-    // a new set: clear the running bests and thresholds
-    if (tid < CONSUMERS / 32 * ND) {
-      (&w_best[0][0])[tid] = -FLT_MAX;
-      (&w_bidx[0][0])[tid] = NONE;
-    }
-    if (tid < ND) thr[tid] = (tid & 1) ? -FLT_MAX : FLT_MAX;
-    consumers_sync();
+    begin_set();
     const int nck = nchunks(n);
     for (int k = 0; k < nck; ++k, ++c) {
       const int st = c % SS::STAGES;
       if (!stop && !mbar_wait_status(&SM.full[st], (unsigned)((c / SS::STAGES) & 1), gstatus)) stop = true;
       if (stop) continue;
       const int f = k * CHUNK;
-      const int cnt = min(CHUNK, n - f);
-      const float4* sp = SM.stage[st];
-      const float4 a = sp[tid < cnt ? tid : 0];
-      const float4 b = sp[tid + CONSUMERS < cnt ? tid + CONSUMERS : 0];
-      const float4 cc = sp[tid + 2 * CONSUMERS < cnt ? tid + 2 * CONSUMERS : 0];
-      const float4 d = sp[tid + 3 * CONSUMERS < cnt ? tid + 3 * CONSUMERS : 0];
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&SM.empty[st]);
-      float tmin[NV], tmax[NV];
-      ext_minmax<ANG>(a, b, cc, d, tmin, tmax);
-      if (k == 0) ext_seed<ANG>(tmin, tmax, thr);
-      float t[ND];
-#pragma unroll
-      for (int q = 0; q < ND / 4; ++q) {
-        const float4 v4 = lds_vol4(&thr[4 * q]);
-        t[4 * q] = v4.x; t[4 * q + 1] = v4.y; t[4 * q + 2] = v4.z; t[4 * q + 3] = v4.w;
-      }
-      bool any = false;
-#pragma unroll
-      for (int kk = 0; kk < NV; ++kk) any |= (tmin[kk] <= t[2 * kk]) | (tmax[kk] >= t[2 * kk + 1]);
-      if (__any_sync(FULL, any)) {  // rare: some lane's tile may improve a best
-#pragma unroll
-        for (int kk = 0; kk < NV; ++kk) {
-          const bool lo2 = __any_sync(FULL, tmin[kk] <= t[2 * kk]), hi2 = __any_sync(FULL, tmax[kk] >= t[2 * kk + 1]);
-          if (lo2 || hi2) ext_slow<ANG>(kk, lo2, hi2, lo + f, cnt, Pp, head, thr, w_best[warp], w_bidx[warp], xy);
-        }
-      }
+      chunk(st, lo + f, min(CHUNK, n - f), k == 0, xy, head);
     }
     ext_block_result<ANG>(xy, &w_bidx[0][0], &w_s64[0][0], bres + ((size_t)blockIdx.x + s) * ND);
   });

@@ -202,15 +202,20 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
   const unsigned lt = (1u << lane) - 1u;
   const bool dead = *reinterpret_cast<volatile uint32_t*>(gstatus) != 0;
   stream_init(SM);
+  // One set: dynamic shares, claimed last chunk first (the extreme search
+  // claimed them first to last, so the chunks it streamed last are still in
+  // L2).  A batch: static shares of the virtual pair axis, blocks and chunks
+  // last-to-first for the same reason.
+  const bool dyn = S.S == 1;
   const int64_t P = S.pp_at(S.S);
-  // blocks take their shares last-to-first: the first ones to run read what
-  // the extreme search read last (still in L2)
   const int64_t v0 = (int64_t)(gridDim.x - 1 - blockIdx.x) * ppb;
   const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
-  // Chunks run last-to-first: the extreme search streamed each block's range
-  // first-to-last, so the tail of every range is still in L2.
   if (warp == PRODUCER_WARP) {
-    stream_produce_sets(SM, S, v0, v1, true, gstatus);
+    if (dyn)
+      stream_produce_dynamic(SM, reinterpret_cast<const float4*>(S.xy_of(0) + 2 * S.head_of(0)), S.npairs_of(0),
+                             &S.h(0)->next_group[1], true, gstatus);
+    else
+      stream_produce_sets(SM, S, v0, v1, true, gstatus);
     return;
   }
   WarpOut<KEYS> O;
@@ -223,6 +228,9 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
   unsigned esc = 0;
   bool all_survive = true;
   Cells C;
+  float ccx = 0.0f, ccy = 0.0f, cr2 = -1.0f;
+  uint32_t ibase = 0;
+  WsHeader* h = nullptr;
   // Full test of the `count` (<= 32) most recently queued points, one per lane.
   auto drain = [&](int count) {
     const bool mine = lane < count;
@@ -244,13 +252,12 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
     qn -= count;
     O.push(keep, i, p.x, p.y);
   };
-  int c = 0;
-  bool stop = false;
-  walk_segments(S, v0, v1, true, [&](int set, int64_t lo, int n) {
-    // a new set: its polygon, inscribed circle and cell grid (section 2,
-    // Step 3: the polygon goes to shared memory), its output
+  // a new set (first pair lo of its segment): its polygon, inscribed circle
+  // and cell grid (section 2, Step 3: the polygon goes to shared memory),
+  // its output
+  auto begin_set = [&](int set, int64_t lo) {
     consumers_sync();
-    WsHeader* h = S.h(set);
+    h = S.h(set);
     if (tid < MAXV * (int)(sizeof(Edge) / 4))
       reinterpret_cast<uint32_t*>(s_e)[tid] = reinterpret_cast<const uint32_t*>(h->poly.e)[tid];
     if (tid == 0) {
@@ -266,53 +273,77 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
     C.gy = (float)s_pm[2];
     C.sx = __int_as_float((127 - s_pm[3]) << 23);  // 2^-kx
     C.sy = __int_as_float((127 - s_pm[4]) << 23);
-    const float ccx = s_circ[0], ccy = s_circ[1];
-    const float cr2 = all_survive ? -1.0f : s_circ[2];
+    ccx = s_circ[0];
+    ccy = s_circ[1];
+    cr2 = all_survive ? -1.0f : s_circ[2];
     O.h = h;
     O.g_idx = surv_idx + S.off_at(set);
     O.g_key = KEYS ? surv_key + S.off_at(set) : nullptr;
     esc = 0;
-    const uint32_t ibase = (uint32_t)(S.head_of(set) + 2 * lo) + 2u * (uint32_t)tid;
+    ibase = (uint32_t)(S.head_of(set) + 2 * lo) + 2u * (uint32_t)tid;
+  };
+  // one chunk in stage st: cnt pairs from pair f of the segment
+  auto chunk = [&](int st, int f, int cnt) {
+    const float4* sp = SM.stage[st];
+    float4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = sp[tid + j * CONSUMERS];  // beyond cnt: ignored below
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&SM.empty[st]);
+    const uint32_t i0 = ibase + 2u * (uint32_t)f;
+    const int lim = cnt - tid;
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0 += FLT_DRAIN_POINTS) {
+#pragma unroll
+      for (int j = j0; j < j0 + FLT_DRAIN_POINTS; ++j) {
+        const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
+        const float dx = x - ccx, dy = y - ccy;
+        const bool need = (j >> 1) * CONSUMERS < lim && !(fmaf(dx, dx, dy * dy) < cr2);
+        const unsigned bal = __ballot_sync(FULL, need);
+        const int slot = qn + __popc(bal & lt);
+        if (need) {
+          qxy[slot] = make_float2(x, y);
+          qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
+        }
+        qn += __popc(bal);
+      }
+      __syncwarp();
+      while (qn >= 32) drain(32);
+    }
+  };
+  // the end of a set: queued points, buffered survivors, counters
+  auto end_set = [&]() {
+    __syncwarp();
+    if (qn > 0) drain(qn);
+    O.flush();
+    for (int off = 16; off; off >>= 1) esc += __shfl_xor_sync(FULL, esc, off);
+    if (lane == 0 && esc) atomicAdd(&h->n_escalated, (unsigned long long)esc);
+  };
+  if (dyn) {
+    const int64_t np = S.npairs_of(0);
+    begin_set(0, 0);
+    for (int c = 0;; ++c) {
+      const int id = stream_next_chunk(SM, c, gstatus);
+      if (id < 0) break;
+      const int f = id * CHUNK;
+      chunk(c % FilterStream::STAGES, f, (int)min((int64_t)CHUNK, np - f));
+    }
+    end_set();
+    return;
+  }
+  int c = 0;
+  bool stop = false;
+  walk_segments(S, v0, v1, true, [&](int set, int64_t lo, int n) {
+    begin_set(set, lo);
     const int nck = nchunks(n);
     for (int k = 0; k < nck; ++k, ++c) {
       const int st = c % FilterStream::STAGES;
       if (!stop && !mbar_wait_status(&SM.full[st], (unsigned)((c / FilterStream::STAGES) & 1), gstatus)) stop = true;
       if (stop) continue;
       const int f = chunk_first(k, nck, true);
-      const int cnt = min(CHUNK, n - f);
-      const float4* sp = SM.stage[st];
-      float4 v[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = sp[tid + j * CONSUMERS];  // beyond cnt: ignored below
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&SM.empty[st]);
-      const uint32_t i0 = ibase + 2u * (uint32_t)f;
-      const int lim = cnt - tid;
-#pragma unroll
-      for (int j0 = 0; j0 < 8; j0 += FLT_DRAIN_POINTS) {
-#pragma unroll
-        for (int j = j0; j < j0 + FLT_DRAIN_POINTS; ++j) {
-          const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
-          const float dx = x - ccx, dy = y - ccy;
-          const bool need = (j >> 1) * CONSUMERS < lim && !(fmaf(dx, dx, dy * dy) < cr2);
-          const unsigned bal = __ballot_sync(FULL, need);
-          const int slot = qn + __popc(bal & lt);
-          if (need) {
-            qxy[slot] = make_float2(x, y);
-            qi[slot] = i0 + 2u * (uint32_t)((j >> 1) * CONSUMERS) + (uint32_t)(j & 1);
-          }
-          qn += __popc(bal);
-        }
-        __syncwarp();
-        while (qn >= 32) drain(32);
-      }
+      chunk(st, f, min(CHUNK, n - f));
     }
-    // finish the set: queued points, buffered survivors, counters
-    __syncwarp();
-    if (qn > 0) drain(qn);
-    O.flush();
-    for (int off = 16; off; off >>= 1) esc += __shfl_xor_sync(FULL, esc, off);
-    if (lane == 0 && esc) atomicAdd(&h->n_escalated, (unsigned long long)esc);
+    end_set();
   });
 }
 

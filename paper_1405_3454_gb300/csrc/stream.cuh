@@ -28,6 +28,17 @@ constexpr long long WAIT_LIMIT_CYCLES = 1ll << 31;  // about one second
 constexpr int BATCH_WAVES = 4;
 constexpr int64_t WAVE_MIN_CHUNKS = 32;
 constexpr int64_t MAX_STREAM_BLOCKS = 4096;  // partial-result slots per call
+// One set streams with partly dynamic shares: every block first takes a
+// static run of DYN_STATIC_PCT percent of an equal share, then producers
+// claim groups of DYN_GROUP chunks of the rest from a counter in the set's
+// header, so blocks that draw more bandwidth take more chunks (equal static
+// shares ended up to 2x apart in time on a 2^28-point set).
+#ifndef DYN_GROUP
+#define DYN_GROUP 4
+#endif
+#ifndef DYN_STATIC_PCT
+#define DYN_STATIC_PCT 75
+#endif
 
 inline int stream_waves(int sets, int64_t npairs, int64_t resident_blocks) {
   if (sets <= 1) return 1;
@@ -107,6 +118,7 @@ struct StreamSmemT {
   float4 stage[NS][CHUNK];
   unsigned long long full[NS];
   unsigned long long empty[NS];
+  int id[NS];  // dynamic shares: the chunk in the stage, -1 = end of the stream
 };
 
 // Chunk c of a block's pair range [p0, p1) in processing order; `reverse`
@@ -196,6 +208,63 @@ __device__ __forceinline__ void stream_produce_sets(SS& SM, const Sets& S, int64
   });
   for (int d = c > STAGES ? c - STAGES : 0; d < c; ++d)
     mbar_wait_status(&SM.full[d % STAGES], (unsigned)((d / STAGES) & 1), status);
+}
+
+// Producer (lane 0 of the producer warp) with partly dynamic shares over
+// the nck chunks of one set (npairs pairs from P).  Logical chunk k is
+// chunk k, or nck - 1 - k when `reverse`.  Block b first streams logical
+// chunks [b q, (b + 1) q), q = DYN_STATIC_PCT percent of nck / gridDim.x,
+// then claims groups of the rest from *next (one claim kept in flight; every
+// claimed group is streamed, so every chunk is streamed by exactly one
+// block).  Each chunk's number goes into the stage before its "full" barrier
+// is armed; -1 (a plain arrival) ends the stream.
+template <class SS>
+__device__ __forceinline__ void stream_produce_dynamic(SS& SM, const float4* P, int64_t npairs, uint32_t* next,
+                                                       bool reverse, uint32_t* status) {
+  constexpr int STAGES = SS::STAGES;
+  if ((threadIdx.x & 31) != 0) return;
+  const int nck = (int)((npairs + CHUNK - 1) / CHUNK);
+  const int q = (int)((int64_t)nck * DYN_STATIC_PCT / 100 / gridDim.x);
+  const int pool = q * (int)gridDim.x;  // first logical chunk of the shared pool
+  const int ngroups = (nck - pool + DYN_GROUP - 1) / DYN_GROUP;
+  const bool dead = *reinterpret_cast<volatile uint32_t*>(status) != 0;
+  uint32_t nxt = dead ? (uint32_t)ngroups : atomicAdd(next, 1u);
+  int k = dead ? nck : (int)blockIdx.x * q, kend = dead ? nck : k + q;
+  int c = 0;
+  for (;; ++c) {
+    const int st = c % STAGES;
+    const int ph = c / STAGES;
+    if (ph > 0 && !mbar_wait_status(&SM.empty[st], (unsigned)((ph - 1) & 1), status)) break;
+    if (k >= kend) {
+      k = nxt < (uint32_t)ngroups ? pool + (int)nxt * DYN_GROUP : nck;
+      kend = min(k + DYN_GROUP, nck);
+      if (k < nck) nxt = atomicAdd(next, 1u);
+    }
+    if (k >= nck || (*reinterpret_cast<volatile uint32_t*>(status) & HULL_DEVICE_TIMEOUT)) {
+      SM.id[st] = -1;
+      mbar_arrive(&SM.full[st]);
+      ++c;
+      break;
+    }
+    const int id = reverse ? nck - 1 - k : k;
+    ++k;
+    const unsigned bytes = (unsigned)min((int64_t)CHUNK, npairs - (int64_t)id * CHUNK) * 16u;
+    SM.id[st] = id;
+    mbar_arrive_tx(&SM.full[st], bytes);
+    bulk_g2s(&SM.stage[st][0], P + (int64_t)id * CHUNK, bytes, &SM.full[st]);
+  }
+  // c stages were armed (the end marker included): the last ones must land
+  for (int d = c > STAGES ? c - STAGES : 0; d < c; ++d)
+    mbar_wait_status(&SM.full[d % STAGES], (unsigned)((d / STAGES) & 1), status);
+}
+
+// Consumers' side of dynamic shares: wait for stage c and read its chunk
+// number; -1 at the end of the stream or when the wait gave up.
+template <class SS>
+__device__ __forceinline__ int stream_next_chunk(SS& SM, int c, uint32_t* status) {
+  const int st = c % SS::STAGES;
+  if (!mbar_wait_status(&SM.full[st], (unsigned)((c / SS::STAGES) & 1), status)) return -1;
+  return *reinterpret_cast<volatile int*>(&SM.id[st]);
 }
 
 template <class SS>
