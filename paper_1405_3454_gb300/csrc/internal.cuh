@@ -105,6 +105,9 @@ struct WsHeader {
   uint32_t hist[8][256];  // radix-sort digit histograms (all passes)
   unsigned long long n_surv2;  // survivors left by the refinement round
   uint32_t n_lower, n_upper;   // small-set hull: vertices of the lower / upper chain
+  float refine_r2;             // refinement: squared radius of a disk inside the winners' polygon (or -1)
+  int32_t refine_cx, refine_cy;  // and its centre
+  uint32_t refine_pad_;
   Poly poly;
   unsigned long long rbin[1024];  // refinement: per angular bin, packed farthest survivor
 };

@@ -117,6 +117,19 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_bins(Sets S, Tiles T, const u
 
 // For every bin: its winner W (if any) and the nearest winners L before and R
 // after it (cyclically), as coordinates.  One block per set.
+//
+// Also a disk inside the winners' polygon (the winners in bin order).  When
+// O is strictly left of every edge W -> R, each edge turns by less than 180
+// degrees about O; the winners follow the bins' monotone pseudo-angle, so
+// the turns add up to one full turn and the polygon is simple and
+// star-shaped about O: the union of the triangles (O, W, R), inside the hull
+// of the input.  Its centre C is the winners' mean truncated to integers; C
+// is inside iff a ray from C crosses the polygon an odd number of times
+// (exact tests), and then every point closer to C than each edge segment is
+// strictly inside it.  h->refine_r2 gets the squared distance from C to the
+// nearest segment in float32 (at most 2^-22 too large), shrunk by 2^-18 and
+// rounded down, which also covers the float32 rounding of the per-point test
+// (at most 2^-21); or -1 when a condition fails.  h->refine_cx/cy get C.
 __global__ void __launch_bounds__(REFINE_BINS) k_refine_links(Sets S, const uint32_t* gstatus,
                                                                const unsigned long long* __restrict__ keys_base,
                                                                int4* __restrict__ tri_base) {
@@ -172,13 +185,71 @@ __global__ void __launch_bounds__(REFINE_BINS) k_refine_links(Sets S, const uint
   }
   int4 a = make_int4(0, 0, 0, 0), c = make_int4(0, 0, 0, 0);
   int flags = 0;
-  if (!dead && h->poly.refine_on && nw >= 2 && l >= 0 && r >= 0) {
+  const bool on = !dead && h->poly.refine_on;
+  if (on && nw >= 2 && l >= 0 && r >= 0) {
     flags = 1 | (has ? 2 : 0);
     a = make_int4(s_x[l], s_y[l], has ? s_x[b] : 0, has ? s_y[b] : 0);
     c = make_int4(s_x[r], s_y[r], flags, 0);
   }
   tri[2 * b] = a;
   tri[2 * b + 1] = c;
+  // the disk: the winners' mean, then every winner's edge to the next winner
+  __shared__ long long s_sum[2][NWARP];
+  __shared__ int s_c[2];
+  __shared__ unsigned s_d2;  // float bits of the minimum (non-negative floats order as integers)
+  __shared__ int s_bad;
+  long long sx = has ? s_x[b] : 0, sy = has ? s_y[b] : 0;
+  for (int off = 16; off; off >>= 1) {
+    sx += __shfl_xor_sync(FULL, sx, off);
+    sy += __shfl_xor_sync(FULL, sy, off);
+  }
+  if (lane == 0) { s_sum[0][wp] = sx; s_sum[1][wp] = sy; }
+  __syncthreads();
+  if (b == 0) {
+    long long tx = 0, ty = 0;
+    for (int w = 0; w < NWARP; ++w) { tx += s_sum[0][w]; ty += s_sum[1][w]; }
+    s_c[0] = nw > 0 ? (int)(tx / nw) : 0;
+    s_c[1] = nw > 0 ? (int)(ty / nw) : 0;
+    s_d2 = 0x7F7FFFFFu;
+    s_bad = (on && nw >= 3) ? 0 : 1;
+  }
+  __syncthreads();
+  int cross = 0;
+  if (has && on && nw >= 3) {
+    const long long ox = h->poly.rox, oy = h->poly.roy, cx = s_c[0], cy = s_c[1];
+    const long long wx = s_x[b], wy = s_y[b], rx = s_x[r], ry = s_y[r];
+    const long long ex = rx - wx, ey = ry - wy, e2 = ex * ex + ey * ey;
+    const long long oo = ex * (oy - wy) - ey * (ox - wx);  // orient(W, R, O)
+    const long long oc = ex * (cy - wy) - ey * (cx - wx);  // orient(W, R, C)
+    if (oo <= 0 || oc == 0 || e2 == 0) {
+      atomicOr(&s_bad, 1);
+    } else {
+      // the ray from C towards +x crosses this edge (half-open in y)
+      if ((wy > cy) != (ry > cy)) cross = (ry > wy) ? (oc > 0) : (oc < 0);
+      // squared distance from C to the segment W R, in float32 (four
+      // roundings to nearest at most: at most 2^-22 too large)
+      const long long dot = (cx - wx) * ex + (cy - wy) * ey;
+      float d2;
+      if (dot <= 0) {
+        d2 = __ll2float_rn((cx - wx) * (cx - wx) + (cy - wy) * (cy - wy));
+      } else if (dot >= e2) {
+        d2 = __ll2float_rn((cx - rx) * (cx - rx) + (cy - ry) * (cy - ry));
+      } else {
+        const float of = __ll2float_rn(oc);
+        d2 = __fmul_rn(of, of) / __ll2float_rn(e2);
+      }
+      atomicMin(&s_d2, __float_as_uint(d2));
+    }
+  }
+  // C is inside the (simple) polygon iff the ray crosses it an odd number of times
+  const int ncross = __syncthreads_count(cross);
+  if (b == 0 && !(ncross & 1)) s_bad = 1;
+  __syncthreads();
+  if (b == 0) {
+    h->refine_r2 = (dead || s_bad) ? -1.0f : __fmul_rd(__uint_as_float(s_d2), 1.0f - 0x1p-18f);
+    h->refine_cx = s_c[0];
+    h->refine_cy = s_c[1];
+  }
 }
 
 // Exact orientation of (a, b, p) for lattice points within +-2^24: every
@@ -202,7 +273,8 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const
   int cur = -1;
   WsHeader* h = nullptr;
   int ox = 0, oy = 0;
-  float oxf = 0.0f, oyf = 0.0f;
+  int cx = 0, cy = 0;
+  float oxf = 0.0f, oyf = 0.0f, rr2 = -1.0f;
   int64_t m = 0;
   const unsigned long long* kin = nullptr;
   const uint32_t* vin = nullptr;
@@ -221,12 +293,13 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const
       oxf = (float)ox;
       oyf = (float)oy;
       m = count_of(h, &h->n_surv);
+      rr2 = *reinterpret_cast<const volatile float*>(&h->refine_r2);
+      cx = *reinterpret_cast<const volatile int*>(&h->refine_cx);
+      cy = *reinterpret_cast<const volatile int*>(&h->refine_cy);
       const int64_t o = S.off_at(s);
       kin = kin_base + o; vin = vin_base + o; kout = kout_base + o; vout = vout_base + o;
       __syncthreads();
     }
-    // 4 independent loads in flight per thread; a warp handles 4 x 32
-    // consecutive survivors
     const int64_t j0 = (t - T.first(s)) * RT;
     unsigned long long kv[RU];
 #pragma unroll
@@ -238,14 +311,16 @@ __global__ void __launch_bounds__(RBLOCK) k_refine_filter(Sets S, Tiles T, const
     for (int u = 0; u < RU; ++u) {
       const int64_t j = j0 + u * RBLOCK + tid;
       bool keep = false;
-      if (j < m) {
+      const unsigned long long key = kv[u];
+      const int px = key_x(key), py = key_y(key);
+      // inside the disk: strictly inside the winners' polygon
+      const float fx = (float)(px - cx), fy = (float)(py - cy);
+      if (j < m && !(fmaf(fx, fx, fy * fy) < rr2)) {
         // One triangle (O, A, B) per bin and side, chosen without branching:
         // with a winner W, (O, L, W) on the L side of the ray O->W and
         // (O, W, R) on the other; without one, (O, L, R).  p is dropped iff
         // it is strictly inside (all three orientations positive); a point
         // on the ray O->W has a zero orientation and stays.
-        const unsigned long long key = kv[u];
-        const int px = key_x(key), py = key_y(key);
         const int b = bin_of((float)px - oxf, (float)py - oyf);
         const int4 a = s_tri[2 * b], c = s_tri[2 * b + 1];
         const bool has_w = (c.z & 2) != 0;

@@ -105,9 +105,11 @@ def test_near_edge_2p28_fp32_decisions_match_exact(gpu_lib):
 
 
 def test_time_grows_linearly_with_n(gpu_lib):
-    """Linear time: on the disk workload, 4x the points costs between 2.5x
-    and 5x the device time of hull_compute (below 4x while fixed costs still
-    weigh), median of 7 timed calls after 3 warm-up calls each."""
+    """Linear time: on the disk workload, 4x the points costs between 2x and
+    4.4x the device time of hull_compute (at most linear growth, within
+    noise; below 4x while the costs that do not grow with n, about 0.2 ms
+    of the survivors' hull, still weigh), median of 7 timed calls after 3
+    warm-up calls each."""
     import torch
     cp = gpu_lib
     ms = {}
@@ -126,4 +128,4 @@ def test_time_grows_linearly_with_n(gpu_lib):
         ms[n] = float(np.median(t))
         del d, ws
     r = ms[1 << 28] / ms[1 << 26]
-    assert 2.5 < r < 5.0, ms
+    assert 2.0 < r < 4.4, ms

@@ -264,3 +264,45 @@ def test_survivor_fraction_bands(gpu_lib, name, lo, hi):
     surv, cnt, _, ws = gpu_lib.prefilter(to_dev(xy))
     torch.cuda.synchronize()
     assert lo <= int(cnt.item()) / n <= hi
+
+
+def _crescent(n, seed):
+    # lattice points of the disk of radius 2^23 outside an offset disk of
+    # radius 0.9 * 2^23: hull and Step-2 polygon are round, the survivors and
+    # the refinement winners form a crescent whose mean lies off-centre
+    rng = np.random.default_rng(seed)
+    r = float(1 << 23)
+    out = np.zeros((0, 2))
+    while len(out) < n:
+        p = rng.uniform(-r, r, size=(2 * n, 2)).round()
+        keep = (np.hypot(p[:, 0], p[:, 1]) <= r) & (np.hypot(p[:, 0] - 0.15 * r, p[:, 1]) > 0.9 * r)
+        out = np.concatenate([out, p[keep]])
+    return out[:n].astype(np.float32)
+
+
+def _two_blobs(n, seed):
+    # two lattice disks of radius 2^22, centres 2^24 apart: a stadium-like
+    # hull with two long straight edges
+    rng = np.random.default_rng(seed)
+    r = float(1 << 22)
+    out = np.zeros((0, 2))
+    while len(out) < n:
+        p = rng.uniform(-r, r, size=(2 * n, 2)).round()
+        out = np.concatenate([out, p[np.hypot(p[:, 0], p[:, 1]) <= r]])
+    out = out[:n]
+    out[::2] += [-(2.0 ** 23), 0.0]
+    out[1::2] += [2.0 ** 23 - 2.0 ** 22, 2.0 ** 21]
+    return out.astype(np.float32)
+
+
+@pytest.mark.parametrize("name", ["crescent", "two_blobs"])
+def test_refinement_on_uneven_shapes(gpu_lib, name):
+    # shapes whose refinement winners are far from round: the disk inside the
+    # winners' polygon must be rejected or small, never wrong
+    import torch
+    for n in (70_000, 1 << 20):
+        xy = _crescent(n, 61) if name == "crescent" else _two_blobs(n, 62)
+        out, cnt, ws = gpu_lib.compute(to_dev(xy))
+        torch.cuda.synchronize()
+        assert gpu_lib.device_status(ws) == (0, 0)
+        assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist(), n
