@@ -77,7 +77,7 @@ struct Tester<HULL_FILTER_EXACT> {
 // buffer is flushed by its warp with one global atomic and coalesced stores.
 // No block-wide barrier in the streaming loop.
 #ifndef FLT_WBUF
-#define FLT_WBUF 256
+#define FLT_WBUF 320
 #endif
 constexpr int WBUF = FLT_WBUF;
 
@@ -138,7 +138,7 @@ struct WarpOut {
 using FilterStream = StreamSmemT<FLT_STAGES>;
 // Points per thread between two drains of the queue (8 = once per chunk).
 #ifndef FLT_DRAIN_POINTS
-#define FLT_DRAIN_POINTS 4
+#define FLT_DRAIN_POINTS 2
 #endif
 constexpr int QCAP = 31 + 32 * FLT_DRAIN_POINTS;  // left over + pushed between drains (a per-warp stack)
 
