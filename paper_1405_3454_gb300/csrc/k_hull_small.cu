@@ -335,33 +335,41 @@ __global__ void __launch_bounds__(TB) k_small_tiny(Sets S, const uint32_t* gstat
       __syncthreads();
     }
   }
+  // the sorted keys decoded in place (each thread its own slots)
+  int2* sp = reinterpret_cast<int2*>(sk);
+  for (int i = tid; i < m; i += TB) {
+    const unsigned long long k = sk[i];
+    sp[i] = make_int2(key_x(k), key_y(k));
+  }
+  __syncthreads();
   // lower chain (thread 0) and upper chain (thread 32): pop while the turn
-  // is not strictly left (lower) / not strictly right (upper)
+  // is not strictly left (lower) / not strictly right (upper).  The chain is
+  // sequential, so its latency is what counts: the next point is loaded one
+  // step ahead, the top two stack entries stay in registers (1 top, 2 below
+  // it) and the stack keeps coordinates, one load per pop.
   if (tid == 0 || tid == 32) {
-    // the top two stack entries stay in registers (t1 top, t2 below it)
     const int c = tid == 0 ? 0 : 1;
     uint16_t* q = st[c];
-    unsigned long long* kq = stk[c];
+    int2* cq = reinterpret_cast<int2*>(stk[c]);
     int n = 0;
-    long long x1 = 0, y1 = 0, x2 = 0, y2 = 0;
-    unsigned long long prev = ~0ull;
+    int x1 = 0, y1 = 0, x2 = 0, y2 = 0;
+    int2 nxt = sp[0];
     for (int p = 0; p < m; ++p) {
-      const unsigned long long kp = sk[p];
-      if (kp == prev) continue;
-      prev = kp;
-      const long long px = key_x(kp), py = key_y(kp);
+      const int2 cur = nxt;
+      if (p + 1 < m) nxt = sp[p + 1];
+      if (n > 0 && cur.x == x1 && cur.y == y1) continue;  // equal points: the first (lowest index) stands
       while (n >= 2) {
-        const long long cr2 = (x1 - x2) * (py - y2) - (y1 - y2) * (px - x2);
+        const long long cr2 = (long long)(x1 - x2) * (cur.y - y2) - (long long)(y1 - y2) * (cur.x - x2);
         if (c == 0 ? cr2 > 0 : cr2 < 0) break;
         --n;
         x1 = x2; y1 = y2;
-        if (n >= 2) { const unsigned long long k2 = kq[n - 2]; x2 = key_x(k2); y2 = key_y(k2); }
+        if (n >= 2) { const int2 t = cq[n - 2]; x2 = t.x; y2 = t.y; }
       }
       q[n] = (uint16_t)p;
-      kq[n] = kp;
+      cq[n] = cur;
       ++n;
       x2 = x1; y2 = y1;
-      x1 = px; y1 = py;
+      x1 = cur.x; y1 = cur.y;
     }
     s_n[c] = n;
   }
