@@ -841,10 +841,11 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
 // maximum.  Bit k of a cell's mask: some point of the cell may fail edge k;
 // a cell entirely outside edge k keeps only bit k.  Byte code: 0 inside,
 // k + 1 only edge k, CELL_MULTI several edges.
-constexpr int CELL_ROW_BLOCKS = 16;
-constexpr int CELL_ROWS = GRID / CELL_ROW_BLOCKS;
 constexpr int CELL_THREADS = 256;
 
+// CELL_ROWS rows per group: a single set spreads 2-row groups over 64
+// blocks (latency), a batch takes 8-row groups in one block per set.
+template <int CELL_ROWS>
 __global__ void __launch_bounds__(CELL_THREADS) k_cells(Sets S, const uint32_t* gstatus, uint16_t* cells_base) {
   // blockIdx.y takes every gridDim.y-th group of CELL_ROWS rows
   __shared__ long long s_ax[MAXV][GRID];       // per edge: min of A x per column
@@ -1023,8 +1024,11 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
     }
   }
 #undef FIN
-  // one set: its rows over CELL_ROW_BLOCKS blocks; a batch: one block per set
-  k_cells<<<dim3(nsets, S.S == 1 ? CELL_ROW_BLOCKS : 1), CELL_THREADS, 0, st>>>(S, gstatus, cells);
+  // one set: its rows over GRID / 2 blocks; a batch: one block per set
+  if (S.S == 1)
+    k_cells<2><<<dim3(nsets, GRID / 2), CELL_THREADS, 0, st>>>(S, gstatus, cells);
+  else
+    k_cells<8><<<dim3(nsets, 1), CELL_THREADS, 0, st>>>(S, gstatus, cells);
   count_launches(3);
   return cudaGetLastError();
 }
