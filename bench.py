@@ -50,7 +50,7 @@ def peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("k_extremes.cu", "k_filter.cu", "internal.cuh"):
+    for f in ("k_extremes.cu", "k_filter.cu", "internal.cuh", "stream.cuh"):
         with open(os.path.join(ROOT, "paper_1405_3454_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

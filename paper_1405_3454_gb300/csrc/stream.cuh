@@ -98,10 +98,6 @@ __device__ __forceinline__ bool mbar_wait_status(unsigned long long* bar, unsign
   return mbar_wait_limit(bar, parity, status, WAIT_LIMIT_CYCLES);
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, WsHeader* h) {
-  return mbar_wait_status(bar, parity, &h->status);
-}
-
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
                                          unsigned long long* bar) {
   asm volatile(
@@ -119,21 +115,6 @@ struct StreamSmemT {
   unsigned long long full[NS];
   unsigned long long empty[NS];
   int id[NS];  // dynamic shares: the chunk in the stage, -1 = end of the stream
-};
-
-// Chunk c of a block's pair range [p0, p1) in processing order; `reverse`
-// walks the range last chunk first.
-struct StreamRange {
-  int64_t p0, p1, nchunks;
-  bool reverse;
-  __device__ __forceinline__ int64_t first_pair(int64_t c) const {
-    const int64_t k = reverse ? nchunks - 1 - c : c;
-    return p0 + k * CHUNK;
-  }
-  __device__ __forceinline__ int count(int64_t c) const {
-    const int64_t f = first_pair(c);
-    return (int)min((int64_t)CHUNK, p1 - f);
-  }
 };
 
 // The segments of a block's share [v0, v1) of the virtual pair axis, one
@@ -277,27 +258,6 @@ __device__ __forceinline__ void stream_init(SS& S) {
     mbar_init_fence();
   }
   __syncthreads();
-}
-
-// Producer (lane 0 of the producer warp): issue every chunk, waiting for a
-// free stage each time; then wait until the copies it issued have landed.
-template <class SS>
-__device__ __forceinline__ void stream_produce(SS& S, const StreamRange& R, const float4* P, WsHeader* h) {
-  constexpr int STAGES = SS::STAGES;
-  if ((threadIdx.x & 31) != 0) return;
-  int64_t c = 0;
-  for (; c < R.nchunks; ++c) {
-    const int s = (int)(c % STAGES);
-    const int64_t k = c / STAGES;
-    if (k > 0 && !mbar_wait(&S.empty[s], (unsigned)((k - 1) & 1), h)) break;
-    if (*reinterpret_cast<volatile uint32_t*>(&h->status) & HULL_DEVICE_TIMEOUT) break;
-    const unsigned bytes = (unsigned)R.count(c) * 16u;
-    mbar_arrive_tx(&S.full[s], bytes);
-    bulk_g2s(&S.stage[s][0], P + R.first_pair(c), bytes, &S.full[s]);
-  }
-  // drain: the last min(c, STAGES) copies must complete before the block exits
-  for (int64_t d = c > STAGES ? c - STAGES : 0; d < c; ++d)
-    mbar_wait(&S.full[d % STAGES], (unsigned)((d / STAGES) & 1), h);
 }
 
 }  // namespace cudapre
