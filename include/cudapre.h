@@ -212,7 +212,9 @@ hull_status hull_read_counters(const void* d_ws, int64_t* h_n_survivors,
 typedef struct hull_stats {
   int64_t n_survivors;      /* points not strictly inside the Step-2 polygon */
   int64_t n_escalated;      /* float32 decisions escalated to exact arithmetic */
-  int64_t n_refined;        /* survivors left by the refinement round (hull_compute) */
+  int64_t n_refined;        /* entries left by the refinement round (hull_compute); on one set
+                               this can include copies of a survivor (same index), which
+                               hull_compute's survivor buffer holds in reserved slots */
   int32_t polygon_vertices; /* vertices of the Step-2 polygon */
   uint32_t device_status;   /* HULL_DEVICE_* bits */
 } hull_stats;

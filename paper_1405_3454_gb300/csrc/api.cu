@@ -74,7 +74,7 @@ Layout layout(int64_t n, bool full) {
   L.cells = off;
   off += align_up(CELL_BYTES, 256);
   if (full) {
-    const int64_t cap = std::max<int64_t>(n, 1);
+    const int64_t cap = compute_capacity(n);
     L.tri = off; off += align_up(sizeof(int4) * 2 * REFINE_BINS, 256);
     L.small = off; off += align_up(sizeof(SmallWs), 256);
     L.keys_a = off; off += align_up(8 * (size_t)cap, 256);
@@ -171,7 +171,7 @@ Sets single_set(const float* d_xy, int64_t n, char* ws) {
 // Steps 1-3 shared by hull_prefilter and hull_compute.
 hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& L,
                           uint32_t* surv_idx, unsigned long long* surv_key, uint32_t* ext_out,
-                          const hull_options& o, cudaStream_t st) {
+                          const hull_options& o, cudaStream_t st, bool reserve = false) {
   WsHeader* h = reinterpret_cast<WsHeader*>(ws + L.header);
   const Sets S = single_set(d_xy, n, ws + L.header);
   mark(0, st);
@@ -183,7 +183,7 @@ hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& 
   HULL_TRY(launch_extremes(S, npairs, o.angles, o.filter, &h->status, ws + L.blockres, cells, o.grid, ext_out,
                            surv_idx, surv_key, st));  // marks boundary 2 between its two kernels
   mark(3, st);
-  HULL_TRY(launch_filter(S, npairs, o.filter, &h->status, cells, surv_idx, surv_key, o.grid, st));
+  HULL_TRY(launch_filter(S, npairs, o.filter, &h->status, cells, surv_idx, surv_key, o.grid, st, reserve));
   mark(4, st);
   return HULL_OK;
 }
@@ -293,10 +293,11 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
     HULL_TRY(launch_all_keys(d_xy, n, h, ka, va, st));
     mark(4, st);
   } else {
-    s = run_prefilter(d_xy, n, ws, L, va, ka, nullptr, o, st);
+    // the survivor buffers have room for reserved slots (compute_capacity)
+    s = run_prefilter(d_xy, n, ws, L, va, ka, nullptr, o, st, compute_reserves(n));
     if (s != HULL_OK) return s;
   }
-  const int64_t cap = std::max<int64_t>(n, 1);
+  const int64_t cap = compute_capacity(n);
   // The hull of the survivors.  With refinement the survivors in (ka, va)
   // are thinned into (kb, vb) first.  Sets up to SMALL_MAX points take the
   // one-block path; larger ones one cooperative launch of the device radix
@@ -434,7 +435,7 @@ hull_status hull_read_counters(const void* d_ws, int64_t* h_n_survivors, int64_t
   WsHeader hh;
   HULL_TRY(cudaMemcpyAsync(&hh, d_ws, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
   HULL_TRY(cudaStreamSynchronize(st));
-  if (h_n_survivors) *h_n_survivors = (int64_t)hh.n_surv;
+  if (h_n_survivors) *h_n_survivors = (int64_t)(hh.n_surv - hh.n_fill);
   if (h_n_escalated) *h_n_escalated = (int64_t)hh.n_escalated;
   return HULL_OK;
 }
@@ -445,7 +446,7 @@ hull_status hull_read_stats(const void* d_ws, hull_stats* h_out, void* stream) {
   WsHeader hh;
   HULL_TRY(cudaMemcpyAsync(&hh, d_ws, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
   HULL_TRY(cudaStreamSynchronize(st));
-  h_out->n_survivors = (int64_t)hh.n_surv;
+  h_out->n_survivors = (int64_t)(hh.n_surv - hh.n_fill);
   h_out->n_escalated = (int64_t)hh.n_escalated;
   h_out->n_refined = (int64_t)hh.n_surv2;
   h_out->polygon_vertices = hh.poly.m;

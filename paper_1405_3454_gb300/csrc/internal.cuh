@@ -3,6 +3,7 @@
 // public ABI (include/cudapre.h).
 #pragma once
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -101,6 +102,7 @@ struct WsHeader {
   uint32_t next_group[2];  // dynamic shares of one set: chunk-group counters of Step 1 and Step 3
   unsigned long long n_surv;      // survivors written by the inside test
   unsigned long long n_escalated; // float32 decisions escalated to int64
+  unsigned long long n_fill;      // copies of survivors filling reserved slots (hull_compute on one set)
   uint32_t bar_count, bar_gen;  // grid barrier of the cooperative large-set kernel
   uint32_t hist[8][256];  // radix-sort digit histograms (all passes)
   unsigned long long n_surv2;  // survivors left by the refinement round
@@ -206,10 +208,27 @@ cudaError_t launch_validate(const float* xy, int64_t n, uint32_t* status, cudaSt
 cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int filter, uint32_t* gstatus,
                             void* partials, uint16_t* cells, int grid, uint32_t* ext_out, uint32_t* surv_idx,
                             unsigned long long* surv_key, cudaStream_t st);
+// hull_compute on one set of at least RESERVE_MIN_POINTS points gives its
+// per-point buffers RESERVE_WARPS * RESERVE_FLUSH extra entries, so the
+// inside test may reserve survivor slots ahead (k_filter.cu): every warp
+// then writes at most RESERVE_FLUSH copies beyond its survivors.
+// Survivor positions stay below 2^32 (they are packed into 32 bits), so
+// the largest sets do without.
+constexpr int64_t RESERVE_MIN_POINTS = 1ll << 24;
+constexpr int64_t RESERVE_WARPS = 4096;
+constexpr int RESERVE_FLUSH = 256;
+inline bool compute_reserves(int64_t n) {
+  return n >= RESERVE_MIN_POINTS && n <= 0xFFFFFFFFll - RESERVE_WARPS * RESERVE_FLUSH;
+}
+inline int64_t compute_capacity(int64_t n) {
+  return std::max<int64_t>(n, 1) + (compute_reserves(n) ? RESERVE_WARPS * RESERVE_FLUSH : 0);
+}
+
 // Step 3 for every set: survivors (set-local indices, keys when surv_key is
 // not null) at the set's offset, counted in its header.
 cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32_t* gstatus, uint16_t* cells,
-                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st);
+                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st,
+                          bool reserve = false);
 // The large path (sort + chunked chain) of one point set; it runs only when
 // *count > SMALL_MAX and the set's status word is clear.
 struct LargeJob {

@@ -557,8 +557,10 @@ __global__ void __launch_bounds__(CW * 32) k_small_classify(Sets S, const uint32
     bool dup = false;
     for (int a = lane; a < m; a += 32) {
       const unsigned long long ka = __ldg(K + a);
-      if (ka == kv) {  // equal coordinates (rare): the lowest index stands for them
-        dup |= __ldg(V + a) < iv;
+      if (ka == kv) {  // equal coordinates (rare): the lowest index stands for them, and of
+                       // copies of one point (same index) the first position
+        const uint32_t ia = __ldg(V + a);
+        dup |= ia < iv || (ia == iv && a < v);
         continue;
       }
       const bool before = ka < kv;

@@ -129,3 +129,32 @@ def test_time_grows_linearly_with_n(gpu_lib):
         del d, ws
     r = ms[1 << 28] / ms[1 << 26]
     assert 2.0 < r < 4.4, ms
+
+
+@pytest.mark.parametrize("name", ["all_equal", "collinear", "ring"])
+def test_reserved_slots_when_everything_survives(gpu_lib, name):
+    """hull_compute on one set of 2^24 points or more reserves survivor slots
+    ahead and fills a warp's last block with copies of one of its survivors.
+    Sets where every point survives (a degenerate polygon, or points in
+    convex position) use the most slots: the hull must still equal the
+    oracle's, and the reported survivors exclude the copies."""
+    import torch
+    cp = gpu_lib
+    n = 1 << 24
+    rng = np.random.default_rng(24)
+    if name == "all_equal":
+        xy = np.tile(np.array([[3.0, -4.0]], np.float32), (n, 1))
+    elif name == "collinear":
+        k = rng.integers(-(1 << 20), 1 << 20, n)
+        xy = np.stack([k * 7, k * -3], 1).astype(np.float32)
+    else:
+        a = rng.uniform(0, 2 * np.pi, n)
+        xy = np.stack([np.round(8e6 * np.cos(a)), np.round(8e6 * np.sin(a))], 1).astype(np.float32)
+    want = oracle.cudapre(xy)
+    d = torch.from_numpy(xy).cuda()
+    for refine in (True, False):
+        out, cnt, ws = cp.compute(d, cp.Options(refine=refine))
+        torch.cuda.synchronize()
+        assert cp.device_status(ws) == (0, 0)
+        assert cp.as_index(out[:int(cnt.item())], int(cnt.item())).tolist() == want["hull"].tolist()
+        assert cp.read_stats(ws)["n_survivors"] == len(want["survivors"])
