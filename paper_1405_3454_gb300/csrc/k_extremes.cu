@@ -98,11 +98,20 @@ __device__ __forceinline__ float band_of(int v) {
   return v < 2 ? 0.0f : ((ANG == 0 && v >= 4) ? BAND_HI : BAND_LO);
 }
 
+// Value v alone, the same arithmetic as values32 (v is warp-uniform: no
+// indexed local array).
 template <int ANG>
 __device__ __forceinline__ float value32(int v, float x, float y) {
-  float t[Dirs<ANG>::NV];
-  values32<ANG>(x, y, t);
-  return t[v];
+  switch (v) {
+    case 0: return x;
+    case 1: return y;
+    case 2: return fmaf(x, F_2S3, -y);
+    case 3: return fmaf(y, F_2S3, x);
+    case 4: return ANG == 0 ? fmaf(y, -F_T75, x) : x - y;
+    case 5: return ANG == 0 ? fmaf(x, F_T75, y) : x + y;
+    case 6: return fmaf(-y, F_2S3, x);
+    default: return fmaf(x, F_2S3, y);
+  }
 }
 
 __device__ __forceinline__ float max3f(float a, float b, float c) {
