@@ -1,12 +1,15 @@
 // k_extremes.cu -- Step 1 and Step 2 of the CudaPre method (arXiv 1405.3454,
 // section 2): the 16 extreme points of the original and rotated point sets,
-// then the convex polygon of those points by Andrew's monotone chain, all in
-// one launch (the last block to finish runs the polygon stage).
+// then the convex polygon of those points by Andrew's monotone chain.  A
+// streaming pass (k_extremes32 / k_extremes64) leaves one candidate per
+// block and direction; a finishing kernel (one block per set) reduces them
+// exactly and builds the polygon with its edge records, inner box and
+// inscribed circle; k_cells builds the cell grid of the inside test.
 //
-// One pass over the points: each thread loads two points per 16-byte load and
-// keeps, for every direction, its best candidate.  The paper's separate
-// rotation kernels and per-direction reductions (section 4.2) become one
-// fused projection + argreduction; no rotated copy is ever written.
+// One pass over the points, streamed through shared memory by bulk copies.
+// The paper's separate rotation kernels and per-direction reductions
+// (section 4.2) become one fused projection + argreduction; no rotated copy
+// is ever written.
 //
 // FP32 mode: each direction tracks a float32 value, an order-preserving
 // multiple of the rotated coordinate that one fused multiply-add computes,

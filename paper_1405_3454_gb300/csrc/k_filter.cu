@@ -5,7 +5,8 @@
 // As in the paper each block first copies the polygon into shared memory and
 // one thread tests several points.  The survivors are compacted in the same
 // pass through per-warp staging buffers in shared memory (one global atomic
-// per buffer flush, no block-wide barrier in the streaming loop).
+// per buffer flush, no block-wide barrier in the streaming loop; see WarpOut
+// for the reserving variant of hull_compute on large sets).
 //
 // FP32 mode.  A point inside the polygon's inscribed circle (float32 test with
 // a proven margin) is discarded at once.  Every other point goes, with its

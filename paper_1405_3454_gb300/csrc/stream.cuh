@@ -5,9 +5,11 @@
 // One producer warp (its lane 0) issues cp.async.bulk copies of CHUNK pairs
 // per stage; the copy engine signals the stage's "full" mbarrier with the
 // transferred byte count.  Consumer warps wait on "full", copy their pairs to
-// registers and arrive on the stage's "empty" mbarrier at once, so the
-// producer can refill it while they compute.  Every wait is bounded: on
-// timeout the kernel records HULL_DEVICE_TIMEOUT and stops streaming.
+// registers and arrive on the stage's "empty" mbarrier as soon as they no
+// longer read the stage (the inside test at once, the extreme search after
+// its rare path), so the producer can refill it while they compute.  Every
+// wait is bounded: on timeout the kernel records HULL_DEVICE_TIMEOUT and
+// stops streaming.
 #pragma once
 
 #include <algorithm>
