@@ -110,7 +110,9 @@ void hull_default_options(hull_options* opt);
  * for the defaults).  The workspace needs no initialisation. */
 size_t hull_prefilter_workspace_bytes(int64_t n, const hull_options* opt);
 
-/* Bytes of workspace needed by hull_compute for n points. */
+/* Bytes of workspace needed by hull_compute for n points: about 24 bytes per
+ * point plus 1.3 MB; from 2^24 points on, about 25 MB more (survivor slots
+ * the inside test may reserve ahead). */
 size_t hull_workspace_bytes(int64_t n, const hull_options* opt);
 
 /* Steps 1-3 of section 2 on one point set.
@@ -128,8 +130,10 @@ hull_status hull_prefilter(const float* d_xy, int64_t n, void* d_ws, size_t ws_b
                            uint32_t* d_extreme_idx, const hull_options* opt, void* stream);
 
 /* The whole method on one point set: Steps 1-3, compaction of the survivors,
- * then the hull of the survivors by a device radix sort and Andrew's
- * monotone chain (section 3, case (2)).
+ * then the hull of the survivors (section 3, case (2)): a second discard
+ * round (option refine; points strictly inside triangles of farthest
+ * survivors), then up to 8192 points a hull built in one block or on the
+ * whole GPU, more a device radix sort and Andrew's monotone chain.
  *   d_ws             at least hull_workspace_bytes(n).
  *   d_hull_idx       room for n uint32: hull vertex indices, see Hull above.
  *   d_n_hull         one int64: the number of hull vertices (0 when n == 0). */
