@@ -92,3 +92,15 @@ def test_argument_errors_without_gpu(lib):
     assert lib_.hull_selftest_wait(P + 16, 1000, 0) == 1
     assert lib_.hull_selftest_wait(P, 0, 0) == 1
     assert lib_.hull_selftest_wait(P, (1 << 31) + 1, 0) == 1
+
+
+def test_compute_workspace_has_room_for_reserved_slots(lib):
+    # hull_compute on 2^24 points or more may reserve up to 4096 warps x 256
+    # survivor slots beyond n: its workspace holds that many more (key, index)
+    # entries in both buffer pairs; hull_prefilter's workspace does not change
+    a, b = cp.hull_workspace_bytes((1 << 24) - 1), cp.hull_workspace_bytes(1 << 24)
+    assert b - a >= 2 * (8 + 4) * 4096 * 256
+    assert cp.hull_prefilter_workspace_bytes(1 << 24) == cp.hull_prefilter_workspace_bytes((1 << 24) - 1)
+    # the largest sets do without (survivor positions stay below 2^32)
+    top = (1 << 32) - 1
+    assert cp.hull_workspace_bytes(top) - cp.hull_workspace_bytes(top - 1) < 64
