@@ -196,7 +196,9 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
  *   d_hull_idx, d_n_hull, opt, stream   as for hull_compute.
  * The first call on a device looks up the array's device address (a runtime
  * query, not a stream operation); make it before any stream capture begins
- * on that device.  The counters that must start at zero are cleared by every
+ * on that device.  The address is kept for the life of the process: after
+ * cudaDeviceReset on a device (which unloads the library's module there) do
+ * not call this entry point on that device again.  The counters that must start at zero are cleared by every
  * call on its stream.  There is ONE such workspace per device: calls on the
  * same device that may overlap on the GPU (other streams, other host threads)
  * race on it and corrupt each other's results; order them on one stream.
@@ -233,6 +235,28 @@ hull_status hull_read_stats(const void* d_ws, hull_stats* h_out, void* stream);
  * (room for 16 uint32; may be NULL).  Synchronises the stream (host memory). */
 hull_status hull_read_polygon(const void* d_ws, int32_t* h_m, int32_t* h_xy,
                               uint32_t* h_idx, void* stream);
+
+/* One set of the last hull_batch / hull_batch_ranges call on a batch
+ * workspace (host memory). */
+typedef struct hull_set_info {
+  int32_t polygon_vertices;   /* vertices of the set's Step-2 polygon */
+  int32_t polygon_xy[32];     /* their integer coordinates, as hull_read_polygon */
+  uint32_t polygon_idx[16];   /* their indices within the set */
+  uint32_t extreme_idx[16];   /* the set's 16 extremes (Extremes above), indices
+                                 within the set; 0xFFFFFFFF when the set is empty */
+  int64_t n_survivors;        /* points of the set left by Step 3 */
+  int64_t n_escalated;        /* its float32 decisions escalated to exact arithmetic */
+  int64_t n_refined;          /* entries left by its refinement round */
+  uint32_t device_status;     /* the set's HULL_DEVICE_* bits */
+  uint32_t pad_;
+} hull_set_info;
+
+/* Reads set s (0 <= s < S) of the last batch call on d_ws, a workspace laid
+ * out for (n_total, S) as hull_batch_workspace_bytes; synchronises the
+ * stream.  A set whose steps were skipped (a device condition of the batch)
+ * reads as empty. */
+hull_status hull_batch_read_set(const void* d_ws, int64_t n_total, int32_t S, int32_t s, hull_set_info* h_out,
+                                void* stream);
 
 /* Device-side condition bits (HULL_DEVICE_*) recorded by the last call on this
  * workspace; synchronises the stream.  Returns HULL_OK when no bit is set,

@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version", "hull_read_stats",
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
     "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes", "hull_batch_ranges",
-    "hull_selftest_wait",
+    "hull_selftest_wait", "hull_batch_read_set",
 )
 HULL_STAGES = 6
 STAGE_NAMES = ("validate", "extremes", "polygon", "filter", "hull", "final")
@@ -53,6 +53,13 @@ class HullOptions(ctypes.Structure):
 class HullStats(ctypes.Structure):
     _fields_ = [("n_survivors", ctypes.c_int64), ("n_escalated", ctypes.c_int64), ("n_refined", ctypes.c_int64),
                 ("polygon_vertices", ctypes.c_int32), ("device_status", ctypes.c_uint32)]
+
+
+class HullSetInfo(ctypes.Structure):
+    _fields_ = [("polygon_vertices", ctypes.c_int32), ("polygon_xy", ctypes.c_int32 * 32),
+                ("polygon_idx", ctypes.c_uint32 * 16), ("extreme_idx", ctypes.c_uint32 * 16),
+                ("n_survivors", ctypes.c_int64), ("n_escalated", ctypes.c_int64), ("n_refined", ctypes.c_int64),
+                ("device_status", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
 
 
 class HullError(RuntimeError):
@@ -121,6 +128,8 @@ def load(path: str | None = None):
     lib.hull_batch_ranges.restype = st
     lib.hull_selftest_wait.argtypes = [P, i64, P]
     lib.hull_selftest_wait.restype = st
+    lib.hull_batch_read_set.argtypes = [P, i64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(HullSetInfo), P]
+    lib.hull_batch_read_set.restype = st
     _lib = lib
     return lib
 
@@ -342,6 +351,21 @@ def read_polygon(ws, stream=None):
            "hull_read_polygon")
     k = int(m.value)
     return k, [[xy[2 * i], xy[2 * i + 1]] for i in range(k)], [int(idx[i]) for i in range(k)]
+
+
+def batch_read_set(ws, n_total: int, S: int, s: int, stream=None) -> dict:
+    """Set s of the last batch call on a batch workspace laid out for
+    (n_total, S): its polygon (m, xy, point indices within the set), its 16
+    extremes (indices within the set), its counters and status bits."""
+    o = HullSetInfo()
+    _check(load().hull_batch_read_set(_ptr(ws), int(n_total), int(S), int(s), ctypes.byref(o),
+                                      _stream_handle(stream)), "hull_batch_read_set")
+    m = int(o.polygon_vertices)
+    return {"m": m, "poly_xy": [[o.polygon_xy[2 * k], o.polygon_xy[2 * k + 1]] for k in range(m)],
+            "poly_idx": [int(o.polygon_idx[k]) for k in range(m)],
+            "extremes": [int(v) for v in o.extreme_idx], "n_survivors": int(o.n_survivors),
+            "n_escalated": int(o.n_escalated), "n_refined": int(o.n_refined),
+            "device_status": int(o.device_status)}
 
 
 def device_status(ws, stream=None):

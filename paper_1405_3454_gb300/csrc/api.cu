@@ -470,6 +470,31 @@ hull_status hull_read_polygon(const void* d_ws, int32_t* h_m, int32_t* h_xy, uin
   return HULL_OK;
 }
 
+hull_status hull_batch_read_set(const void* d_ws, int64_t n_total, int32_t S, int32_t s, hull_set_info* h_out,
+                                void* stream) {
+  if (!d_ws || !h_out || S < 0 || n_total < 0 || s < 0 || s >= S) return HULL_ERR_INVALID_ARG;
+  const BatchLayout L = batch_layout(n_total, S);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader hh;
+  const char* src = static_cast<const char*>(d_ws) + L.hdr + (size_t)s * HEADER_BYTES;
+  HULL_TRY(cudaMemcpyAsync(&hh, src, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
+  HULL_TRY(cudaStreamSynchronize(st));
+  std::memset(h_out, 0, sizeof(*h_out));
+  const int m = std::max(0, std::min(hh.poly.m, MAXV));
+  h_out->polygon_vertices = m;
+  for (int k = 0; k < m; ++k) {
+    h_out->polygon_xy[2 * k] = hh.poly.vx[k];
+    h_out->polygon_xy[2 * k + 1] = hh.poly.vy[k];
+    h_out->polygon_idx[k] = hh.poly.vidx[k];
+  }
+  for (int k = 0; k < NSLOT; ++k) h_out->extreme_idx[k] = hh.poly.ext[k];
+  h_out->n_survivors = (int64_t)(hh.n_surv - hh.n_fill);
+  h_out->n_escalated = (int64_t)hh.n_escalated;
+  h_out->n_refined = (int64_t)hh.n_surv2;
+  h_out->device_status = hh.status;
+  return HULL_OK;
+}
+
 hull_status hull_get_device_status(const void* d_ws, uint32_t* h_bits, void* stream) {
   if (!d_ws) return HULL_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

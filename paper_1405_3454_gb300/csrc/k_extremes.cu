@@ -70,9 +70,12 @@ __device__ __forceinline__ double score64(int ang, int d, float x, float y) {
 }
 
 // Order-preserving unsigned key of a (non-NaN) double: integer comparisons
-// of keys order the doubles (FP64 compares are slow on this part).
+// of keys order the doubles (FP64 compares are slow on this part).  -0.0 and
+// +0.0 are equal doubles, so they must get one key: adding +0.0 in
+// round-to-nearest turns -0.0 into +0.0 and leaves every other value as it
+// is; without it a -0.0 score would lose a tie it wins by index.
 __device__ __forceinline__ unsigned long long dkey(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(__dadd_rn(v, 0.0));
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
@@ -537,12 +540,8 @@ __device__ __noinline__ void ext_block_result(const float* xy, const uint32_t* w
 
 // Blocks per SM the streaming search is compiled for (registers per thread)
 // and the stages of its shared-memory ring.
-#ifndef EXT_MIN_BLOCKS
-#define EXT_MIN_BLOCKS 2
-#endif
-#ifndef EXT_STAGES
-#define EXT_STAGES 6
-#endif
+constexpr int EXT_MIN_BLOCKS = 2;
+constexpr int EXT_STAGES = 6;
 
 template <int ANG>
 __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(Sets S, int64_t ppb, uint32_t* gstatus,
@@ -730,12 +729,6 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(Sets S, int64_t ppb, const
 // 16 extremes, Step 2 (the polygon, its edge records and inner box) and the
 // cell grid of the inside test.
 
-// Phase hooks of the finishing kernel (no code unless a timing build
-// defines FSTAMP).
-#ifndef FSTAMP
-#define FSTAMP(i) ((void)0)
-#endif
-
 template <int ANG, int FIN_THREADS>
 __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb, const uint32_t* gstatus,
                                                                const BlockBest* bres, uint32_t* ext_out,
@@ -763,7 +756,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
   // points outside the 16-byte pairs: the head point and an odd last point
   const bool lead = !dead && head == 1;
   const bool trail = !dead && n > head && ((n - head) & 1);
-  FSTAMP(0);
   // One warp per direction: its lanes take the set's block results (and the
   // loose points) in turn, then an exact butterfly by (score key, index).
   for (int d = warp; d < ND; d += FIN_THREADS / 32) {
@@ -791,7 +783,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
     if (lane == 0) s_ext[d] = bi;
   }
   __syncthreads();
-  FSTAMP(1);
   if (tid == 0) {
     if (ANG == 0) {
       // 120 degrees from 30 degrees: with the correctly rounded constants,
@@ -812,7 +803,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
     hull16_warp(xy, s_ext, &h->poly, grid_on);
   }
   __syncthreads();
-  FSTAMP(2);
   // The loose points' inside test (Step 3): exact against every edge.
   if (!dead && tid == 0) {
     const int mm = h->poly.m;
@@ -833,7 +823,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
       }
     }
   }
-  FSTAMP(3);
   // Sets below GRID_MIN_POINTS use one cell listing every edge (the cell
   // grid of larger sets is built by k_cells).
   const int m = h->poly.m;
@@ -842,7 +831,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
     cells[0] = (uint16_t)((1u << m) - 1u);
     reinterpret_cast<uint8_t*>(cells + GRID * GRID)[0] = (uint8_t)CELL_MULTI;
   }
-  FSTAMP(5);
 }
 
 // ----------------------------------------------------------------------------

@@ -90,10 +90,7 @@ struct Tester<HULL_FILTER_EXACT> {
 // index and key): the hull kernels keep one of equal points, so copies of a
 // point change no hull, and h->n_fill counts them.  On the 2^28-point disk
 // this took the pass from 0.411 to 0.387 ms and added 2.6% copies.
-#ifndef FLT_WBUF
-#define FLT_WBUF 320
-#endif
-constexpr int WBUF = FLT_WBUF;
+constexpr int WBUF = 320;
 constexpr int WFLUSH = RESERVE_FLUSH;        // entries per reserving-mode flush
 static_assert(WFLUSH + 32 <= WBUF, "a push adds at most 32");
 constexpr int WROW_IDX = WBUF + 4;  // a row's slots: room to shift by up to 3 entries
@@ -271,17 +268,11 @@ struct WarpOut {
 // No point is read from memory twice.
 
 // Blocks per SM the inside test is compiled for, and its ring's stages.
-#ifndef FLT_MIN_BLOCKS
-#define FLT_MIN_BLOCKS 3
-#endif
-#ifndef FLT_STAGES
-#define FLT_STAGES 2
-#endif
+constexpr int FLT_MIN_BLOCKS = 3;
+constexpr int FLT_STAGES = 2;
 using FilterStream = StreamSmemT<FLT_STAGES>;
 // Points per thread between two drains of the queue (8 = once per chunk).
-#ifndef FLT_DRAIN_POINTS
-#define FLT_DRAIN_POINTS 2
-#endif
+constexpr int FLT_DRAIN_POINTS = 2;
 constexpr int QCAP = 31 + 32 * FLT_DRAIN_POINTS;  // left over + pushed between drains (a per-warp stack)
 
 struct Cells {

@@ -35,9 +35,6 @@ namespace {
 
 constexpr int SB = 1024;      // threads
 
-#ifndef STAMP
-#define STAMP(i) ((void)0)
-#endif
 constexpr int NCH = SMALL_NCH;  // chunks (one warp each)
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -136,7 +133,6 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
     return;
   }
   const int m = (int)m64;
-  STAMP(0);
   int P2 = 2;
   while (P2 < m) P2 <<= 1;
   unsigned long long* sk = reinterpret_cast<unsigned long long*>(sm);
@@ -157,7 +153,6 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
       qk[r] = (r < NE && i < m) ? kin[i] : ~0ull;
       qv[r] = (r < NE && i < m) ? vin[i] : ~0u;
     }
-    STAMP(1);
     for (int k = 2; k <= P2; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
         if (j >= SB) {  // partner in the same thread: element r ^ (j / SB)
@@ -218,7 +213,6 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
       if (r < NE) { sk[r * SB + tid] = qk[r]; si[r * SB + tid] = qv[r]; }
     __syncthreads();
   }
-  STAMP(2);
   // dedupe: first of each run of equal keys (lowest index) -> unique arrays
   constexpr int E = SMALL_MAX / SB;  // elements per thread (blocked)
   unsigned long long rk[E];
@@ -254,7 +248,6 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
     return;
   }
   const Pts P{ux, uy};
-  STAMP(3);
   // chunk chains: warp w, lane 0 lower / lane 1 upper
   const int C = (u + NCH - 1) / NCH;
   {
@@ -263,7 +256,6 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
     if (lane < 2) s_cnt[lane][w] = chunk_chain(P, lo, hi, chain + lane * SMALL_MAX + w * C, lane == 0 ? 1 : -1);
   }
   __syncthreads();
-  STAMP(4);
   // publish to global
   for (int i = tid; i < u; i += SB) {
     sw->pts[i] = make_int2(ux[i], uy[i]);
@@ -283,7 +275,6 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
     sw->base[tid][NCH] = run;
   }
   if (tid == 0) { sw->u = u; sw->C = C; sw->active = 1; }
-  STAMP(5);
 }
 
 // tiny: the whole hull of a set with at most TINY_MAX survivors in one

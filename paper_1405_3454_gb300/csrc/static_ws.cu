@@ -32,7 +32,10 @@ std::mutex g_mu;
 void* g_ptr[MAX_DEVICES] = {};
 
 // Set-up, once per device, with that device current: the device address of
-// g_scratch.  Returns nullptr when the query fails.
+// g_scratch.  Returns nullptr when the query fails.  The address is cached
+// for the process; cudaDeviceReset unloads the module and makes it stale,
+// so the header tells callers not to use this entry point on a device after
+// resetting it.
 void* scratch_of_current_device() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;

@@ -35,12 +35,8 @@ constexpr int64_t MAX_STREAM_BLOCKS = 4096;  // partial-result slots per call
 // claim groups of DYN_GROUP chunks of the rest from a counter in the set's
 // header, so blocks that draw more bandwidth take more chunks (equal static
 // shares ended up to 2x apart in time on a 2^28-point set).
-#ifndef DYN_GROUP
-#define DYN_GROUP 4
-#endif
-#ifndef DYN_STATIC_PCT
-#define DYN_STATIC_PCT 75
-#endif
+constexpr int DYN_GROUP = 4;
+constexpr int DYN_STATIC_PCT = 75;
 
 inline int stream_waves(int sets, int64_t npairs, int64_t resident_blocks) {
   if (sets <= 1) return 1;

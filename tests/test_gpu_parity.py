@@ -185,7 +185,8 @@ def test_launch_shapes_do_not_change_results(gpu_lib):
 
 def test_validate_flags_out_of_domain(gpu_lib):
     import torch
-    for bad in (np.float32(0.5), np.float32(np.nan), np.float32(np.inf), np.float32(2 ** 24 + 2)):
+    for bad in (np.float32(0.5), np.float32(np.nan), np.float32(np.inf), np.float32(-np.inf),
+                np.float32(2 ** 24 + 2), np.float32(-(2 ** 24 + 2)), np.float32(-0.5)):
         xy = synth.square(10000, 1, 100)
         xy[1234, 1] = bad
         d = to_dev(xy)
@@ -194,8 +195,10 @@ def test_validate_flags_out_of_domain(gpu_lib):
         code, bits = gpu_lib.device_status(ws)
         assert bits & gpu_lib.HULL_DEVICE_DOMAIN and code == 2
         assert int(cnt.item()) == 0
-    # in-domain input passes validation
+    # in-domain input passes validation, boundary values and -0.0 included
     xy = synth.square(10000, 1, 100)
+    xy[10] = (2.0 ** 24, -(2.0 ** 24))
+    xy[20] = (-0.0, 0.0)
     out, cnt, ws = gpu_lib.compute(to_dev(xy), gpu_lib.Options(validate=True))
     assert gpu_lib.device_status(ws) == (0, 0)
     assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()

@@ -304,3 +304,27 @@ def test_remaining_fraction_cumulative_angles_closed_form():
     assert len(dirs) == 12
     assert abs(f - frac) < 0.003, (f, frac)
     assert len(res["poly_xy"]) == 12
+
+
+def test_check_domain_accepts_exactly_the_stated_domain():
+    # The domain (finite, integer-valued, |v| <= 2^24, -0.0 equal to 0) fixed
+    # where the paper is silent on precision.  Each bad value, alone in an
+    # otherwise valid set, in either coordinate, must be rejected; the
+    # boundary values must pass.
+    base = np.array([[1.0, 2.0], [-3.0, 4.0], [5.0, -6.0]], np.float32)
+    good = [0.0, -0.0, 1.0, -1.0, 2.0 ** 24, -(2.0 ** 24), 2.0 ** 24 - 1, 12345678.0]
+    bad = [np.nan, np.inf, -np.inf, 0.5, -0.5, 2.0 ** 24 + 2, -(2.0 ** 24 + 2), 2.0 ** 25, 1e30, 8388607.5,
+           np.float32(1.5e-45)]
+    assert oracle.check_domain(base)
+    assert oracle.check_domain(np.zeros((0, 2), np.float32))
+    for v in good:
+        for c in (0, 1):
+            xy = base.copy()
+            xy[1, c] = v
+            assert oracle.check_domain(xy), (v, c)
+    for v in bad:
+        for row in (0, 2):
+            for c in (0, 1):
+                xy = base.copy()
+                xy[row, c] = v
+                assert not oracle.check_domain(xy), (v, row, c)
