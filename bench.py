@@ -156,32 +156,40 @@ def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def cpu_oracle_sample(n_sample: int, seed: int, xy=None):
-    """The CPU oracle (as it stands, single-threaded) on the first n_sample
-    points of the workload's generator stream (or on xy when given):
-    (Gpoints/s, seconds)."""
+def cpu_oracle_sample(n_sample: int, seed: int, xy=None, threads: int = 1):
+    """The CPU oracle (as it stands) on the first n_sample points of the
+    workload's generator stream (or on xy when given), single-threaded or
+    with its point loops split over `threads` host threads (0: all):
+    (Gpoints/s, seconds, threads used)."""
     import oracle
     import synth
     if xy is None:
         xy = synth.disk(n_sample, seed)
     oracle.cudapre(xy[:1024])  # load the library outside the timing
     t0 = time.perf_counter()
-    oracle.cudapre(xy)
+    if threads == 1:
+        oracle.cudapre(xy)
+        used = 1
+    else:
+        _, used = oracle.cudapre_mt(xy, 0, threads)
     dt = time.perf_counter() - t0
-    return n_sample / dt / 1e9, dt
+    return n_sample / dt / 1e9, dt, used
 
 
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
         return 0
-    # Bounded samples: 2^22 points per step (a few seconds of CPU each).
+    # Bounded samples: 2^22 points per step, the oracle's point loops on all
+    # host cores (a fraction of a second each).
     n_sample = 1 << 22
+    import synth
+    xy = synth.disk(n_sample, SEED)
     for _ in range(args.warmup):
-        cpu_oracle_sample(n_sample, SEED)
-    times = []
+        cpu_oracle_sample(n_sample, SEED, xy, threads=0)
+    times, cores = [], 1
     for _ in range(args.steps):
-        _, dt = cpu_oracle_sample(n_sample, SEED)
+        _, dt, cores = cpu_oracle_sample(n_sample, SEED, xy, threads=0)
         times.append(dt)
     t = sum(times) / len(times)
     v = n_sample / t / 1e9
@@ -190,12 +198,53 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+int64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_points_per_step": n_sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "first 2^22 points of the disk workload's generator stream per step"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "first 2^22 points of the disk workload's generator stream per step, "
+                                   "the oracle's point loops split over all host threads"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def small_set_leg(cp, torch, synth, exact, fp32, steps, sh, stream):
+    """hull_compute on the 1,000,000-point square, each call timed alone by
+    CUDA events after an L2 flush: microseconds per call and Gpoints/s for
+    both arithmetic forms."""
+    if steps <= 0:
+        return None
+    n1 = 1_000_000
+    d1 = torch.from_numpy(synth.square(n1, SEED, 1 << 20)).cuda()
+    ws_b = cp.hull_workspace_bytes(n1)
+    ws1 = cp.workspace(ws_b)
+    out1 = torch.empty(n1, dtype=torch.int32, device="cuda")
+    cnt1 = torch.empty(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {"workload": "1,000,000 points, integers uniform in [-2^20, 2^20]^2 (seeded)",
+           "l2": "256 MB buffer written before every timed call"}
+    for name, opt in (("plain_exact", exact), ("fp32_filtered", fp32)):
+        def call():
+            code = cp.hull_compute(d1.data_ptr(), n1, ws1.data_ptr(), ws_b, out1.data_ptr(), cnt1.data_ptr(), opt,
+                                   sh)
+            if code:
+                raise cp.HullError(code, "hull_compute")
+        for _ in range(5):
+            call()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(k & 255)
+            evs[k][0].record(stream)
+            call()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in evs)
+        mean = sum(ms) / len(ms)
+        res[name] = {"us_per_call": mean * 1e3, "us_median": ms[len(ms) // 2] * 1e3,
+                     "value": n1 / (mean * 1e-3) / 1e9, "unit": UNIT, "calls": steps}
+    res["hull_vertices"] = int(cnt1.item())
+    del d1, ws1, out1, flush
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args):
@@ -376,6 +425,11 @@ def run_ours(args):
     e2e = {"value": world * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": d2h // e2e_steps}
 
+    # The 1,000,000-point square (integers uniform in [-2^20, 2^20]^2), both
+    # arithmetic forms: latency-bound (8 MB fits in L2, so L2 is flushed by
+    # writing a 256 MB buffer before every timed call).
+    small = small_set_leg(cp, torch, synth, exact, fp32, args.small_steps, sh, stream)
+
     # Batched workload: many independent sets in one hull_batch call.
     batch = None
     if args.batch_sets > 0:
@@ -423,7 +477,8 @@ def run_ours(args):
         pxy, pstarts, psizes, _ = synth.serving_pool(args.serve_per_decile, SEED + 29 + rank)
         dpool = torch.from_numpy(pxy).cuda()
         del pxy
-        server = serve.Server(dpool, max_points=256 << 20, max_sets=2048, slots=2, opt=fp32)
+        budget = 64 << 30
+        server = serve.Server(dpool, budget_bytes=budget, max_points=256 << 20, max_sets=2048, streams=2, opt=fp32)
         req_set, unit_arr = synth.serving_requests(args.serve_requests, len(psizes), SEED + 31 + rank)
         mean_size = float(psizes[req_set].mean())
         cap_gpts = batch["value"] / world if batch else value / world
@@ -437,17 +492,23 @@ def run_ours(args):
         serving = {"requests": args.serve_requests, "mean_points": mean_size,
                    "pool": "%d sets (%d per size decile of [1e4, 1.6e7), log-uniform), %d points resident"
                            % (len(psizes), args.serve_per_decile, int(psizes.sum())),
-                   "capacity_gpoints_per_s": cap_gpts, "slots": 2, "max_batch_points": 256 << 20,
-                   "max_batch_sets": 2048, "memory_budget": "64 GiB", "ingestion": "excluded (pool resident)",
-                   **runs}
+                   "capacity_gpoints_per_s": cap_gpts, "streams": 2, "max_batch_points": 256 << 20,
+                   "max_batch_sets": 2048, "memory_budget_bytes": budget,
+                   "admission": "a batch is formed only if its workspace and outputs fit in the largest free "
+                                "block of the budget's arena; the head request waits otherwise",
+                   "ingestion": "excluded (pool resident)", **runs}
         del server, dpool
         torch.cuda.empty_cache()
 
     cpu = None
     if world == 1 and rank == 0 and not args.no_cpu:
-        v, dt = cpu_oracle_sample(n, SEED, host)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "the whole workload: all %d points of the same disk (%.1f s, single thread)" % (n, dt)}
+        v, dt, used = cpu_oracle_sample(n, SEED, host, threads=0)
+        v1, dt1, _ = cpu_oracle_sample(n, SEED, host, threads=1)
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": "the whole workload: all %d points of the same disk (%.1f s on %d host threads)"
+                         % (n, dt, used),
+               "host_threads": os.cpu_count(),
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "seconds": dt1}}
 
     if rank == 0:
         line = {
@@ -463,6 +524,7 @@ def run_ours(args):
                                           "cudapre_speedup": ms_np / ms},
                          "prefilter_only": prefilter,
                          "near_edge": near_edge,
+                         "small_set_1m": small,
                          "batch": batch,
                          "serving": serving},
             "stages_ms_per_step": stages_out,
@@ -489,6 +551,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--small-steps", type=int, default=200, help="timed calls of the 1M-point leg (0: skip it)")
     ap.add_argument("--batch-sets", type=int, default=4096, help="sets of the batched leg (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=100_000, help="requests of the serving leg (0: skip it)")

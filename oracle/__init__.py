@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
         subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-Wno-stringop-overflow", "-shared", "-fPIC",
-                               "-o", tmp, _SRC])
+                               "-pthread", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,6 +59,8 @@ def _get():
         lib.oracle_brute_hull.argtypes = [P, i64, P]
         lib.oracle_brute_hull.restype = i64
         lib.oracle_cudapre.argtypes = [P, i64, ctypes.c_int, P, P, P, P, P, P, P]
+        lib.oracle_cudapre_mt.argtypes = [P, i64, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P]
+        lib.oracle_cudapre_mt.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -161,3 +163,22 @@ def cudapre(xy, angles: int = ANGLES_CUMULATIVE) -> dict:
         "survivors": surv[: int(ns[0])].copy(),
         "hull": hl[: int(nh[0])].copy(),
     }
+
+
+def cudapre_mt(xy, angles: int = ANGLES_CUMULATIVE, threads: int = 0) -> tuple[dict, int]:
+    """cudapre() with the point loops split over host threads (0: all
+    hardware threads); returns (the same dict as cudapre, threads used)."""
+    a = _pts(xy)
+    n = a.shape[0]
+    ext = np.full(16, -1, dtype=np.int64)
+    m = np.zeros(1, dtype=np.int32)
+    pxy = np.zeros(32, dtype=np.int32)
+    surv = np.empty(max(n, 1), dtype=np.int64)
+    ns = np.zeros(1, dtype=np.int64)
+    hl = np.empty(max(n, 1), dtype=np.int64)
+    nh = np.zeros(1, dtype=np.int64)
+    t = _get().oracle_cudapre_mt(a.ctypes.data, n, angles, int(threads), ext.ctypes.data, m.ctypes.data,
+                                 pxy.ctypes.data, surv.ctypes.data, ns.ctypes.data, hl.ctypes.data, nh.ctypes.data)
+    mm = int(m[0])
+    return ({"extremes": ext, "poly_xy": pxy[: 2 * mm].reshape(mm, 2).copy(),
+             "survivors": surv[: int(ns[0])].copy(), "hull": hl[: int(nh[0])].copy()}, int(t))

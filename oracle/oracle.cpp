@@ -21,6 +21,9 @@
 //                          monotone chain; applied to all points it is the
 //                          plain definition of the convex hull.
 //   O5 oracle_brute_hull-- O(n^3) definition of the hull for tiny inputs.
+//   oracle_cudapre_mt   -- the same steps split over host threads, for the
+//                          all-cores CPU baseline (tested equal to the
+//                          single-thread oracle).
 //
 // Conventions where the paper is silent (each is a stated reading):
 //   * Rotation is counter-clockwise: x' = x c - y s, y' = x s + y c, each
@@ -44,6 +47,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -338,6 +342,94 @@ void oracle_cudapre(const float* xy, int64_t n, int angles, int64_t* ext_idx,
   int64_t s = oracle_prefilter(xy, n, poly_xy, m, surv_idx);
   *n_surv = s;
   *n_hull = oracle_hull(xy, surv_idx, s, hull_idx);
+}
+
+// The whole method as oracle_cudapre, with the point loops split over
+// `threads` host threads (0: all hardware threads), for the all-cores CPU
+// baseline.  Step 1: each thread scans a contiguous range in increasing index
+// with the same strict comparisons, and the ranges' winners are combined in
+// range order keeping the earlier on equal values, so ties still go to the
+// lowest index.  Step 3: each range's survivors, concatenated in range order
+// (ascending).  The hull of the survivors: Andrew's chain per range, then
+// once more over the union of the range hulls (every vertex of the whole
+// hull is a vertex of the hull of its range, and equal coordinates keep the
+// lowest index at both levels).  Returns the thread count used.
+int oracle_cudapre_mt(const float* xy, int64_t n, int angles, int threads,
+                      int64_t* ext_idx, int32_t* m_out, int32_t* poly_xy,
+                      int64_t* surv_idx, int64_t* n_surv, int64_t* hull_idx,
+                      int64_t* n_hull) {
+  int T = threads > 0 ? threads : (int)std::thread::hardware_concurrency();
+  if (T < 1) T = 1;
+  if ((int64_t)T > n / 4096 + 1) T = (int)(n / 4096 + 1);
+  std::vector<int64_t> lo(T + 1);
+  for (int t = 0; t <= T; ++t) lo[t] = n * t / T;
+  auto run = [&](auto&& fn) {
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) th.emplace_back(fn, t);
+    for (auto& x : th) x.join();
+  };
+  // Step 1
+  Rot tab[4];
+  angle_table(angles, tab);
+  std::vector<int64_t> part_idx((size_t)T * 16, -1);
+  std::vector<double> part_val((size_t)T * 16, 0.0);
+  run([&](int t) {
+    for (int g = 0; g < 4; ++g) {
+      int64_t* pi = &part_idx[(size_t)t * 16 + 4 * g];
+      double* pv = &part_val[(size_t)t * 16 + 4 * g];
+      for (int64_t i = lo[t]; i < lo[t + 1]; ++i) {
+        double x = (double)xy[2 * i];
+        double y = (double)xy[2 * i + 1];
+        double px = rot_x(x, y, tab[g]);
+        double py = rot_y(x, y, tab[g]);
+        if (pi[0] < 0 || px < pv[0]) { pv[0] = px; pi[0] = i; }
+        if (pi[1] < 0 || px > pv[1]) { pv[1] = px; pi[1] = i; }
+        if (pi[2] < 0 || py < pv[2]) { pv[2] = py; pi[2] = i; }
+        if (pi[3] < 0 || py > pv[3]) { pv[3] = py; pi[3] = i; }
+      }
+    }
+  });
+  for (int k = 0; k < 16; ++k) {
+    int64_t bi = -1;
+    double bv = 0.0;
+    for (int t = 0; t < T; ++t) {
+      int64_t i = part_idx[(size_t)t * 16 + k];
+      double v = part_val[(size_t)t * 16 + k];
+      if (i < 0) continue;
+      bool better = (k & 1) ? v > bv : v < bv;  // odd slots are maxima
+      if (bi < 0 || better) { bi = i; bv = v; }
+    }
+    ext_idx[k] = bi;
+  }
+  // Step 2
+  int64_t poly_idx[16];
+  int m = n > 0 ? oracle_hull16(xy, ext_idx, poly_idx, poly_xy) : 0;
+  *m_out = m;
+  // Step 3
+  std::vector<std::vector<int64_t>> surv(T);
+  run([&](int t) {
+    for (int64_t i = lo[t]; i < lo[t + 1]; ++i)
+      if (!oracle_strictly_inside(poly_xy, m, to_i(xy[2 * i]), to_i(xy[2 * i + 1])))
+        surv[t].push_back(i);
+  });
+  int64_t c = 0;
+  for (int t = 0; t < T; ++t)
+    for (int64_t i : surv[t]) surv_idx[c++] = i;
+  *n_surv = c;
+  // hull of the survivors: per range, then over the union of range hulls
+  std::vector<std::vector<Pt>> part(T);
+  run([&](int t) {
+    std::vector<Pt> pts;
+    pts.reserve(surv[t].size());
+    for (int64_t i : surv[t]) pts.push_back({to_i(xy[2 * i]), to_i(xy[2 * i + 1]), i});
+    part[t] = andrew(sorted_unique(std::move(pts)));
+  });
+  std::vector<Pt> all;
+  for (int t = 0; t < T; ++t) all.insert(all.end(), part[t].begin(), part[t].end());
+  std::vector<Pt> hull = andrew(sorted_unique(std::move(all)));
+  for (size_t j = 0; j < hull.size(); ++j) hull_idx[j] = hull[j].idx;
+  *n_hull = (int64_t)hull.size();
+  return T;
 }
 
 }  // extern "C"

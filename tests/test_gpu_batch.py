@@ -163,12 +163,12 @@ def test_server_slots_match_oracle_and_simulation_completes(gpu_lib):
     cp = gpu_lib
     pxy, starts, sizes, _ = synth.serving_pool(1, 9900, 1e3, 2e5)
     pool = torch.from_numpy(pxy).cuda()
-    server = serve.Server(pool, max_points=1 << 20, max_sets=64, slots=2)
+    server = serve.Server(pool, budget_bytes=1 << 30, max_points=1 << 20, max_sets=64, streams=2)
     picks = [[0, 3, 5, 9, 9], [1, 2, 4, 6, 7, 8]]
     slots = []
     for k, p in enumerate(picks):
         slot = server.free_slot()
-        server.launch(slot, starts[p], sizes[p], k)
+        assert server.launch(slot, starts[p], sizes[p], k)
         slots.append(slot)
     torch.cuda.synchronize()
     done = server.poll()
@@ -193,7 +193,7 @@ def test_set_alone_equals_in_batch_equals_in_serving_mix(gpu_lib):
     cp = gpu_lib
     pxy, starts, sizes, _ = synth.serving_pool(1, 9950, 1e3, 3e5)
     pool = torch.from_numpy(pxy).cuda()
-    server = serve.Server(pool, max_points=1 << 22, max_sets=32, slots=1)
+    server = serve.Server(pool, budget_bytes=1 << 30, max_points=1 << 22, max_sets=32, streams=1)
     rng = np.random.default_rng(9951)
     for j in range(len(sizes)):
         a, b = int(starts[j]), int(sizes[j])
@@ -209,7 +209,7 @@ def test_set_alone_equals_in_batch_equals_in_serving_mix(gpu_lib):
         hoff = hoff.cpu().numpy()
         in_batch = out[hoff[3]:hoff[4]].cpu().tolist()
         slot = server.free_slot()
-        server.launch(slot, starts[mix[::-1]], sizes[mix[::-1]], j)
+        assert server.launch(slot, starts[mix[::-1]], sizes[mix[::-1]], j)
         torch.cuda.synchronize()
         assert [t for _, t in server.poll()] == [j]
         so = slot["hoff"][:len(mix) + 1].cpu().numpy()
@@ -219,3 +219,43 @@ def test_set_alone_equals_in_batch_equals_in_serving_mix(gpu_lib):
     want = oracle.cudapre(pxy[starts[0]:starts[0] + sizes[0]])["hull"].astype(np.int64) + starts[0]
     h, c, _ = cp.compute(pool[int(starts[0]):int(starts[0] + sizes[0])])
     assert (cp.as_index(h, int(c.item())) + starts[0]).tolist() == want.tolist()
+
+
+def test_server_admits_by_memory_budget(gpu_lib):
+    # A budget that holds one large batch at a time: requests wait for
+    # memory (in arrival order), one that could never fit is refused, the
+    # bytes in flight never exceed the budget, and every served hull is the
+    # oracle's.
+    import torch
+    from paper_1405_3454_gb300 import serve
+    cp = gpu_lib
+    pxy, starts, sizes, _ = synth.serving_pool(1, 9960, 1e4, 4e5)
+    pool = torch.from_numpy(pxy).cuda()
+    big = int(np.argmax(sizes))
+    budget = serve.batch_bytes(cp, int(sizes[big]) + 2000, 2, cp.Options()) + 4096
+    server = serve.Server(pool, budget_bytes=budget, max_points=1 << 22, max_sets=8, streams=3)
+    # a request above the budget is refused before any CUDA call
+    huge = np.array([0], np.int64), np.array([len(pxy)], np.int64)
+    if serve.batch_bytes(cp, len(pxy), 1, cp.Options()) > budget:
+        with pytest.raises(cp.HullError):
+            server.launch(server.free_slot(), huge[0], huge[1], -1)
+    req_set = np.array([big, big, 0, big, 1, 2, big, 3], np.int64)
+    res = serve.simulate(server, starts, sizes, req_set, np.zeros(len(req_set)))
+    assert not res.refused and np.all(np.isfinite(res.completion_s))
+    assert res.peak_bytes <= budget and res.deferred >= 1
+    # a pool row range as one request larger than the whole budget
+    starts2 = np.concatenate([starts, [0]]).astype(np.int64)
+    sizes2 = np.concatenate([sizes, [len(pxy)]]).astype(np.int64)
+    res2 = serve.simulate(server, starts2, sizes2, np.array([0, len(sizes), 1], np.int64), np.zeros(3))
+    if serve.batch_bytes(cp, len(pxy), 1, cp.Options()) > budget:
+        assert res2.refused == [1] and np.isnan(res2.latency_s[1])
+    assert np.isfinite(res2.latency_s[0]) and np.isfinite(res2.latency_s[2])
+    # served results are the oracle's hulls
+    for j in (big, 0, 1):
+        slot = server.free_slot()
+        assert server.launch(slot, starts[[j]], sizes[[j]], j)
+        torch.cuda.synchronize()
+        server.poll()
+        want = oracle.cudapre(pxy[starts[j]:starts[j] + sizes[j]])["hull"].astype(np.int64) + starts[j]
+        h = slot["hoff"].cpu().numpy()
+        assert slot["out"][h[0]:h[1]].cpu().tolist() == want.tolist()

@@ -328,3 +328,27 @@ def test_check_domain_accepts_exactly_the_stated_domain():
                 xy = base.copy()
                 xy[row, c] = v
                 assert not oracle.check_domain(xy), (v, row, c)
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8, 0])
+def test_multithreaded_oracle_equals_single_thread(threads):
+    # the all-cores CPU baseline runs oracle_cudapre_mt; it must give exactly
+    # the single-thread oracle's extremes, polygon, survivors and hull,
+    # including lowest-index ties that straddle the threads' ranges
+    for kind, n, seed in ((1, 200_001, 3), (0, 65_536, 4), (2, 100_003, 5), (1, 5, 6), (0, 0, 7)):
+        xy = synth.shape(kind, n, seed, 9)
+        if n > 1000:
+            xy[n // 2] = xy[n // 5]      # a duplicate of an early point late in the set
+            xy[n - 1] = xy[0]
+        for angles in (0, 1):
+            want = oracle.cudapre(xy, angles)
+            got, used = oracle.cudapre_mt(xy, angles, threads)
+            assert used >= 1
+            for k in ("extremes", "poly_xy", "survivors", "hull"):
+                assert np.array_equal(got[k], want[k]), (kind, n, angles, k)
+    sq = synth.square(40_000, 8, 50)   # heavy duplication: many ties across ranges
+    for angles in (0, 1):
+        got, _ = oracle.cudapre_mt(sq, angles, threads)
+        want = oracle.cudapre(sq, angles)
+        for k in ("extremes", "poly_xy", "survivors", "hull"):
+            assert np.array_equal(got[k], want[k]), k

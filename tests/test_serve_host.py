@@ -3,7 +3,7 @@ serving workload's request stream."""
 import numpy as np
 
 import synth
-from paper_1405_3454_gb300.serve import Batcher
+from paper_1405_3454_gb300.serve import ALIGN, Arena, Batcher
 
 
 def test_batcher_fifo_and_caps():
@@ -50,3 +50,60 @@ def test_serving_pool_deciles():
         assert edges[d] - 1 <= s <= edges[d + 1]
     assert starts[0] == 0 and np.all(np.diff(starts) == sizes[:-1])
     assert len(xy) == sizes.sum() and set(shapes.tolist()) <= {0, 1, 2}
+
+
+def test_arena_first_fit_coalesces_and_tracks_peak():
+    a = Arena(10 * ALIGN)
+    x = a.alloc(3 * ALIGN)
+    y = a.alloc(ALIGN + 1)          # rounded up to 2 ALIGN
+    z = a.alloc(5 * ALIGN)
+    assert (x, y, z) == (0, 3 * ALIGN, 5 * ALIGN) and a.in_use == 10 * ALIGN
+    assert a.alloc(1) is None and a.largest_free() == 0
+    a.free(y)
+    assert a.largest_free() == 2 * ALIGN and a.alloc(3 * ALIGN) is None
+    a.free(x)                        # merges with y's block
+    assert a.largest_free() == 5 * ALIGN
+    a.free(z)                        # everything merges back
+    assert a.free_blocks == [(0, 10 * ALIGN)] and a.in_use == 0 and a.peak == 10 * ALIGN
+
+
+def test_batcher_defers_on_memory_keeps_fifo_and_refuses_the_impossible():
+    need = lambda pts, sets: 10 * pts + 100 * sets    # fake sizes
+    b = Batcher(max_points=1000, max_sets=4, need=need, budget=5000)
+    for rid, size in enumerate([100, 300, 600, 20, 50]):
+        b.push(rid, size)
+    assert b.take(room=0) == []                       # head waits: nothing fits
+    assert b.take(room=4300) == [(0, 100), (1, 300)]   # 10*400+200 = 4200; adding 600 would not fit
+    # 600 alone needs 6100 > budget: refused, not deferred forever; the
+    # requests behind it go on
+    assert b.take(room=1000) == [(3, 20), (4, 50)]
+    assert b.refused == [2] and len(b) == 0
+
+
+def test_admission_simulation_never_exceeds_the_budget():
+    # Requests of random sizes arrive; batches are formed within the arena's
+    # largest free block and complete in random order.  The bytes in flight
+    # stay within the budget, no request overtakes an earlier one, and only
+    # requests that could never fit are refused.
+    rng = np.random.default_rng(12)
+    need = lambda pts, sets: 8 * pts + 256 * sets
+    budget = 64 * 1024
+    arena = Arena(budget)
+    b = Batcher(max_points=4000, max_sets=5, need=need, budget=arena.capacity)
+    sizes = rng.integers(1, 9000, 400)
+    for r, s in enumerate(sizes):
+        b.push(r, int(s))
+    inflight, order = [], []
+    while len(b) or inflight:
+        batch = b.take(arena.largest_free()) if len(b) else []
+        if batch:
+            off = arena.alloc(need(sum(s for _, s in batch), len(batch)))
+            assert off is not None and arena.in_use <= budget
+            inflight.append(off)
+            order.extend(r for r, _ in batch)
+        elif inflight:
+            arena.free(inflight.pop(int(rng.integers(len(inflight)))))
+    assert order == sorted(order)
+    assert sorted(order + b.refused) == list(range(400))
+    assert b.refused == [r for r, s in enumerate(sizes) if need(int(s), 1) > arena.capacity]
+    assert arena.peak <= budget and arena.in_use == 0
