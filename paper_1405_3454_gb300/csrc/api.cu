@@ -81,7 +81,7 @@ Layout layout(int64_t n, bool full) {
     L.vals_a = off; off += align_up(4 * (size_t)cap, 256);
     L.keys_b = off; off += align_up(8 * (size_t)cap, 256);
     L.vals_b = off; off += align_up(4 * (size_t)cap, 256);
-    L.tilecnt = off; off += align_up(4 * 256 * (size_t)sort_tiles(cap), 256);
+    L.tilecnt = off; off += align_up(8 * 256 * (size_t)sort_tiles(cap), 256);
     const int64_t nch0 = (cap + CHAIN_C0 - 1) / CHAIN_C0;
     L.cnt = off; off += align_up(4 * 4 * (size_t)nch0, 256);
   }
@@ -117,7 +117,7 @@ BatchLayout batch_layout(int64_t n_total, int32_t S) {
   put(L.vals_a, 4 * n);
   put(L.keys_b, 8 * n);
   put(L.vals_b, 4 * n);
-  put(L.tilecnt, 4 * 256 * (n / SORT_TILE + s + 1));
+  put(L.tilecnt, 8 * 256 * (n / SORT_TILE + s + 1));
   put(L.cnt, 4 * 4 * (n / CHAIN_C0 + s + 1));
   put(L.hstage, 4 * n);
   L.total = off;
@@ -321,7 +321,7 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   J.h = h;
   J.count = count;
   J.ka = kin; J.va = vin; J.kb = kot; J.vb = vot;
-  J.tilecnt = reinterpret_cast<uint32_t*>(ws + L.tilecnt);
+  J.tilecnt = reinterpret_cast<unsigned long long*>(ws + L.tilecnt);
   J.cnt = reinterpret_cast<uint32_t*>(ws + L.cnt);
   J.out_idx = d_hull_idx;
   J.out_n = d_n_hull;
@@ -408,7 +408,7 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
   HULL_TRY(launch_small_hull(SS, bstatus, which, kin, vin, reinterpret_cast<SmallWs*>(ws + L.small), hstage, hcnt,
                              st));
   LargeJob* jobs = reinterpret_cast<LargeJob*>(ws + L.jobs);
-  HULL_TRY(launch_batch_jobs(SS, bstatus, which, kin, vin, kot, vot, reinterpret_cast<uint32_t*>(ws + L.tilecnt),
+  HULL_TRY(launch_batch_jobs(SS, bstatus, which, kin, vin, kot, vot, reinterpret_cast<unsigned long long*>(ws + L.tilecnt),
                              reinterpret_cast<uint32_t*>(ws + L.cnt), hstage, hcnt, jobs, &bw->njobs, st));
   mark(5, st);
   LargeJob none{};

@@ -105,6 +105,8 @@ struct WsHeader {
   unsigned long long n_fill;      // copies of survivors filling reserved slots (hull_compute on one set)
   uint32_t bar_count, bar_gen;  // grid barrier of the cooperative large-set kernel
   uint32_t hist[8][256];  // radix-sort digit histograms (all passes)
+  uint32_t tile_next[8];  // radix sort: next tile to claim, per pass
+  unsigned long long key_or, key_nor;  // radix sort: OR of the keys and of their complements
   unsigned long long n_surv2;  // survivors left by the refinement round
   uint32_t n_lower, n_upper;   // small-set hull: vertices of the lower / upper chain
   float refine_r2;             // refinement: squared radius of a disk inside the winners' polygon (or -1)
@@ -238,7 +240,7 @@ struct LargeJob {
   uint32_t* va;
   unsigned long long* kb;           // second buffer pair (capacity cap)
   uint32_t* vb;
-  uint32_t* tilecnt;                // 256 * sort_tiles(cap)
+  unsigned long long* tilecnt;      // 256 * sort_tiles(cap) tile status words of the sort
   uint32_t* cnt;                    // 4 * ceil(cap / CHAIN_C0)
   uint32_t* out_idx;                // hull vertex indices (local to the set)
   int64_t* out_n;
@@ -303,7 +305,7 @@ cudaError_t launch_wait_selftest(uint32_t* status, long long limit, cudaStream_t
 cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, int64_t n_xy, uint32_t* bstatus, int64_t* pp,
                                cudaStream_t st);
 cudaError_t launch_batch_jobs(const Sets& S, const uint32_t* bstatus, int which, unsigned long long* ka, uint32_t* va,
-                              unsigned long long* kb, uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out,
+                              unsigned long long* kb, uint32_t* vb, unsigned long long* tilecnt, uint32_t* cnt, uint32_t* out,
                               int64_t* out_n, LargeJob* jobs, int* njobs, cudaStream_t st);
 cudaError_t launch_batch_emit(const Sets& S, uint32_t* bstatus, const int64_t* hcnt, const uint32_t* hstage,
                               int64_t* hull_offsets, int64_t* hull_idx, cudaStream_t st);

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TB) k_batch_setup(Sets S, int64_t n_total, int
 // (which = 1) or after Step 3 (which = 0) exceed the one-block hull, listed
 // in jobs[0 .. *njobs) in any order.
 __global__ void k_batch_jobs(Sets S, const uint32_t* bstatus, int which, unsigned long long* ka, uint32_t* va,
-                             unsigned long long* kb, uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out,
+                             unsigned long long* kb, uint32_t* vb, unsigned long long* tilecnt, uint32_t* cnt, uint32_t* out,
                              int64_t* out_n, LargeJob* jobs, int* njobs) {
   if (*reinterpret_cast<const volatile uint32_t*>(bstatus)) return;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S.S; s += gridDim.x * blockDim.x) {
@@ -137,7 +137,7 @@ cudaError_t launch_batch_setup(const Sets& S, int64_t n_total, int64_t n_xy, uin
 }
 
 cudaError_t launch_batch_jobs(const Sets& S, const uint32_t* bstatus, int which, unsigned long long* ka, uint32_t* va,
-                              unsigned long long* kb, uint32_t* vb, uint32_t* tilecnt, uint32_t* cnt, uint32_t* out,
+                              unsigned long long* kb, uint32_t* vb, unsigned long long* tilecnt, uint32_t* cnt, uint32_t* out,
                               int64_t* out_n, LargeJob* jobs, int* njobs, cudaStream_t st) {
   const unsigned g = (unsigned)std::min<int64_t>(((int64_t)S.S + 255) / 256, 1024);
   k_batch_jobs<<<g, 256, 0, st>>>(S, bstatus, which, ka, va, kb, vb, tilecnt, cnt, out, out_n, jobs, njobs);

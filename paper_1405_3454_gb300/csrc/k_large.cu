@@ -4,21 +4,20 @@
 // the hull of the points that remain; the paper ran Qhull on the CPU there).
 //
 // One cooperative launch does the whole stage for a list of jobs (one per
-// point set), its phases separated by a grid barrier: the sort is 7 passes
-// of 8-bit digits over the 52-bit keys, each reduce-then-scan (per-tile digit
-// counts, a per-digit scan over tiles, a stable scatter in which each warp
-// ranks its own 512-element slice); the chain is chunked -- level 0 chains
-// every sorted chunk of CHAIN_C0 keys, each later level concatenates
-// CHAIN_FAN consecutive chunk chains (still sorted) and chains them again,
-// until one chunk is left.  A hull vertex of the whole set is a vertex of
-// every chunk chain that contains it, so the last chain is the hull.  Stacks
-// are written in place over the consumed input (a push never overtakes the
-// read cursor); among equal keys the lowest index is kept.
+// point set), its phases separated by a grid barrier.  The sort runs one
+// sweep per 8-bit digit of the 52-bit keys that varies among them (at most
+// 7): each sweep reads and writes every element once, tiles finding their
+// output offsets by decoupled look-back (see sort_pass).  The chain is
+// chunked: level 0 chains every sorted chunk of CHAIN_C0 keys, each later
+// level concatenates CHAIN_FAN consecutive chunk chains (still sorted) and
+// chains them again, until one chunk is left.  A hull vertex of the whole
+// set is a vertex of every chunk chain that contains it, so the last chain
+// is the hull.  Among equal keys the lowest index is kept.
 //
 // Every size is read on the device.  A job whose count is at most SMALL_MAX
 // (the one-block path has written its result) or whose status word is set
-// is skipped by every block alike.  Barrier waits are bounded: on expiry the
-// kernel records HULL_DEVICE_TIMEOUT and returns.
+// is skipped by every block alike.  Barrier and look-back waits are
+// bounded: on expiry the kernel records HULL_DEVICE_TIMEOUT and returns.
 #include "internal.cuh"
 
 namespace cudapre {
@@ -70,233 +69,448 @@ __device__ __forceinline__ long long cross_k(unsigned long long o, unsigned long
   return (long long)(key_x(a) - ox) * (key_y(b) - oy) - (long long)(key_y(a) - oy) * (key_x(b) - ox);
 }
 
-// One monotone chain kept as an in-place stack K[base..base+n), V likewise.
+// One monotone chain as a stack of n entries in three tiers: the top WIN
+// entries in registers (wk[0] = top); below them the bottom SD entries of
+// the stack in the thread's column of shared memory; entries from SD up in
+// K[base ..], V likewise.  An entry moves down a tier only when it leaves
+// the register window and comes back when a pop brings it in again, so the
+// stacks of ordinary chunks (a few dozen entries deep at most) never wait
+// for global memory.  finish() leaves the chain in K[base .. base + n).
 // UPPER = false: lower chain (pop while the turn is not strictly left);
 // UPPER = true: upper chain walked left to right (pop while not strictly right).
+constexpr int WIN = 4;
+constexpr int SD = 12;  // shared-memory entries per stack
+// Elements a chain loads together before pushing them.
+constexpr int CB = 8;
+
+// Shared memory of the chain phases (the same dynamic buffer as the sort's):
+// per thread, CB staged input elements and two stacks' shared tiers, each
+// element i of thread t at i * LBLOCK + t (a warp's accesses fall in
+// distinct banks).
+struct ChainSmem {
+  unsigned long long keys[CB * LBLOCK];
+  uint32_t vals[CB * LBLOCK];
+  unsigned long long tk[2][SD * LBLOCK];
+  uint32_t tv[2][SD * LBLOCK];
+};
+
 template <bool UPPER>
 struct Stack {
   unsigned long long* K;
   uint32_t* V;
+  unsigned long long* TK;  // this stack's shared tier, thread column
+  uint32_t* TV;
   int64_t base;
   int64_t n;
-  unsigned long long t1, t2;  // top and second keys (valid when n >= 1 / 2)
+  unsigned long long wk[WIN];
+  uint32_t wv[WIN];
 
-  __device__ __forceinline__ void init(unsigned long long* k, uint32_t* v, int64_t b) {
-    K = k; V = v; base = b; n = 0; t1 = t2 = 0;
+  __device__ __forceinline__ void init(unsigned long long* k, uint32_t* v, int64_t b, ChainSmem& C, int which) {
+    K = k; V = v; base = b; n = 0;
+    TK = C.tk[which] + threadIdx.x;
+    TV = C.tv[which] + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < WIN; ++i) { wk[i] = 0; wv[i] = 0; }
+  }
+  __device__ __forceinline__ void put(int64_t e, unsigned long long k, uint32_t v) {
+    if (e < SD) { TK[e * LBLOCK] = k; TV[e * LBLOCK] = v; }
+    else { K[base + e] = k; V[base + e] = v; }
+  }
+  __device__ __forceinline__ void pop() {
+#pragma unroll
+    for (int i = 0; i < WIN - 1; ++i) { wk[i] = wk[i + 1]; wv[i] = wv[i + 1]; }
+    --n;
+    if (n >= WIN) {
+      const int64_t e = n - WIN;
+      if (e < SD) { wk[WIN - 1] = TK[e * LBLOCK]; wv[WIN - 1] = TV[e * LBLOCK]; }
+      else { wk[WIN - 1] = K[base + e]; wv[WIN - 1] = V[base + e]; }
+    }
   }
   __device__ __forceinline__ void push(unsigned long long key, uint32_t idx) {
-    if (n >= 1 && key == t1) {  // equal coordinates: keep the lowest index
-      const uint32_t old = V[base + n - 1];
-      if (idx < old) V[base + n - 1] = idx;
+    if (n >= 1 && key == wk[0]) {  // equal coordinates: keep the lowest index
+      if (idx < wv[0]) wv[0] = idx;
       return;
     }
     while (n >= 2) {
-      const long long c = cross_k(t2, t1, key);
+      const long long c = cross_k(wk[1], wk[0], key);
       if (UPPER ? (c < 0) : (c > 0)) break;
-      --n;
-      t1 = t2;
-      if (n >= 2) t2 = K[base + n - 2];
+      pop();
     }
-    K[base + n] = key;
-    V[base + n] = idx;
-    ++n;
-    t2 = t1;
-    t1 = key;
-  }
-};
-
-struct SortSmem {
-  uint32_t hs[SORT_PASSES][256];
-  uint32_t wc[WARPS][256];
-  uint32_t sw[WARPS];
-  uint32_t carry;
-};
-
-// Digit histograms of all passes in one read (they do not depend on order).
-__device__ void hist_all(SortSmem& S, const unsigned long long* keys, int64_t m, uint32_t* hist) {
-  for (int k = threadIdx.x; k < SORT_PASSES * 256; k += LBLOCK) (&S.hs[0][0])[k] = 0;
-  __syncthreads();
-  for (int64_t j = (int64_t)blockIdx.x * LBLOCK + threadIdx.x; j < m; j += (int64_t)gridDim.x * LBLOCK) {
-    const unsigned long long k = keys[j];
+    if (n >= WIN) put(n - WIN, wk[WIN - 1], wv[WIN - 1]);
 #pragma unroll
-    for (int p = 0; p < SORT_PASSES; ++p) atomicAdd(&S.hs[p][digit(k, p)], 1u);
+    for (int i = WIN - 1; i > 0; --i) { wk[i] = wk[i - 1]; wv[i] = wv[i - 1]; }
+    wk[0] = key;
+    wv[0] = idx;
+    ++n;
+  }
+  __device__ __forceinline__ void finish() {
+#pragma unroll
+    for (int i = 0; i < WIN; ++i)
+      if (i < n) { K[base + n - 1 - i] = wk[i]; V[base + n - 1 - i] = wv[i]; }
+    const int64_t low = min(n - WIN, (int64_t)SD);  // shared-tier entries
+    for (int64_t e = 0; e < low; ++e) { K[base + e] = TK[e * LBLOCK]; V[base + e] = TV[e * LBLOCK]; }
+  }
+};
+
+// ----------------------------------------------------------------------------
+// One-sweep LSD radix sort.  Every pass reads each (key, index) once and
+// writes it once.  A block claims tiles of SORT_TILE elements in order from
+// a counter; per tile it ranks the elements by digit (per-warp counts, the
+// lanes sharing a digit found by nine ballots; one warp per 512-element
+// slice, so ranks are stable), publishes
+// the tile's per-digit counts in the tile's status words, and finds how many
+// elements of each digit all earlier tiles hold by looking back over their
+// status words (decoupled look-back: a word holds either the tile's own
+// count or the inclusive prefix through that tile; the walk adds counts until
+// it meets a prefix).  The tile is then reordered by digit in shared memory
+// and written out in that order, so consecutive threads write consecutive
+// addresses.  Status words carry the pass number, so one clearing per job
+// serves every pass.  A pass whose digit is the same for every key moves
+// nothing and is skipped: a bit varies among the keys iff both the OR of the
+// keys and the OR of their complements have it.  The digit histogram a pass
+// needs is counted while the pass before it writes its output (the first
+// one by a read of the keys, with the two ORs).
+
+constexpr unsigned long long ST_AGG = 1ull << 62;     // the word holds the tile's own count
+constexpr unsigned long long ST_PREFIX = 2ull << 62;  // ... the inclusive prefix through the tile
+constexpr int ST_TAG_SHIFT = 58;                      // 4-bit pass tag (pass + 1)
+constexpr unsigned long long ST_COUNT = (1ull << ST_TAG_SHIFT) - 1;
+constexpr int LOOK = 8;  // status words of earlier tiles read at once in the look-back
+
+__device__ __forceinline__ unsigned long long st_word(unsigned long long state, int pass, unsigned long long c) {
+  return state | ((unsigned long long)(pass + 1) << ST_TAG_SHIFT) | c;
+}
+
+// Shared memory of the sort (dynamic): the tile reordered by digit, and the
+// per-warp / per-digit bookkeeping.  The histogram phase reuses the key area.
+struct SortSmem {
+  unsigned long long keys[SORT_TILE];
+  uint32_t vals[SORT_TILE];
+  uint32_t wc[WARPS][256];     // per warp: digit counts, then their exclusive prefix over warps
+  uint32_t lstart[256];        // first position of each digit in the reordered tile
+  long long delta[256];        // output position - position in the reordered tile, per digit
+  uint32_t excl[256];          // elements of all keys with a smaller digit (this pass)
+  uint32_t hn[256];            // histogram of the next pass's digit, this block's part
+  uint32_t wsum[WARPS];
+  uint32_t tile;
+};
+
+// Passes whose digit varies among the keys, as a bit mask (bit p: pass p).
+__device__ __forceinline__ unsigned live_passes(const WsHeader* h) {
+  const unsigned long long v = h->key_or & h->key_nor;
+  unsigned mask = 0;
+  for (int p = 0; p < SORT_PASSES; ++p)
+    if ((v >> (8 * p)) & 255ull) mask |= 1u << p;
+  return mask;
+}
+
+// One read of the keys: the digit histogram of pass `pass` (when or_too,
+// also the OR of the keys and of their complements, and the job's tile
+// status words cleared).
+__device__ __noinline__ void hist_read(SortSmem& S, const unsigned long long* keys, int64_t m, int pass, WsHeader* h,
+                                       bool or_too, unsigned long long* status, int64_t nstatus) {
+  // HCOPIES sub-histograms (warp w counts into copy w % HCOPIES) in the key
+  // area, to spread the shared-memory atomics
+  constexpr int HCOPIES = 4;
+  static_assert(HCOPIES * 256 * 4 <= (int)sizeof(S.keys), "sub-histograms fit");
+  uint32_t* hs = reinterpret_cast<uint32_t*>(S.keys);
+  for (int k = threadIdx.x; k < HCOPIES * 256; k += LBLOCK) hs[k] = 0;
+  __syncthreads();
+  uint32_t* mine = hs + ((threadIdx.x >> 5) % HCOPIES) * 256;
+  const int64_t gt = (int64_t)blockIdx.x * LBLOCK + threadIdx.x, gs = (int64_t)gridDim.x * LBLOCK;
+  unsigned long long o = 0, no = 0;
+  for (int64_t j = gt; j < m; j += gs) {
+    const unsigned long long k = __ldcs(keys + j);
+    o |= k;
+    no |= ~k;
+    atomicAdd(&mine[digit(k, pass)], 1u);
+  }
+  if (or_too) {
+    for (int off = 16; off; off >>= 1) {
+      o |= __shfl_xor_sync(FULL, o, off);
+      no |= __shfl_xor_sync(FULL, no, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicOr(&h->key_or, o);
+      atomicOr(&h->key_nor, no);
+    }
+    for (int64_t j = gt; j < nstatus; j += gs) status[j] = 0ull;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < SORT_PASSES * 256; k += LBLOCK) {
-    const uint32_t c = (&S.hs[0][0])[k];
-    if (c) atomicAdd(hist + k, c);
+  for (int k = threadIdx.x; k < 256; k += LBLOCK) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < HCOPIES; ++q) c += hs[q * 256 + k];
+    if (c) atomicAdd(&h->hist[pass][k], c);
   }
+  __syncthreads();
 }
 
-// Per-tile digit counts of one pass: tilecnt[d * NT + t].
-__device__ void tile_count(SortSmem& S, const unsigned long long* keys, int64_t m, int pass, int64_t NT,
-                           uint32_t* tilecnt) {
-  const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
-  const int lane = threadIdx.x & 31;
-  for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
-    S.hs[0][threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t b = t * SORT_TILE;
-    for (int r = 0; r < ROWS; ++r) {
-      const int64_t j = b + (int64_t)r * LBLOCK + threadIdx.x;
-      const uint32_t d = j < m ? digit(keys[j], pass) : 256u;
-      const unsigned peers = __match_any_sync(FULL, d);
-      if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&S.hs[0][d], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    tilecnt[(int64_t)threadIdx.x * NT + t] = S.hs[0][threadIdx.x];
-    __syncthreads();
-  }
-}
-
-// Exclusive scan over tiles of each digit's counts, offset by the number of
-// elements with a smaller digit.  Digits are spread over the blocks.
-__device__ void tile_scan(SortSmem& S, int64_t m, int pass, int64_t NT, const uint32_t* hist, uint32_t* tilecnt) {
-  const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
+// Exclusive block scan of one value per thread (LBLOCK == 256 threads).
+__device__ __forceinline__ uint32_t block_excl_scan(SortSmem& S, uint32_t v) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = blockIdx.x; d < 256; d += gridDim.x) {
-    if (threadIdx.x == 0) {
-      uint32_t base = 0;
-      for (int e = 0; e < d; ++e) base += hist[pass * 256 + e];
-      S.carry = base;
-    }
-    __syncthreads();
-    uint32_t* row = tilecnt + (int64_t)d * NT;
-    for (int64_t c0 = 0; c0 < nt; c0 += LBLOCK) {
-      const int64_t t = c0 + threadIdx.x;
-      const uint32_t v = t < nt ? row[t] : 0u;
-      uint32_t incl = v;
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t u = __shfl_up_sync(FULL, incl, off);
-        if (lane >= off) incl += u;
-      }
-      if (lane == 31) S.sw[warp] = incl;
-      __syncthreads();
-      uint32_t wpre = 0, tot = 0;
-      for (int w = 0; w < WARPS; ++w) {
-        const uint32_t x = S.sw[w];
-        if (w < warp) wpre += x;
-        tot += x;
-      }
-      const uint32_t carry = S.carry;
-      if (t < nt) row[t] = carry + wpre + incl - v;
-      __syncthreads();
-      if (threadIdx.x == 0) S.carry = carry + tot;
-      __syncthreads();
-    }
+  uint32_t incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t u = __shfl_up_sync(FULL, incl, off);
+    if (lane >= off) incl += u;
   }
+  if (lane == 31) S.wsum[warp] = incl;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int w = 0; w < warp; ++w) pre += S.wsum[w];
+  __syncthreads();
+  return pre + incl - v;
 }
 
-// Stable scatter of one pass.  Warp w owns elements [t*T + w*512, +512) of
-// tile t, read in rows of 32 (so order is (warp, row, lane) = index order).
-__device__ void tile_scatter(SortSmem& S, const unsigned long long* kin, const uint32_t* vin,
-                             unsigned long long* kout, uint32_t* vout, int64_t m, int pass, int64_t NT,
-                             const uint32_t* tilecnt) {
-  const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// One pass over m elements from (kin, vin) to (kout, vout).  Returns false
+// when a look-back wait gave up (nothing more is written).
+// pnext: the next pass that will run (-1: none), whose histogram is
+// counted on the way.
+__device__ __noinline__ bool sort_pass(SortSmem& S, const unsigned long long* kin, const uint32_t* vin,
+                                       unsigned long long* kout, uint32_t* vout, int64_t m, int pass, int pnext,
+                                       uint32_t* hist, uint32_t* tile_next, unsigned long long* status,
+                                       uint32_t* gstatus) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, d0 = threadIdx.x;
   const unsigned lt = (1u << lane) - 1u;
-  for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+  const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
+  S.hn[d0] = 0;
+  // elements with a smaller digit, over the whole set (thread d0 = digit d0)
+  {
+    const uint32_t c = hist[pass * 256 + d0];
+    S.excl[d0] = block_excl_scan(S, c);
+  }
+  bool ok = true;
+  for (;;) {
+    if (threadIdx.x == 0) S.tile = atomicAdd(tile_next + pass, 1u);
     for (int k = threadIdx.x; k < WARPS * 256; k += LBLOCK) (&S.wc[0][0])[k] = 0;
     __syncthreads();
+    const int64_t t = S.tile;
+    if (t >= nt) break;
+    // load the warp's slice in rows of 32 and rank each element among the
+    // earlier elements of its warp with the same digit
     const int64_t b = t * SORT_TILE + (int64_t)warp * PER_WARP;
     unsigned long long kk[ROWS];
     uint32_t vv[ROWS];
-    uint32_t dd[ROWS];
+    uint32_t rk2[ROWS / 2];  // ranks (< 4096), two per word
+    unsigned valid = 0;      // bit r: row r holds an element
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       const int64_t j = b + r * 32 + lane;
-      if (j < m) { kk[r] = kin[j]; vv[r] = vin[j]; dd[r] = digit(kk[r], pass); }
-      else { kk[r] = 0; vv[r] = 0; dd[r] = 256u; }
+      if (j < m) { kk[r] = kin[j]; vv[r] = vin[j]; valid |= 1u << r; }
+      else { kk[r] = 0; vv[r] = 0; }
     }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
-      const unsigned peers = __match_any_sync(FULL, dd[r]);
-      if (dd[r] < 256u && lane == __ffs(peers) - 1) S.wc[warp][dd[r]] += (uint32_t)__popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    {
-      const int d = threadIdx.x;
-      uint32_t run = tilecnt[(int64_t)d * NT + t];
+      const uint32_t d = ((valid >> r) & 1u) ? digit(kk[r], pass) : 256u;
+      // lanes with the same digit (9 bits: 256 marks a lane past the end)
+      unsigned peers = FULL;
 #pragma unroll
-      for (int w = 0; w < WARPS; ++w) { const uint32_t c = S.wc[w][d]; S.wc[w][d] = run; run += c; }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-      const unsigned peers = __match_any_sync(FULL, dd[r]);
-      if (dd[r] < 256u) {
-        const uint32_t pos = S.wc[warp][dd[r]] + (uint32_t)__popc(peers & lt);
-        kout[pos] = kk[r];
-        vout[pos] = vv[r];
+      for (int bt = 0; bt < 9; ++bt) {
+        const bool on = (d >> bt) & 1u;
+        const unsigned bal = __ballot_sync(FULL, on);
+        peers &= on ? bal : ~bal;
       }
+      const uint32_t c = d < 256u ? S.wc[warp][d] : 0u;
+      const uint32_t rank = c + (uint32_t)__popc(peers & lt);
+      if (r & 1) rk2[r >> 1] |= rank << 16; else rk2[r >> 1] = rank;
       __syncwarp();
-      if (dd[r] < 256u && lane == __ffs(peers) - 1) S.wc[warp][dd[r]] += (uint32_t)__popc(peers);
+      if (d < 256u && lane == __ffs(peers) - 1) S.wc[warp][d] = c + (uint32_t)__popc(peers);
       __syncwarp();
+    }
+    __syncthreads();
+    // thread d0: the tile's count of digit d0, the warps' offsets within it
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) { const uint32_t c = S.wc[w][d0]; S.wc[w][d0] = cnt; cnt += c; }
+    unsigned long long* my = status + (size_t)t * 256 + d0;
+    // publish the count at once, so later tiles need not wait for our look-back
+    atomicExch(my, t == 0 ? st_word(ST_PREFIX, pass, cnt) : st_word(ST_AGG, pass, cnt));
+    const uint32_t ls = block_excl_scan(S, cnt);
+    S.lstart[d0] = ls;
+    __syncthreads();
+    // reorder the tile by digit in shared memory (stable)
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      if ((valid >> r) & 1u) {
+        const uint32_t d = digit(kk[r], pass);
+        const uint32_t pos = S.lstart[d] + S.wc[warp][d] + ((rk2[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
+        S.keys[pos] = kk[r];
+        S.vals[pos] = vv[r];
+      }
+    }
+    // (the tile's data now lives in shared memory only: the look-back holds
+    // no element registers)
+    // look back over the earlier tiles' words for this digit
+    // (LOOK words at a time, loaded together: tile q, q - 1, ...; the walk
+    // consumes them in order and stops at the first prefix; a word not yet
+    // published is read again)
+    unsigned long long before = 0;
+    if (t > 0) {
+      int64_t q = t - 1;
+      const long long t0 = clock64();
+      bool done = false;
+      while (!done) {
+        unsigned long long w[LOOK];
+#pragma unroll
+        for (int k = 0; k < LOOK; ++k)
+          w[k] = q - k >= 0 ? *reinterpret_cast<volatile unsigned long long*>(status + (size_t)(q - k) * 256 + d0)
+                            : 0ull;
+        int used = 0;
+        bool stall = false;
+#pragma unroll
+        for (int k = 0; k < LOOK; ++k) {
+          if (done || stall) continue;
+          if ((int)((w[k] >> ST_TAG_SHIFT) & 15u) == pass + 1 && (w[k] & (3ull << 62))) {
+            before += w[k] & ST_COUNT;
+            ++used;
+            if (w[k] & ST_PREFIX) done = true;
+          } else {
+            stall = true;
+          }
+        }
+        q -= used;
+        if (!done && stall && clock64() - t0 > BAR_LIMIT_CYCLES) {
+          atomicOr(gstatus, HULL_DEVICE_TIMEOUT);
+          ok = false;
+          break;
+        }
+      }
+      if (ok) atomicExch(my, st_word(ST_PREFIX, pass, before + cnt));
+    }
+    S.delta[d0] = (long long)S.excl[d0] + (long long)before - (long long)ls;
+    const int okb = __syncthreads_and(ok ? 1 : 0);
+    if (!okb) return false;
+    // write it out in that order: each digit's run goes to consecutive addresses
+    const int tn = (int)min((int64_t)SORT_TILE, m - t * SORT_TILE);
+    for (int j = threadIdx.x; j < tn; j += LBLOCK) {
+      const unsigned long long k = S.keys[j];
+      const int64_t pos = (int64_t)j + S.delta[digit(k, pass)];
+      kout[pos] = k;
+      vout[pos] = S.vals[j];
+      if (pnext >= 0) atomicAdd(&S.hn[digit(k, pnext)], 1u);
     }
     __syncthreads();
   }
+  if (ok && pnext >= 0 && S.hn[d0]) atomicAdd(&hist[pnext * 256 + d0], S.hn[d0]);
+  return ok;
+}
+
+// The chains read their input CB elements at a time into a per-thread
+// staging area in shared memory: one memory round trip per CB elements, and
+// the pushes read shared memory only.
+__device__ __forceinline__ void stage_in(ChainSmem& S, const unsigned long long* K, const uint32_t* V, int64_t at,
+                                         int nb) {
+#pragma unroll
+  for (int i = 0; i < CB; ++i)
+    if (i < nb) {
+      S.keys[i * LBLOCK + threadIdx.x] = K[at + i];
+      S.vals[i * LBLOCK + threadIdx.x] = V[at + i];
+    }
 }
 
 // Level 0: virtual thread g chains sorted elements [g*C0, min((g+1)*C0, m));
 // the lower chain in place in (Ks, Vs), the upper chain into (Ku, Vu) at the
-// same offsets; counts to cnt_lo[g], cnt_up[g].
-__device__ void chain0(unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku, uint32_t* Vu, int64_t m,
-                       uint32_t* cnt_lo, uint32_t* cnt_up) {
+// same offsets; counts to cnt_lo[g], cnt_up[g].  Only the lowest point of an
+// x column can be a lower-chain vertex and only its highest an upper-chain
+// vertex (every other point of the column lies between them on a vertical
+// segment), so each column sends its first key (and copies of it) to the
+// lower chain and its last key (lowest index among copies) to the upper one.
+// The whole hull's lower chain must still end, and its upper chain start, at
+// the lexicographic maximum resp. minimum (the emission joins them there), so
+// every chunk also gives its last key to the lower chain and its first point
+// to the upper one.
+__device__ __noinline__ void chain0(ChainSmem& S, unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku,
+                                    uint32_t* Vu, int64_t m, uint32_t* cnt_lo, uint32_t* cnt_up) {
   const int64_t nch = (m + CHAIN_C0 - 1) / CHAIN_C0;
   for (int64_t g = (int64_t)blockIdx.x * LBLOCK + threadIdx.x; g < nch; g += (int64_t)gridDim.x * LBLOCK) {
     const int64_t start = g * CHAIN_C0;
     const int64_t end = min(start + (int64_t)CHAIN_C0, m);
     Stack<false> lo;
     Stack<true> up;
-    lo.init(Ks, Vs, start);
-    up.init(Ku, Vu, start);
-    for (int64_t j = start; j < end; ++j) {
-      const unsigned long long k = Ks[j];
-      const uint32_t v = Vs[j];
-      lo.push(k, v);
-      up.push(k, v);
+    lo.init(Ks, Vs, start, S, 0);
+    up.init(Ku, Vu, start, S, 1);
+    // the lower stack is written in place over consumed input; the staged
+    // batch is already in shared memory when its elements are pushed
+    int32_t px = 0;
+    unsigned long long first = 0, pk = 0;
+    uint32_t pv = 0;
+    bool any = false;
+    for (int64_t jb = start; jb < end; jb += CB) {
+      const int nb = (int)min((int64_t)CB, end - jb);
+      stage_in(S, Ks, Vs, jb, nb);
+      for (int i = 0; i < nb; ++i) {
+        const unsigned long long k = S.keys[i * LBLOCK + threadIdx.x];
+        const uint32_t v = S.vals[i * LBLOCK + threadIdx.x];
+        const int32_t x = key_x(k);
+        if (!any || x != px) {  // a new column: its lowest point, and the previous column's highest
+          if (any) up.push(pk, pv);
+          else up.push(k, v);  // the upper chain starts at the chunk's first point
+          lo.push(k, v);
+          first = k;
+          pk = k;
+          pv = v;
+          any = true;
+          px = x;
+        } else {
+          if (k == first) lo.push(k, v);  // a copy of the column's lowest point
+          if (k == pk) { if (v < pv) pv = v; } else { pk = k; pv = v; }
+        }
+      }
     }
+    if (any) {
+      up.push(pk, pv);
+      lo.push(pk, pv);  // the lower chain ends at the chunk's last point
+    }
+    lo.finish();
+    up.finish();
     cnt_lo[g] = (uint32_t)lo.n;
     cnt_up[g] = (uint32_t)up.n;
   }
 }
 
+// One group of a later level: the chains of chunks [c0, c1) of the previous
+// level (span `span` each, counts cin), concatenated in order (still sorted),
+// chained again in place from c0 * span.  Returns the new chain's length.
+template <bool UPPER>
+__device__ __forceinline__ uint32_t merge_group(ChainSmem& S, unsigned long long* K, uint32_t* V, const uint32_t* cin,
+                                                int64_t c0, int64_t c1, int64_t span) {
+  Stack<UPPER> st;
+  st.init(K, V, c0 * span, S, 0);
+  for (int64_t c = c0; c < c1; ++c) {
+    const int64_t b = c * span, cnt = cin[c];
+    for (int64_t jb = 0; jb < cnt; jb += CB) {
+      const int nb = (int)min((int64_t)CB, cnt - jb);
+      stage_in(S, K, V, b + jb, nb);
+      for (int i = 0; i < nb; ++i) st.push(S.keys[i * LBLOCK + threadIdx.x], S.vals[i * LBLOCK + threadIdx.x]);
+    }
+  }
+  st.finish();
+  return (uint32_t)st.n;
+}
+
 // Later level: group g merges the chains of chunks [g*FAN, (g+1)*FAN) of the
-// previous level (span `span` each); virtual thread 2g does the lower
-// chains, 2g+1 the upper ones.
-__device__ void chainN(unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku, uint32_t* Vu, int64_t m,
-                       const uint32_t* cin_lo, const uint32_t* cin_up, uint32_t* cout_lo, uint32_t* cout_up,
-                       int64_t nch_prev, int64_t span) {
+// previous level; virtual thread 2g does the lower chains, 2g+1 the upper
+// ones.
+__device__ __noinline__ void chainN(ChainSmem& S, unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku,
+                                    uint32_t* Vu, int64_t m, const uint32_t* cin_lo, const uint32_t* cin_up,
+                                    uint32_t* cout_lo, uint32_t* cout_up, int64_t nch_prev, int64_t span) {
   const int64_t ng = (nch_prev + CHAIN_FAN - 1) / CHAIN_FAN;
   for (int64_t t = (int64_t)blockIdx.x * LBLOCK + threadIdx.x; t < 2 * ng; t += (int64_t)gridDim.x * LBLOCK) {
     const int64_t g = t >> 1;
     const int64_t c0 = g * CHAIN_FAN;
     const int64_t c1 = min(c0 + (int64_t)CHAIN_FAN, nch_prev);
-    if (!(t & 1)) {
-      Stack<false> s;
-      s.init(Ks, Vs, c0 * span);
-      for (int64_t c = c0; c < c1; ++c) {
-        const int64_t b = c * span, cnt = cin_lo[c];
-        for (int64_t j = 0; j < cnt; ++j) s.push(Ks[b + j], Vs[b + j]);
-      }
-      cout_lo[g] = (uint32_t)s.n;
-    } else {
-      Stack<true> s;
-      s.init(Ku, Vu, c0 * span);
-      for (int64_t c = c0; c < c1; ++c) {
-        const int64_t b = c * span, cnt = cin_up[c];
-        for (int64_t j = 0; j < cnt; ++j) s.push(Ku[b + j], Vu[b + j]);
-      }
-      cout_up[g] = (uint32_t)s.n;
-    }
+    if (t & 1)
+      cout_up[g] = merge_group<true>(S, Ku, Vu, cin_up, c0, c1, span);
+    else
+      cout_lo[g] = merge_group<false>(S, Ks, Vs, cin_lo, c0, c1, span);
   }
 }
 
 // The hull counter-clockwise from the lexicographic minimum: the lower chain
 // left to right, then the upper chain right to left, without repeating the
 // two end points.
-__device__ void chain_emit(const uint32_t* Vs, const uint32_t* Vu, const uint32_t* cnt_lo, const uint32_t* cnt_up,
+__device__ __noinline__ void chain_emit(const uint32_t* Vs, const uint32_t* Vu, const uint32_t* cnt_lo, const uint32_t* cnt_up,
                            uint32_t* out_idx, int64_t* out_n) {
   const int64_t a = cnt_lo[0], b = cnt_up[0];
   const int64_t gt = (int64_t)blockIdx.x * LBLOCK + threadIdx.x, gs = (int64_t)gridDim.x * LBLOCK;
@@ -313,27 +527,35 @@ __device__ void chain_emit(const uint32_t* Vs, const uint32_t* Vu, const uint32_
   if (gt == 0) *out_n = (a - 1) + (b - 1);
 }
 
-__global__ void __launch_bounds__(LBLOCK) k_large(const LargeJob* __restrict__ table, const int* njobs_dev,
+__global__ void __launch_bounds__(LBLOCK, 2) k_large(const LargeJob* __restrict__ table, const int* njobs_dev,
                                                    LargeJob single, uint32_t* bar, uint32_t* bar_status) {
-  __shared__ SortSmem S;
+  extern __shared__ __align__(16) unsigned char lsm[];
+  SortSmem& S = *reinterpret_cast<SortSmem*>(lsm);
+  ChainSmem& C = *reinterpret_cast<ChainSmem*>(lsm);
   const int njobs = table ? *reinterpret_cast<const volatile int*>(njobs_dev) : 1;
   for (int jb = 0; jb < njobs; ++jb) {
     const LargeJob J = table ? table[jb] : single;
     if (*reinterpret_cast<const volatile uint32_t*>(&J.h->status)) continue;
     const int64_t m = (int64_t)*reinterpret_cast<const volatile unsigned long long*>(J.count);
     if (m <= SMALL_MAX) continue;
-    const int64_t NT = sort_tiles(J.cap);
-    hist_all(S, J.ka, m, &J.h->hist[0][0]);
+    const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
+    hist_read(S, J.ka, m, 0, J.h, true, J.tilecnt, nt * 256);
     if (!grid_sync(bar, bar_status)) return;
+    // the passes that move anything; the first one's histogram if not pass 0's
+    const unsigned live = live_passes(J.h);
+    if (live && !(live & 1u)) {
+      hist_read(S, J.ka, m, __ffs(live) - 1, J.h, false, nullptr, 0);
+      if (!grid_sync(bar, bar_status)) return;
+    }
     unsigned long long *kin = J.ka, *kout = J.kb;
     uint32_t *vin = J.va, *vout = J.vb;
     for (int p = 0; p < SORT_PASSES; ++p) {
-      tile_count(S, kin, m, p, NT, J.tilecnt);
-      if (!grid_sync(bar, bar_status)) return;
-      tile_scan(S, m, p, NT, &J.h->hist[0][0], J.tilecnt);
-      if (!grid_sync(bar, bar_status)) return;
-      tile_scatter(S, kin, vin, kout, vout, m, p, NT, J.tilecnt);
-      if (!grid_sync(bar, bar_status)) return;
+      if (!((live >> p) & 1u)) continue;
+      const unsigned later = live & ~((2u << p) - 1u);
+      const int pnext = later ? __ffs(later) - 1 : -1;
+      const bool ok = sort_pass(S, kin, vin, kout, vout, m, p, pnext, &J.h->hist[0][0], J.h->tile_next, J.tilecnt,
+                                bar_status);
+      if (!grid_sync(bar, bar_status) || !ok) return;
       unsigned long long* tk = kin; kin = kout; kout = tk;
       uint32_t* tv = vin; vin = vout; vout = tv;
     }
@@ -341,21 +563,20 @@ __global__ void __launch_bounds__(LBLOCK) k_large(const LargeJob* __restrict__ t
     const int64_t nch0 = (std::max<int64_t>(J.cap, 1) + CHAIN_C0 - 1) / CHAIN_C0;
     uint32_t* lo[2] = {J.cnt, J.cnt + 2 * nch0};
     uint32_t* up[2] = {J.cnt + nch0, J.cnt + 3 * nch0};
-    chain0(kin, vin, kout, vout, m, lo[0], up[0]);
+    chain0(C, kin, vin, kout, vout, m, lo[0], up[0]);
     if (!grid_sync(bar, bar_status)) return;
     int64_t nch = (m + CHAIN_C0 - 1) / CHAIN_C0, span = CHAIN_C0;
     int par = 0;
     while (nch > 1) {
-      chainN(kin, vin, kout, vout, m, lo[par], up[par], lo[par ^ 1], up[par ^ 1], nch, span);
+      chainN(C, kin, vin, kout, vout, m, lo[par], up[par], lo[par ^ 1], up[par ^ 1], nch, span);
       if (!grid_sync(bar, bar_status)) return;
       par ^= 1;
       nch = (nch + CHAIN_FAN - 1) / CHAIN_FAN;
       span *= CHAIN_FAN;
     }
     chain_emit(vin, vout, lo[par], up[par], J.out_idx, J.out_n);
-    // the next job reuses nothing of this one, but its histogram phase must
-    // not overtake this one's emission on shared barrier state: no barrier
-    // needed (the buffers differ and the barrier counter is balanced).
+    // the next job uses other buffers and its own counters; the barrier
+    // words are balanced, so it needs no barrier first
   }
 }
 
@@ -374,9 +595,12 @@ cudaError_t launch_large(const LargeJob* table, const int* njobs, const LargeJob
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
+  const size_t dsm = std::max(sizeof(SortSmem), sizeof(ChainSmem));
   if (occ_cache[dev] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    if (e != cudaSuccess) return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_large, LBLOCK, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_large, LBLOCK, dsm);
     if (e != cudaSuccess) return e;
     occ_cache[dev] = std::max(1, std::min(occ, 4));
   }
@@ -387,7 +611,7 @@ cudaError_t launch_large(const LargeJob* table, const int* njobs, const LargeJob
   uint32_t* b = bar;
   uint32_t* bs = bar_status;
   void* args[] = {(void*)&tab, (void*)&nj, (void*)&one, (void*)&b, (void*)&bs};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_large, dim3(G), dim3(LBLOCK), args, 0, st);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_large, dim3(G), dim3(LBLOCK), args, dsm, st);
   count_launches(1);
   return e;
 }

@@ -309,3 +309,40 @@ def test_refinement_on_uneven_shapes(gpu_lib, name):
         torch.cuda.synchronize()
         assert gpu_lib.device_status(ws) == (0, 0)
         assert gpu_lib.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist(), n
+
+
+def _columns(n, seed, w, h):
+    # n lattice points in w columns of height h: many points per column and
+    # many exact copies, so the large-set hull sees long x runs and ties
+    rng = np.random.default_rng(seed)
+    xy = np.stack([rng.integers(-w, w + 1, n), rng.integers(-h, h + 1, n)], 1).astype(np.float32)
+    return xy
+
+
+@pytest.mark.parametrize("name", ["columns", "one_column", "two_columns", "copies_late"])
+def test_large_path_columns_and_copies(gpu_lib, name):
+    # The large-set hull keeps only the lowest and highest point of each x
+    # column for its chains; columns, copies of the extreme points at high
+    # and low indices and single-column sets must still give the oracle's
+    # hull, through the case (1) path (every point) and through the
+    # survivors of Step 3 without refinement (compaction order).
+    import torch
+    cp = gpu_lib
+    if name == "columns":
+        xy = _columns(300_000, 71, 60, 3000)
+    elif name == "one_column":
+        xy = _columns(50_000, 72, 0, 1 << 20)
+    elif name == "two_columns":
+        xy = _columns(50_000, 73, 1, 1 << 20)
+        xy[:, 0] *= 5
+    else:
+        xy = _columns(120_000, 74, 300, 300)
+        # copies of the extremes of every column, late in the set
+        xy[-2000:] = xy[:2000][np.argsort(xy[:2000, 1])]
+    want = oracle.hull(xy)
+    d = torch.from_numpy(np.ascontiguousarray(xy)).cuda()
+    for opt in (cp.Options(no_prefilter=True), cp.Options(refine=False), cp.Options()):
+        out, cnt, ws = cp.compute(d, opt)
+        torch.cuda.synchronize()
+        assert cp.device_status(ws) == (0, 0)
+        assert cp.as_index(out, int(cnt.item())).tolist() == want.tolist(), opt
