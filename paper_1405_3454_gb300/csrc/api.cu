@@ -109,7 +109,8 @@ BatchLayout batch_layout(int64_t n_total, int32_t S) {
   put(L.tp, 8 * (s + 1));
   put(L.jobs, sizeof(LargeJob) * s);
   put(L.hcnt, 8 * s);
-  put(L.blockres, sizeof(BlockBest) * NSLOT * ((size_t)MAX_BLOCKS + s));
+  // partial results: per (block, set) of a static split, or per (unit, set)
+  put(L.blockres, sizeof(BlockBest) * NSLOT * ((size_t)MAX_BLOCKS + s + n / 2048 + 2));
   put(L.cells, CELL_BYTES * s);
   put(L.tri, sizeof(int4) * 2 * REFINE_BINS * s);
   put(L.small, sizeof(SmallWs) * s);
@@ -128,7 +129,8 @@ BatchLayout batch_layout(int64_t n_total, int32_t S) {
 struct BatchWords {
   uint32_t status;
   uint32_t bar_count, bar_gen;
-  int njobs;  // sets that take the large-set hull path
+  int njobs;             // sets that take the large-set hull path
+  uint32_t next_unit[2];  // units claimed by the streaming search and by the inside test
 };
 
 hull_status check_opts(const hull_options* o) {
@@ -383,15 +385,18 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
   auto* hstage = reinterpret_cast<uint32_t*>(ws + L.hstage);
   auto* hcnt = reinterpret_cast<int64_t*>(ws + L.hcnt);
   uint16_t* cells = reinterpret_cast<uint16_t*>(ws + L.cells);
+  // The streaming search keeps several waves of static shares (its per-set
+  // work is heavier than the inside test's); the inside test claims units.
+  const bool ext_units = false;
   mark(0, st);
   if (o.validate) HULL_TRY(launch_validate(d_xy, n_xy, bstatus, st));
   HULL_TRY(launch_batch_setup(SS, n_total, n_xy, bstatus, reinterpret_cast<int64_t*>(ws + L.pp), st));
   mark(1, st);
   const int64_t pairs_bound = n_total / 2;
   HULL_TRY(launch_extremes(SS, pairs_bound, o.angles, o.filter, bstatus, ws + L.blockres, cells, o.grid, nullptr, va,
-                           ka, st));  // marks boundary 2 between its two kernels
+                           ka, st, ext_units ? &bw->next_unit[0] : nullptr));  // marks boundary 2 between its two kernels
   mark(3, st);
-  HULL_TRY(launch_filter(SS, pairs_bound, o.filter, bstatus, cells, va, ka, o.grid, st));
+  HULL_TRY(launch_filter(SS, pairs_bound, o.filter, bstatus, cells, va, ka, o.grid, st, false, &bw->next_unit[1]));
   mark(4, st);
   const int64_t cap = std::max<int64_t>(n_total, 1);
   const bool refine = o.refine != 0;

@@ -207,9 +207,12 @@ cudaError_t launch_validate(const float* xy, int64_t n, uint32_t* status, cudaSt
 // the polygon, the cell grid, and the inside test of the points outside the
 // 16-byte pairs, whose survivors go to surv_idx / surv_key at the set's
 // offset).  `partials` holds (blocks + S) x 16 block results.
+// A batch passes `units` (a zeroed counter): its FP32 streaming search
+// claims units of the pair axis dynamically, and `partials` then needs
+// npairs / 1024 + 1 + S slots.
 cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int filter, uint32_t* gstatus,
                             void* partials, uint16_t* cells, int grid, uint32_t* ext_out, uint32_t* surv_idx,
-                            unsigned long long* surv_key, cudaStream_t st);
+                            unsigned long long* surv_key, cudaStream_t st, uint32_t* units = nullptr);
 // hull_compute on one set of at least RESERVE_MIN_POINTS points gives its
 // per-point buffers RESERVE_WARPS * RESERVE_FLUSH extra entries, so the
 // inside test may reserve survivor slots ahead (k_filter.cu): every warp
@@ -228,9 +231,11 @@ inline int64_t compute_capacity(int64_t n) {
 
 // Step 3 for every set: survivors (set-local indices, keys when surv_key is
 // not null) at the set's offset, counted in its header.
+// (a batch passes `units`, a zeroed counter: the FP32 pass then claims
+// units of the pair axis dynamically)
 cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32_t* gstatus, uint16_t* cells,
                           uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st,
-                          bool reserve = false);
+                          bool reserve = false, uint32_t* units = nullptr);
 // The large path (sort + chunked chain) of one point set; it runs only when
 // *count > SMALL_MAX and the set's status word is clear.
 struct LargeJob {

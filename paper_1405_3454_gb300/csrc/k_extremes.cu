@@ -543,9 +543,14 @@ __device__ __noinline__ void ext_block_result(const float* xy, const uint32_t* w
 constexpr int EXT_MIN_BLOCKS = 2;
 constexpr int EXT_STAGES = 6;
 
+// One set: partly dynamic shares (stream.cuh), one partial result per
+// block.  A batch with units != null: static shares, then units claimed from
+// *units (Split), one partial result per (share or unit, set).  Otherwise
+// static shares of sp.ppb pairs, one partial result per (block, set).
 template <int ANG>
-__global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(Sets S, int64_t ppb, uint32_t* gstatus,
-                                                                   BlockBest* bres) {
+__global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(Sets S, Split sp, uint32_t* gstatus,
+                                                                   BlockBest* bres, uint32_t* units) {
+  const int64_t ppb = sp.ppb;
   constexpr int NV = Dirs<ANG>::NV, ND = Dirs<ANG>::ND;
   extern __shared__ __align__(128) unsigned char dsm[];
   using SS = StreamSmemT<EXT_STAGES>;
@@ -567,6 +572,8 @@ __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(S
     if (dyn)
       stream_produce_dynamic(SM, reinterpret_cast<const float4*>(S.xy_of(0) + 2 * S.head_of(0)), S.npairs_of(0),
                              &S.h(0)->next_group[0], false, gstatus);
+    else if (units)
+      stream_produce_units(SM, S, sp, units, false, gstatus);
     else
       stream_produce_sets(SM, S, v0, v1, false, gstatus);
     return;
@@ -623,6 +630,27 @@ __global__ void __launch_bounds__(STREAM_THREADS, EXT_MIN_BLOCKS) k_extremes32(S
       chunk(c % SS::STAGES, f, (int)min((int64_t)CHUNK, np - f), c == 0, xy, head);
     }
     ext_block_result<ANG>(xy, &w_bidx[0][0], &w_s64[0][0], bres + (size_t)blockIdx.x * ND);
+    return;
+  }
+  if (units) {
+    // the running bests carry over while the block stays in one set: each
+    // segment's result (slot unit + set) is then the best over all of the
+    // set's points this block has seen, still a candidate of that set
+    int cur = -1;
+    for (int c = 0;; ++c) {
+      const ChunkMeta M = stream_next_meta(SM, c, gstatus);
+      if (M.flags & META_END) break;
+      const float* xy = S.xy_of(M.set);
+      const bool fresh = M.set != cur;
+      if (fresh) {
+        begin_set();
+        cur = M.set;
+      }
+      chunk(c % SS::STAGES, M.first, M.cnt, fresh && (M.flags & META_FIRST) != 0, xy, S.head_of(M.set));
+      if (M.flags & META_LAST) {
+        ext_block_result<ANG>(xy, &w_bidx[0][0], &w_s64[0][0], bres + ((size_t)M.unit + M.set) * ND);
+      }
+    }
     return;
   }
   int c = 0;
@@ -730,7 +758,7 @@ __global__ void __launch_bounds__(BLOCK) k_extremes64(Sets S, int64_t ppb, const
 // cell grid of the inside test.
 
 template <int ANG, int FIN_THREADS>
-__global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb, const uint32_t* gstatus,
+__global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, Split sp, const uint32_t* gstatus,
                                                                const BlockBest* bres, uint32_t* ext_out,
                                                                uint16_t* cells_base, uint32_t* surv_idx,
                                                                unsigned long long* surv_key) {
@@ -746,13 +774,21 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
   uint16_t* cells = cells_base + (size_t)set * (CELL_BYTES / 2);
   const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0 ||
                     *reinterpret_cast<volatile uint32_t*>(&h->status) != 0;
-  // this set's partial results: slot (block + set) of every block whose
-  // share of the pair axis meets the set
-  int64_t e0 = 0, e1 = 0;
+  // this set's partial results (Split): slots [e0, e1) of the static
+  // shares that meet the set, then [f0, f1) of the units that meet it
+  int64_t e0 = 0, e1 = 0, f0 = 0, f1 = 0;
   if (!dead && S.npairs_of(set) > 0) {
-    e0 = S.pp_at(set) / ppb + set;
-    e1 = (S.pp_at(set + 1) - 1) / ppb + set + 1;
+    const int64_t p0 = S.pp_at(set), p1 = S.pp_at(set + 1);
+    if (p0 < sp.A) {
+      e0 = p0 / sp.ppb + set;
+      e1 = (min(p1, sp.A) - 1) / sp.ppb + set + 1;
+    }
+    if (p1 > sp.A) {
+      f0 = sp.G + (max(p0, sp.A) - sp.A) / sp.U + set;
+      f1 = sp.G + (p1 - 1 - sp.A) / sp.U + set + 1;
+    }
   }
+  const int64_t n_e = e1 - e0, n_all = n_e + (f1 - f0);
   // points outside the 16-byte pairs: the head point and an odd last point
   const bool lead = !dead && head == 1;
   const bool trail = !dead && n > head && ((n - head) & 1);
@@ -764,7 +800,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_ext_finish(Sets S, int64_t ppb,
     auto take = [&](unsigned long long k, uint32_t i) {
       return i != NONE && (bi == NONE || k > ks || (k == ks && i < bi));
     };
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
+    for (int64_t q = lane; q < n_all; q += 32) {
+      const int64_t e = q < n_e ? e0 + q : f0 + (q - n_e);
       const BlockBest b = bres[e * ND + d];
       const unsigned long long k = dkey(b.s);
       if (take(k, b.idx)) { ks = k; bi = b.idx; }
@@ -955,7 +992,7 @@ cudaError_t launch_validate(const float* xy, int64_t n, uint32_t* status, cudaSt
 
 cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int filter, uint32_t* gstatus,
                             void* partials, uint16_t* cells, int grid, uint32_t* ext_out, uint32_t* surv_idx,
-                            unsigned long long* surv_key, cudaStream_t st) {
+                            unsigned long long* surv_key, cudaStream_t st, uint32_t* units) {
   const int64_t npairs = std::max<int64_t>(pairs_bound, 0);
   BlockBest* bres = static_cast<BlockBest*>(partials);
   const unsigned nsets = (unsigned)S.S;
@@ -977,11 +1014,9 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
 #define FIN(A)                                                                                           \
   do {                                                                                                   \
     if (S.S == 1)                                                                                        \
-      k_ext_finish<A, 1024><<<nsets, 1024, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx, \
-                                                    surv_key);                                           \
+      k_ext_finish<A, 1024><<<nsets, 1024, 0, st>>>(S, sp, gstatus, bres, ext_out, cells, surv_idx, surv_key); \
     else                                                                                                 \
-      k_ext_finish<A, 256><<<nsets, 256, 0, st>>>(S, gp.second, gstatus, bres, ext_out, cells, surv_idx,   \
-                                                  surv_key);                                             \
+      k_ext_finish<A, 256><<<nsets, 256, 0, st>>>(S, sp, gstatus, bres, ext_out, cells, surv_idx, surv_key);   \
   } while (0)
   if (filter == HULL_FILTER_FP32) {
     const size_t dsmem = sizeof(StreamSmemT<EXT_STAGES>);
@@ -1000,19 +1035,36 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_extremes32<0>, STREAM_THREADS, dsmem);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_extremes32<1>, STREAM_THREADS, dsmem);
-    const auto gp = shape(occ);
+    auto gp = shape(occ);
+    Split sp{gp.second, npairs, 1, gp.first};
+    uint32_t* un = nullptr;
+    if (S.S > 1 && units) {
+      // a batch: one wave of resident blocks, static shares of the first
+      // DYN_STATIC_PCT percent of the pair axis, then units claimed
+      // dynamically (partial slots: G + npairs / CHUNK + 1 + S at most)
+      const int64_t resident = (int64_t)device_sm_count() * std::max(occ, 1);
+      const int64_t G = grid > 0 ? std::min<int64_t>(grid, MAX_STREAM_BLOCKS) : resident;
+      sp.G = G;
+      sp.ppb = npairs * DYN_STATIC_PCT / 100 / G / CHUNK * CHUNK;
+      sp.A = sp.ppb * G;
+      if (sp.ppb == 0) { sp.ppb = CHUNK; sp.A = 0; }
+      sp.U = unit_pairs(npairs - sp.A, G, EXT_UNIT_CHUNKS);
+      gp.first = G;
+      un = units;
+    }
     if (angles == HULL_ANGLES_CUMULATIVE) {
-      k_extremes32<0><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
+      k_extremes32<0><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, sp, gstatus, bres, un);
       stage_mark(2, st);
       FIN(0);
     } else {
-      k_extremes32<1><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, gp.second, gstatus, bres);
+      k_extremes32<1><<<(unsigned)gp.first, STREAM_THREADS, dsmem, st>>>(S, sp, gstatus, bres, un);
       stage_mark(2, st);
       FIN(1);
     }
   } else {
     const int occ = angles == HULL_ANGLES_CUMULATIVE ? occupancy(k_extremes64<0>) : occupancy(k_extremes64<1>);
     const auto gp = shape(occ);
+    const Split sp{gp.second, npairs, 1, gp.first};
     if (angles == HULL_ANGLES_CUMULATIVE) {
       k_extremes64<0><<<(unsigned)gp.first, BLOCK, 0, st>>>(S, gp.second, gstatus, bres);
       stage_mark(2, st);

@@ -318,11 +318,13 @@ __device__ __forceinline__ unsigned full_test(const Edge* E, const Cells& C, flo
 }
 
 // RES: reserving mode (one set with keys, see WarpOut).
+// units != null: a batch streaming by units of ppb pairs (stream.cuh).
 template <bool KEYS, bool RES>
 __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Sets S, int64_t ppb, uint32_t* gstatus,
                                                                  const uint16_t* __restrict__ cells_base,
                                                                  uint32_t* __restrict__ surv_idx,
-                                                                 unsigned long long* __restrict__ surv_key) {
+                                                                 unsigned long long* __restrict__ surv_key,
+                                                                 uint32_t* units) {
   extern __shared__ __align__(128) unsigned char dsm[];
   FilterStream& SM = *reinterpret_cast<FilterStream*>(dsm);
   __shared__ __align__(16) Edge s_e[MAXV];
@@ -348,6 +350,8 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
     if (dyn)
       stream_produce_dynamic(SM, reinterpret_cast<const float4*>(S.xy_of(0) + 2 * S.head_of(0)), S.npairs_of(0),
                              &S.h(0)->next_group[1], true, gstatus);
+    else if (units)
+      stream_produce_units(SM, S, Split{CHUNK, 0, ppb, (int64_t)gridDim.x}, units, true, gstatus);
     else
       stream_produce_sets(SM, S, v0, v1, true, gstatus);
     return;
@@ -466,6 +470,16 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
     O.drain_copies();
     return;
   }
+  if (units) {
+    for (int c = 0;; ++c) {
+      const ChunkMeta M = stream_next_meta(SM, c, gstatus);
+      if (M.flags & META_END) break;
+      if (M.flags & META_FIRST) begin_set(M.set, 0);
+      chunk(c % FilterStream::STAGES, M.first, M.cnt);
+      if (M.flags & META_LAST) end_set();
+    }
+    return;
+  }
   int c = 0;
   bool stop = false;
   walk_segments(S, v0, v1, true, [&](int set, int64_t lo, int n) {
@@ -574,7 +588,7 @@ __global__ void k_copy_count(const WsHeader* h, int64_t* out) {
 
 template <class K>
 cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npairs, int grid, int sets, int64_t& G,
-                          int64_t& ppb) {
+                          int64_t& ppb, bool by_units = false) {
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
     if (e != cudaSuccess) return e;
@@ -584,6 +598,13 @@ cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npair
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, STREAM_THREADS, dsmem);
   occ = std::max(occ, 1);
   const int64_t resident = (int64_t)device_sm_count() * occ;
+  if (by_units) {
+    // one wave of resident blocks claiming units of ppb pairs
+    const int64_t G0 = grid > 0 ? std::min<int64_t>(grid, MAX_STREAM_BLOCKS) : resident;
+    ppb = unit_pairs(npairs, G0, FILTER_UNIT_CHUNKS);
+    G = std::max<int64_t>(1, std::min<int64_t>(G0, (npairs + ppb - 1) / ppb));
+    return cudaSuccess;
+  }
   G = grid > 0 ? grid : resident * stream_waves(sets, npairs, resident);
   G = std::min<int64_t>(G, MAX_STREAM_BLOCKS);
   G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
@@ -598,7 +619,7 @@ cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npair
 
 cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32_t* gstatus, uint16_t* cells,
                           uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st,
-                          bool reserve) {
+                          bool reserve, uint32_t* units) {
   const int64_t npairs = std::max<int64_t>(pairs_bound, 0);
   if (npairs == 0) return cudaSuccess;  // every point is a loose point (finishing kernel)
   const bool keys = surv_key != nullptr;
@@ -609,22 +630,29 @@ cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32
   int64_t G = 1, ppb = CHUNK;
   cudaError_t e;
   const size_t ds = sizeof(FilterStream);
+  const bool by_units = S.S > 1 && units != nullptr;
+  uint32_t* un = by_units ? units : nullptr;
   if (filter == HULL_FILTER_FP32) {
     if (keys) {
-      if ((e = stream_launch(k_filter32<true, false>, attr[dev][0], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess)
+      if ((e = stream_launch(k_filter32<true, false>, attr[dev][0], ds, npairs, grid, S.S, G, ppb, by_units)) !=
+          cudaSuccess)
         return e;
       // reserving mode only within the capacity the caller's layout added
       if (reserve && S.S == 1 && G * (CONSUMERS / 32) <= RESERVE_WARPS) {
         if ((e = stream_launch(k_filter32<true, true>, attr[dev][4], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess)
           return e;
-        k_filter32<true, true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key);
+        k_filter32<true, true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key,
+                                                                         nullptr);
       } else {
-        k_filter32<true, false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key);
+        k_filter32<true, false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key,
+                                                                          un);
       }
     } else {
-      if ((e = stream_launch(k_filter32<false, false>, attr[dev][1], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess)
+      if ((e = stream_launch(k_filter32<false, false>, attr[dev][1], ds, npairs, grid, S.S, G, ppb, by_units)) !=
+          cudaSuccess)
         return e;
-      k_filter32<false, false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key);
+      k_filter32<false, false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key,
+                                                                         un);
     }
   } else {
     if (keys) {

@@ -37,6 +37,11 @@ constexpr int64_t MAX_STREAM_BLOCKS = 4096;  // partial-result slots per call
 // shares ended up to 2x apart in time on a 2^28-point set).
 constexpr int DYN_GROUP = 4;
 constexpr int DYN_STATIC_PCT = 75;
+// Largest unit of a batch's dynamic streaming, in chunks: the inside test
+// keeps no state across units; the extreme search carries its running bests
+// across units of one set, but starts afresh (and re-seeds) on each new set.
+constexpr int64_t FILTER_UNIT_CHUNKS = 64;
+constexpr int64_t EXT_UNIT_CHUNKS = 64;
 
 inline int stream_waves(int sets, int64_t npairs, int64_t resident_blocks) {
   if (sets <= 1) return 1;
@@ -105,6 +110,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// What a stage holds when a batch streams by units (see
+// stream_produce_units): the chunk's set, its unit, its first pair within
+// the set and its pairs, and whether it opens / closes its segment (the
+// part of one set inside one unit) or ends the stream.
+constexpr int META_FIRST = 1, META_LAST = 2, META_END = 4;
+struct ChunkMeta {
+  int set;
+  int unit;
+  int first;
+  int cnt;
+  int flags;
+};
+
 // Shared state of one block's stream with NS stages.
 template <int NS>
 struct StreamSmemT {
@@ -113,7 +131,34 @@ struct StreamSmemT {
   unsigned long long full[NS];
   unsigned long long empty[NS];
   int id[NS];  // dynamic shares: the chunk in the stage, -1 = end of the stream
+  ChunkMeta meta[NS];
 };
+
+// How a streaming pass splits the virtual pair axis [0, P) over its G
+// blocks: block b first takes the static share [b ppb, min((b + 1) ppb, A)),
+// then the blocks claim units of U pairs of [A, P) from a counter.  Results
+// of (block b, set s) of the static part go to slot b + s, those of (unit u,
+// set s) to slot G + u + s: every slot is one (share or unit, set) pair,
+// because shares and units are contiguous, in axis order, and the static
+// part comes first.
+struct Split {
+  int64_t ppb;  // pairs of a static share
+  int64_t A;    // end of the static part (a multiple of ppb, or P)
+  int64_t U;    // pairs of a unit of the dynamic part
+  int64_t G;    // blocks
+};
+
+// A batch's streaming passes split the virtual pair axis into units of
+// `upairs` pairs (a whole number of chunks) that blocks claim one at a time
+// from a counter, so blocks whose sets cost more per point simply claim
+// fewer units.  Unit u's results for set s go to slot u + s: units are
+// contiguous and claimed in axis order, so the pair (u, s) -> u + s is one
+// to one (a later unit never meets an earlier set).
+inline int64_t unit_pairs(int64_t npairs, int64_t blocks, int64_t max_chunks) {
+  const int64_t nck = (npairs + CHUNK - 1) / CHUNK;
+  const int64_t per = nck / (8 * std::max<int64_t>(blocks, 1));  // about 8 units per block at least
+  return std::max<int64_t>(1, std::min<int64_t>(max_chunks, per)) * CHUNK;
+}
 
 // The segments of a block's share [v0, v1) of the virtual pair axis, one
 // per set it meets, in order (or in reverse): f(s, first local pair, pairs).
@@ -235,6 +280,83 @@ __device__ __forceinline__ void stream_produce_dynamic(SS& SM, const float4* P, 
   // c stages were armed (the end marker included): the last ones must land
   for (int d = c > STAGES ? c - STAGES : 0; d < c; ++d)
     mbar_wait_status(&SM.full[d % STAGES], (unsigned)((d / STAGES) & 1), status);
+}
+
+// Producer (lane 0 of the producer warp) of a batch streaming by units:
+// this block's static share of [0, sp.A) first (unit number blockIdx.x),
+// then units of [sp.A, P) claimed from *next (unit number G + u; last unit
+// first when `reverse`) until none is left.  Each chunk of each segment (the
+// part of one set inside a share or unit) is described in its stage's meta;
+// a stage flagged META_END (a plain arrival) ends the stream.
+template <class SS>
+__device__ __forceinline__ void stream_produce_units(SS& SM, const Sets& S, const Split& sp, uint32_t* next,
+                                                     bool reverse, uint32_t* status) {
+  constexpr int STAGES = SS::STAGES;
+  if ((threadIdx.x & 31) != 0) return;
+  const int64_t P = S.pp_at(S.S);
+  const int64_t nunits = P > sp.A ? (P - sp.A + sp.U - 1) / sp.U : 0;
+  int c = 0;
+  bool stop = *reinterpret_cast<volatile uint32_t*>(status) != 0;
+  auto stream_range = [&](int64_t v0, int64_t v1, int64_t unit) {
+    walk_segments(S, v0, v1, reverse, [&](int s, int64_t lo, int n) {
+      const float4* Pp = reinterpret_cast<const float4*>(S.xy_of(s) + 2 * S.head_of(s)) + lo;
+      const int nck = nchunks(n);
+      for (int q = 0; q < nck && !stop; ++q, ++c) {
+        const int st = c % STAGES;
+        const int ph = c / STAGES;
+        if (ph > 0 && !mbar_wait_status(&SM.empty[st], (unsigned)((ph - 1) & 1), status)) { stop = true; break; }
+        if (*reinterpret_cast<volatile uint32_t*>(status) & HULL_DEVICE_TIMEOUT) { stop = true; break; }
+        const int f = chunk_first(q, nck, reverse);
+        const int cnt = min(CHUNK, n - f);
+        ChunkMeta& M = SM.meta[st];
+        M.set = s;
+        M.unit = (int)unit;
+        M.first = (int)(lo + f);
+        M.cnt = cnt;
+        M.flags = (q == 0 ? META_FIRST : 0) | (q == nck - 1 ? META_LAST : 0);
+        mbar_arrive_tx(&SM.full[st], (unsigned)cnt * 16u);
+        bulk_g2s(&SM.stage[st][0], Pp + f, (unsigned)cnt * 16u, &SM.full[st]);
+      }
+    });
+  };
+  if (!stop && sp.A > 0) {
+    const int64_t v0 = (int64_t)blockIdx.x * sp.ppb;
+    stream_range(v0, min(v0 + sp.ppb, sp.A), blockIdx.x);
+  }
+  while (!stop) {
+    const int64_t k = (int64_t)atomicAdd(next, 1u);
+    if (k >= nunits) break;
+    const int64_t u = reverse ? nunits - 1 - k : k;
+    const int64_t v0 = sp.A + u * sp.U;
+    stream_range(v0, min(v0 + sp.U, P), sp.G + u);
+  }
+  // the end marker (after a timeout the consumers stop by themselves)
+  {
+    const int st = c % STAGES;
+    const int ph = c / STAGES;
+    if (ph == 0 || mbar_wait_status(&SM.empty[st], (unsigned)((ph - 1) & 1), status)) {
+      SM.meta[st].flags = META_END;
+      mbar_arrive(&SM.full[st]);
+      ++c;
+    }
+  }
+  for (int d = c > STAGES ? c - STAGES : 0; d < c; ++d)
+    mbar_wait_status(&SM.full[d % STAGES], (unsigned)((d / STAGES) & 1), status);
+}
+
+// Consumers' side of streaming by units: wait for stage c and read its
+// meta; a copy with META_END when the stream ends or the wait gave up.
+template <class SS>
+__device__ __forceinline__ ChunkMeta stream_next_meta(SS& SM, int c, uint32_t* status) {
+  const int st = c % SS::STAGES;
+  ChunkMeta M;
+  if (!mbar_wait_status(&SM.full[st], (unsigned)((c / SS::STAGES) & 1), status)) {
+    M.set = 0; M.unit = 0; M.first = 0; M.cnt = 0; M.flags = META_END;
+    return M;
+  }
+  const volatile ChunkMeta& V = SM.meta[st];
+  M.set = V.set; M.unit = V.unit; M.first = V.first; M.cnt = V.cnt; M.flags = V.flags;
+  return M;
 }
 
 // Consumers' side of dynamic shares: wait for stage c and read its chunk
