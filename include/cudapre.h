@@ -92,7 +92,12 @@ typedef struct hull_options {
                             all points without Steps 1-3 (the paper's case (1),
                             for comparison; same result).  Not for hull_prefilter
                             or a batch (HULL_ERR_UNSUPPORTED). */
-  int32_t reserved[9];   /* must be zero */
+  int32_t waves;         /* a batch's streaming extreme search: waves of resident
+                            blocks its static shares make (1 .. 16); 0 = tuned */
+  int32_t unit_chunks;   /* a batch's inside test: pairs claimed at a time, in
+                            chunks of 1024 pairs (1 .. 1024); 0 = tuned.  No
+                            launch-shape option changes any result. */
+  int32_t reserved[7];   /* must be zero */
 } hull_options;
 
 /* Device-side condition bits (hull_get_device_status). */
@@ -183,6 +188,33 @@ hull_status hull_batch(const float* d_xy, const int64_t* d_offsets, int32_t S, i
 hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_starts, const int64_t* d_offsets,
                               int32_t S, int64_t n_total, void* d_ws, size_t ws_bytes, int64_t* d_hull_idx,
                               int64_t* d_hull_offsets, const hull_options* opt, void* stream);
+
+/* ---- Batches as CUDA graphs (the paper has no counterpart) ------------ */
+
+/* A host object that runs hull_batch_ranges calls as CUDA graphs, so that a
+ * repeated batch launches all of its kernels with one graph launch.  The
+ * first call captures the call's work on `stream` into a graph and
+ * instantiates it.  A call whose arguments and options all equal the
+ * previous call's replays that graph (the kernels read every size, offset
+ * and start from device memory, so new contents of the same buffers are
+ * fine).  Any other call captures anew and updates the instantiated graph in
+ * place, or instantiates a new one when CUDA refuses the update (another
+ * sequence of kernels, e.g. other options).  Results, workspace sizes and
+ * device-side status are those of hull_batch_ranges.
+ *   stream   must not be the legacy default stream (NULL): it cannot be
+ *            captured (HULL_ERR_INVALID_ARG); nor may it be capturing already.
+ * Not thread-safe: one host thread per object; no stage timer may be
+ * attached on that thread during a capture. */
+typedef struct hull_graph hull_graph;
+hull_graph* hull_graph_create(void);
+void hull_graph_destroy(hull_graph* g);
+hull_status hull_graph_batch_ranges(hull_graph* g, const float* d_xy, int64_t n_xy, const int64_t* d_starts,
+                                    const int64_t* d_offsets, int32_t S, int64_t n_total, void* d_ws,
+                                    size_t ws_bytes, int64_t* d_hull_idx, int64_t* d_hull_offsets,
+                                    const hull_options* opt, void* stream);
+/* h_out[6] (host): calls, captures, in-place updates, instantiations,
+ * replays, and the kernels of the current graph. */
+void hull_graph_counts(const hull_graph* g, int64_t* h_out);
 
 /* hull_compute without a caller workspace; the paper has no counterpart (it
  * is a library convenience, not a step of the method).  The workspace is a

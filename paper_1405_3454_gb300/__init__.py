@@ -38,7 +38,8 @@ ABI_SYMBOLS = (
     "hull_get_device_status", "hull_strerror", "hull_constants", "hull_abi_version", "hull_read_stats",
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
     "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes", "hull_batch_ranges",
-    "hull_selftest_wait", "hull_batch_read_set",
+    "hull_selftest_wait", "hull_batch_read_set", "hull_graph_create", "hull_graph_destroy",
+    "hull_graph_batch_ranges", "hull_graph_counts",
 )
 HULL_STAGES = 6
 STAGE_NAMES = ("validate", "extremes", "polygon", "filter", "hull", "final")
@@ -47,7 +48,8 @@ STAGE_NAMES = ("validate", "extremes", "polygon", "filter", "hull", "final")
 class HullOptions(ctypes.Structure):
     _fields_ = [("angles", ctypes.c_int32), ("filter", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("refine", ctypes.c_int32),
-                ("no_prefilter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("no_prefilter", ctypes.c_int32), ("waves", ctypes.c_int32), ("unit_chunks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class HullStats(ctypes.Structure):
@@ -130,6 +132,14 @@ def load(path: str | None = None):
     lib.hull_selftest_wait.restype = st
     lib.hull_batch_read_set.argtypes = [P, i64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(HullSetInfo), P]
     lib.hull_batch_read_set.restype = st
+    lib.hull_graph_create.argtypes = []
+    lib.hull_graph_create.restype = P
+    lib.hull_graph_destroy.argtypes = [P]
+    lib.hull_graph_destroy.restype = None
+    lib.hull_graph_batch_ranges.argtypes = [P, P, i64, P, P, ctypes.c_int32, i64, P, sz, P, P, OP, P]
+    lib.hull_graph_batch_ranges.restype = st
+    lib.hull_graph_counts.argtypes = [P, P]
+    lib.hull_graph_counts.restype = None
     _lib = lib
     return lib
 
@@ -155,6 +165,8 @@ class Options:
     grid: int = 0
     refine: bool = True
     no_prefilter: bool = False
+    waves: int = 0
+    unit_chunks: int = 0
 
     def c(self) -> HullOptions:
         o = HullOptions()
@@ -162,6 +174,7 @@ class Options:
         o.angles, o.filter, o.validate = int(self.angles), int(self.filter), int(bool(self.validate))
         o.block, o.grid, o.refine = int(self.block), int(self.grid), int(bool(self.refine))
         o.no_prefilter = int(bool(self.no_prefilter))
+        o.waves, o.unit_chunks = int(self.waves), int(self.unit_chunks)
         return o
 
 
@@ -326,6 +339,53 @@ def batch_ranges(pool, starts, sizes, opt: Options | None = None, ws=None, strea
     _check(hull_batch_ranges(_ptr(pool), n_xy, _ptr(starts), _ptr(offsets), S, n_total, _ptr(ws), ws.numel(),
                              _ptr(out), _ptr(hoff), opt, _stream_handle(stream)), "hull_batch_ranges")
     return out, hoff, ws
+
+
+def hull_graph_batch_ranges(g: int, d_xy: int, n_xy: int, d_starts: int, d_offsets: int, S: int, n_total: int,
+                            d_ws: int, ws_bytes: int, d_hull_idx: int, d_hull_offsets: int, opt: Options | None,
+                            stream: int) -> int:
+    o = (opt or Options()).c()
+    return load().hull_graph_batch_ranges(g, d_xy or None, n_xy, d_starts or None, d_offsets, S, n_total, d_ws,
+                                          ws_bytes, d_hull_idx or None, d_hull_offsets, ctypes.byref(o),
+                                          stream or None)
+
+
+class Graph:
+    """Batches run as CUDA graphs (hull_graph_*): a call repeating the
+    previous call's arguments replays its graph with one launch."""
+
+    def __init__(self):
+        self._g = load().hull_graph_create()
+        if not self._g:
+            raise RuntimeError("hull_graph_create failed")
+
+    def batch_ranges(self, pool, starts, offsets, n_total: int, ws, out, hoff, opt: Options | None = None,
+                     stream=None):
+        """hull_batch_ranges through the graph; starts (or None for
+        contiguous sets) and offsets are int64 device tensors, the outputs and
+        workspace preallocated (sizes as for hull_batch_ranges)."""
+        S = offsets.numel() - 1
+        n_xy = _check_points(pool)
+        code = hull_graph_batch_ranges(self._g, _ptr(pool), n_xy if starts is not None else n_total, _ptr(starts),
+                                       _ptr(offsets), S, n_total, _ptr(ws), ws.numel(), _ptr(out), _ptr(hoff), opt,
+                                       _stream_handle(stream))
+        _check(code, "hull_graph_batch_ranges")
+
+    def counts(self) -> dict:
+        a = (ctypes.c_int64 * 6)()
+        load().hull_graph_counts(self._g, a)
+        return dict(zip(("calls", "captures", "updates", "instantiations", "replays", "kernels"), [int(v) for v in a]))
+
+    def close(self):
+        if self._g:
+            load().hull_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def read_counters(ws, stream=None):

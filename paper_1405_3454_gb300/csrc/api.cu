@@ -140,7 +140,8 @@ hull_status check_opts(const hull_options* o) {
   if (o->block < 0 || o->grid < 0 || o->grid > MAX_BLOCKS) return HULL_ERR_INVALID_ARG;
   if (o->refine != 0 && o->refine != 1) return HULL_ERR_UNSUPPORTED;
   if (o->no_prefilter != 0 && o->no_prefilter != 1) return HULL_ERR_UNSUPPORTED;
-  for (int k = 0; k < 9; ++k) if (o->reserved[k] != 0) return HULL_ERR_UNSUPPORTED;
+  if (o->waves < 0 || o->waves > 16 || o->unit_chunks < 0 || o->unit_chunks > 1024) return HULL_ERR_INVALID_ARG;
+  for (int k = 0; k < 7; ++k) if (o->reserved[k] != 0) return HULL_ERR_UNSUPPORTED;
   return HULL_OK;
 }
 
@@ -151,6 +152,8 @@ hull_options opts_or_default(const hull_options* o) {
 }
 
 hull_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HULL_OK : HULL_ERR_CUDA; }
+
+LaunchShape shape_of(const hull_options& o) { return LaunchShape{o.grid, o.waves, o.unit_chunks}; }
 
 #define HULL_TRY(expr)                               \
   do {                                               \
@@ -182,10 +185,10 @@ hull_status run_prefilter(const float* d_xy, int64_t n, char* ws, const Layout& 
   mark(1, st);
   const int64_t npairs = S.npairs_of(0);
   uint16_t* cells = reinterpret_cast<uint16_t*>(ws + L.cells);
-  HULL_TRY(launch_extremes(S, npairs, o.angles, o.filter, &h->status, ws + L.blockres, cells, o.grid, ext_out,
+  HULL_TRY(launch_extremes(S, npairs, o.angles, o.filter, &h->status, ws + L.blockres, cells, shape_of(o), ext_out,
                            surv_idx, surv_key, st));  // marks boundary 2 between its two kernels
   mark(3, st);
-  HULL_TRY(launch_filter(S, npairs, o.filter, &h->status, cells, surv_idx, surv_key, o.grid, st, reserve));
+  HULL_TRY(launch_filter(S, npairs, o.filter, &h->status, cells, surv_idx, surv_key, shape_of(o), st, reserve));
   mark(4, st);
   return HULL_OK;
 }
@@ -393,10 +396,10 @@ hull_status hull_batch_ranges(const float* d_xy, int64_t n_xy, const int64_t* d_
   HULL_TRY(launch_batch_setup(SS, n_total, n_xy, bstatus, reinterpret_cast<int64_t*>(ws + L.pp), st));
   mark(1, st);
   const int64_t pairs_bound = n_total / 2;
-  HULL_TRY(launch_extremes(SS, pairs_bound, o.angles, o.filter, bstatus, ws + L.blockres, cells, o.grid, nullptr, va,
+  HULL_TRY(launch_extremes(SS, pairs_bound, o.angles, o.filter, bstatus, ws + L.blockres, cells, shape_of(o), nullptr, va,
                            ka, st, ext_units ? &bw->next_unit[0] : nullptr));  // marks boundary 2 between its two kernels
   mark(3, st);
-  HULL_TRY(launch_filter(SS, pairs_bound, o.filter, bstatus, cells, va, ka, o.grid, st, false, &bw->next_unit[1]));
+  HULL_TRY(launch_filter(SS, pairs_bound, o.filter, bstatus, cells, va, ka, shape_of(o), st, false, &bw->next_unit[1]));
   mark(4, st);
   const int64_t cap = std::max<int64_t>(n_total, 1);
   const bool refine = o.refine != 0;

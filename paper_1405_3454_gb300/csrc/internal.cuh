@@ -192,6 +192,14 @@ struct Sets {
 // Launch shapes and per-device facts.
 int device_sm_count();
 
+// Launch shape of the streaming passes (hull_options; 0 = built-in choice):
+// blocks, waves of a batch's static shares, chunks of a batch's units.
+struct LaunchShape {
+  int grid;
+  int waves;
+  int unit_chunks;
+};
+
 // Process-wide count of kernels enqueued by this library (instrumentation).
 void count_launches(int k);
 // Stage boundary b of the current call for an attached stage timer
@@ -211,7 +219,7 @@ cudaError_t launch_validate(const float* xy, int64_t n, uint32_t* status, cudaSt
 // claims units of the pair axis dynamically, and `partials` then needs
 // npairs / 1024 + 1 + S slots.
 cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int filter, uint32_t* gstatus,
-                            void* partials, uint16_t* cells, int grid, uint32_t* ext_out, uint32_t* surv_idx,
+                            void* partials, uint16_t* cells, LaunchShape ls, uint32_t* ext_out, uint32_t* surv_idx,
                             unsigned long long* surv_key, cudaStream_t st, uint32_t* units = nullptr);
 // hull_compute on one set of at least RESERVE_MIN_POINTS points gives its
 // per-point buffers RESERVE_WARPS * RESERVE_FLUSH extra entries, so the
@@ -234,7 +242,7 @@ inline int64_t compute_capacity(int64_t n) {
 // (a batch passes `units`, a zeroed counter: the FP32 pass then claims
 // units of the pair axis dynamically)
 cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32_t* gstatus, uint16_t* cells,
-                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st,
+                          uint32_t* surv_idx, unsigned long long* surv_key, LaunchShape ls, cudaStream_t st,
                           bool reserve = false, uint32_t* units = nullptr);
 // The large path (sort + chunked chain) of one point set; it runs only when
 // *count > SMALL_MAX and the set's status word is clear.

@@ -991,7 +991,7 @@ cudaError_t launch_validate(const float* xy, int64_t n, uint32_t* status, cudaSt
 }
 
 cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int filter, uint32_t* gstatus,
-                            void* partials, uint16_t* cells, int grid, uint32_t* ext_out, uint32_t* surv_idx,
+                            void* partials, uint16_t* cells, LaunchShape ls, uint32_t* ext_out, uint32_t* surv_idx,
                             unsigned long long* surv_key, cudaStream_t st, uint32_t* units) {
   const int64_t npairs = std::max<int64_t>(pairs_bound, 0);
   BlockBest* bres = static_cast<BlockBest*>(partials);
@@ -1000,7 +1000,7 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
   // share a whole number of chunks
   auto shape = [&](int occ) {
     const int64_t resident = (int64_t)device_sm_count() * std::max(occ, 1);
-    int64_t G = grid > 0 ? grid : resident * stream_waves(S.S, npairs, resident);
+    int64_t G = ls.grid > 0 ? ls.grid : resident * stream_waves(S.S, npairs, resident, ls.waves);
     G = std::min<int64_t>(G, MAX_STREAM_BLOCKS);
     G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
     int64_t ppb = (npairs + G - 1) / G;
@@ -1043,7 +1043,7 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
       // DYN_STATIC_PCT percent of the pair axis, then units claimed
       // dynamically (partial slots: G + npairs / CHUNK + 1 + S at most)
       const int64_t resident = (int64_t)device_sm_count() * std::max(occ, 1);
-      const int64_t G = grid > 0 ? std::min<int64_t>(grid, MAX_STREAM_BLOCKS) : resident;
+      const int64_t G = ls.grid > 0 ? std::min<int64_t>(ls.grid, MAX_STREAM_BLOCKS) : resident;
       sp.G = G;
       sp.ppb = npairs * DYN_STATIC_PCT / 100 / G / CHUNK * CHUNK;
       sp.A = sp.ppb * G;

@@ -587,8 +587,9 @@ __global__ void k_copy_count(const WsHeader* h, int64_t* out) {
 }
 
 template <class K>
-cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npairs, int grid, int sets, int64_t& G,
-                          int64_t& ppb, bool by_units = false) {
+cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npairs, const LaunchShape& ls, int sets,
+                          int64_t& G, int64_t& ppb, bool by_units = false) {
+  const int grid = ls.grid;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
     if (e != cudaSuccess) return e;
@@ -601,11 +602,11 @@ cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npair
   if (by_units) {
     // one wave of resident blocks claiming units of ppb pairs
     const int64_t G0 = grid > 0 ? std::min<int64_t>(grid, MAX_STREAM_BLOCKS) : resident;
-    ppb = unit_pairs(npairs, G0, FILTER_UNIT_CHUNKS);
+    ppb = unit_pairs(npairs, G0, ls.unit_chunks > 0 ? ls.unit_chunks : FILTER_UNIT_CHUNKS);
     G = std::max<int64_t>(1, std::min<int64_t>(G0, (npairs + ppb - 1) / ppb));
     return cudaSuccess;
   }
-  G = grid > 0 ? grid : resident * stream_waves(sets, npairs, resident);
+  G = grid > 0 ? grid : resident * stream_waves(sets, npairs, resident, ls.waves);
   G = std::min<int64_t>(G, MAX_STREAM_BLOCKS);
   G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
   ppb = (npairs + G - 1) / G;
@@ -618,7 +619,7 @@ cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npair
 }  // namespace
 
 cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32_t* gstatus, uint16_t* cells,
-                          uint32_t* surv_idx, unsigned long long* surv_key, int grid, cudaStream_t st,
+                          uint32_t* surv_idx, unsigned long long* surv_key, LaunchShape ls, cudaStream_t st,
                           bool reserve, uint32_t* units) {
   const int64_t npairs = std::max<int64_t>(pairs_bound, 0);
   if (npairs == 0) return cudaSuccess;  // every point is a loose point (finishing kernel)
@@ -634,12 +635,12 @@ cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32
   uint32_t* un = by_units ? units : nullptr;
   if (filter == HULL_FILTER_FP32) {
     if (keys) {
-      if ((e = stream_launch(k_filter32<true, false>, attr[dev][0], ds, npairs, grid, S.S, G, ppb, by_units)) !=
+      if ((e = stream_launch(k_filter32<true, false>, attr[dev][0], ds, npairs, ls, S.S, G, ppb, by_units)) !=
           cudaSuccess)
         return e;
       // reserving mode only within the capacity the caller's layout added
       if (reserve && S.S == 1 && G * (CONSUMERS / 32) <= RESERVE_WARPS) {
-        if ((e = stream_launch(k_filter32<true, true>, attr[dev][4], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess)
+        if ((e = stream_launch(k_filter32<true, true>, attr[dev][4], ds, npairs, ls, S.S, G, ppb)) != cudaSuccess)
           return e;
         k_filter32<true, true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key,
                                                                          nullptr);
@@ -648,7 +649,7 @@ cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32
                                                                           un);
       }
     } else {
-      if ((e = stream_launch(k_filter32<false, false>, attr[dev][1], ds, npairs, grid, S.S, G, ppb, by_units)) !=
+      if ((e = stream_launch(k_filter32<false, false>, attr[dev][1], ds, npairs, ls, S.S, G, ppb, by_units)) !=
           cudaSuccess)
         return e;
       k_filter32<false, false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, cells, surv_idx, surv_key,
@@ -656,10 +657,10 @@ cudaError_t launch_filter(const Sets& S, int64_t pairs_bound, int filter, uint32
     }
   } else {
     if (keys) {
-      if ((e = stream_launch(k_filter_exact<true>, attr[dev][2], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess) return e;
+      if ((e = stream_launch(k_filter_exact<true>, attr[dev][2], ds, npairs, ls, S.S, G, ppb)) != cudaSuccess) return e;
       k_filter_exact<true><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, surv_idx, surv_key);
     } else {
-      if ((e = stream_launch(k_filter_exact<false>, attr[dev][3], ds, npairs, grid, S.S, G, ppb)) != cudaSuccess) return e;
+      if ((e = stream_launch(k_filter_exact<false>, attr[dev][3], ds, npairs, ls, S.S, G, ppb)) != cudaSuccess) return e;
       k_filter_exact<false><<<(unsigned)G, STREAM_THREADS, ds, st>>>(S, ppb, gstatus, surv_idx, surv_key);
     }
   }

@@ -43,10 +43,10 @@ constexpr int DYN_STATIC_PCT = 75;
 constexpr int64_t FILTER_UNIT_CHUNKS = 64;
 constexpr int64_t EXT_UNIT_CHUNKS = 64;
 
-inline int stream_waves(int sets, int64_t npairs, int64_t resident_blocks) {
+inline int stream_waves(int sets, int64_t npairs, int64_t resident_blocks, int max_waves = 0) {
   if (sets <= 1) return 1;
   const int64_t w = npairs / (resident_blocks * WAVE_MIN_CHUNKS * CHUNK);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(BATCH_WAVES, w));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(max_waves > 0 ? max_waves : BATCH_WAVES, w));
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {

@@ -104,3 +104,16 @@ def test_compute_workspace_has_room_for_reserved_slots(lib):
     # the largest sets do without (survivor positions stay below 2^32)
     top = (1 << 32) - 1
     assert cp.hull_workspace_bytes(top) - cp.hull_workspace_bytes(top - 1) < 64
+
+
+def test_graph_rejects_the_default_stream_before_any_cuda_call(lib):
+    # the legacy default stream cannot be captured: refused up front
+    g = lib.hull_graph_create()
+    assert g
+    P = 256 * 1024
+    code = cp.hull_graph_batch_ranges(g, P, 10, 0, P, 1, 10, P, 1 << 20, P, P, None, 0)
+    assert code == 1
+    counts = (ctypes.c_int64 * 6)()
+    lib.hull_graph_counts(g, counts)
+    assert list(counts) == [0, 0, 0, 0, 0, 0]
+    lib.hull_graph_destroy(g)
