@@ -61,6 +61,13 @@ def _get():
         lib.oracle_cudapre.argtypes = [P, i64, ctypes.c_int, P, P, P, P, P, P, P]
         lib.oracle_cudapre_mt.argtypes = [P, i64, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P]
         lib.oracle_cudapre_mt.restype = ctypes.c_int
+        lib.oracle3_extremes.argtypes = [P, i64, ctypes.c_int, P]
+        lib.oracle3_facets.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int]
+        lib.oracle3_facets.restype = ctypes.c_int
+        lib.oracle3_prefilter.argtypes = [P, i64, P, ctypes.c_int, P]
+        lib.oracle3_prefilter.restype = i64
+        lib.oracle3_check_domain.argtypes = [P, i64]
+        lib.oracle3_check_domain.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -182,3 +189,49 @@ def cudapre_mt(xy, angles: int = ANGLES_CUMULATIVE, threads: int = 0) -> tuple[d
     mm = int(m[0])
     return ({"extremes": ext, "poly_xy": pxy[: 2 * mm].reshape(mm, 2).copy(),
              "survivors": surv[: int(ns[0])].copy(), "hull": hl[: int(nh[0])].copy()}, int(t))
+
+
+# ---- the 3D extension (section 5) -------------------------------------------
+
+def _pts3(xyz) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
+
+
+def extremes3(xyz, angles: int = ANGLES_CUMULATIVE) -> np.ndarray:
+    """24 extreme indices: slot 6g + {0..5} = argmin/argmax of x', y', z' of rotation group g (about z)."""
+    a = _pts3(xyz)
+    out = np.full(24, -1, dtype=np.int64)
+    _get().oracle3_extremes(a.ctypes.data, a.shape[0], angles, out.ctypes.data)
+    return out
+
+
+def facets3(xyz, ext_idx, max_planes: int = 256) -> np.ndarray:
+    """Facet planes [m, 4] (Nx, Ny, Nz, d; N.p <= d on the polyhedron, reduced, sorted)."""
+    a = _pts3(xyz)
+    e = np.ascontiguousarray(np.asarray(ext_idx, dtype=np.int64))
+    out = np.zeros(4 * max_planes, dtype=np.int64)
+    m = _get().oracle3_facets(a.ctypes.data, e.ctypes.data, e.shape[0], out.ctypes.data, max_planes)
+    if m < 0:
+        raise ValueError("more facets than max_planes")
+    return out[:4 * m].reshape(m, 4).copy()
+
+
+def prefilter3(xyz, planes) -> np.ndarray:
+    """Ascending indices of the points not strictly inside the polyhedron."""
+    a = _pts3(xyz)
+    p = np.ascontiguousarray(np.asarray(planes, dtype=np.int64).reshape(-1, 4))
+    out = np.empty(max(a.shape[0], 1), dtype=np.int64)
+    c = _get().oracle3_prefilter(a.ctypes.data, a.shape[0], p.ctypes.data, p.shape[0], out.ctypes.data)
+    return out[:c].copy()
+
+
+def check_domain3(xyz) -> bool:
+    a = _pts3(xyz)
+    return bool(_get().oracle3_check_domain(a.ctypes.data, a.shape[0]))
+
+
+def cudapre3(xyz, angles: int = ANGLES_CUMULATIVE) -> dict:
+    """The 3D extension in order: extremes, polyhedron, survivors."""
+    ext = extremes3(xyz, angles)
+    planes = facets3(xyz, ext) if _pts3(xyz).shape[0] else np.zeros((0, 4), np.int64)
+    return {"extremes": ext, "planes": planes, "survivors": prefilter3(xyz, planes)}

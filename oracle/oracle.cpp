@@ -24,6 +24,9 @@
 //   oracle_cudapre_mt   -- the same steps split over host threads, for the
 //                          all-cores CPU baseline (tested equal to the
 //                          single-thread oracle).
+//   oracle3_*           -- the 3D extension sketched in section 5: extremes
+//                          of the set and of copies rotated about one axis,
+//                          their convex polyhedron, the strict-inside discard.
 //
 // Conventions where the paper is silent (each is a stated reading):
 //   * Rotation is counter-clockwise: x' = x c - y s, y' = x s + y c, each
@@ -430,6 +433,136 @@ int oracle_cudapre_mt(const float* xy, int64_t n, int angles, int threads,
   for (size_t j = 0; j < hull.size(); ++j) hull_idx[j] = hull[j].idx;
   *n_hull = (int64_t)hull.size();
   return T;
+}
+
+// ---------------------------------------------------------------------------
+// The 3D extension (section 5): six extremes (min/max of x, y, z) of the
+// original set and of copies rotated about one axis, the convex polyhedron
+// of those points, and the discard of the points strictly inside it.
+// Readings where section 5 is silent:
+//   * the rotation axis is z, with the angle table of 2D (cumulative 0, 30,
+//     75, 120 degrees or absolute 0, 30, 45, 60): x' and y' exactly as in
+//     2D, z' = z;
+//   * slot 6g + k of group g: k = 0 argmin x', 1 argmax x', 2 argmin y',
+//     3 argmax y', 4 argmin z', 5 argmax z'; ties go to the lowest index;
+//   * points are float32 xyz, integer-valued with |v| <= 2^19, so every
+//     plane test below is exact in int64 (normal components below 2^42,
+//     offsets and tests below 2^63);
+//   * the polyhedron is given by its facet planes (N, d), N an outward
+//     normal with N.p <= d for every extreme point, reduced so that the
+//     gcd of |Nx|, |Ny|, |Nz|, |d| is 1; fewer than four affinely
+//     independent extremes give no facets and discard nothing;
+//   * "inside" is strictly inside: N.p < d for every facet.
+
+// O1-3D -- the 24 extremes; every group and axis computed independently.
+void oracle3_extremes(const float* xyz, int64_t n, int angles, int64_t* out_idx) {
+  Rot t[4];
+  angle_table(angles, t);
+  for (int g = 0; g < 4; ++g) {
+    int64_t best[6];
+    double val[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 6; ++k) best[k] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+      double x = (double)xyz[3 * i];
+      double y = (double)xyz[3 * i + 1];
+      double z = (double)xyz[3 * i + 2];
+      double v[3] = {rot_x(x, y, t[g]), rot_y(x, y, t[g]), z};
+      for (int a = 0; a < 3; ++a) {
+        if (best[2 * a] < 0 || v[a] < val[2 * a]) { val[2 * a] = v[a]; best[2 * a] = i; }
+        if (best[2 * a + 1] < 0 || v[a] > val[2 * a + 1]) { val[2 * a + 1] = v[a]; best[2 * a + 1] = i; }
+      }
+    }
+    for (int k = 0; k < 6; ++k) out_idx[6 * g + k] = best[k];
+  }
+}
+
+namespace {
+
+struct P3 {
+  int64_t x, y, z, idx;
+};
+
+int64_t gcd_abs(int64_t a, int64_t b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+}  // namespace
+
+// O2-3D -- the facet planes of the convex polyhedron of the extremes, by
+// the definition: the plane through three distinct, non-collinear extremes
+// is a facet plane when every extreme lies on one closed side of it.  Each
+// plane is written once (reduced, outward), in lexicographic order, as
+// planes[4k..4k+3] = Nx, Ny, Nz, d.  Returns the facet count (at most
+// max_planes; -1 if there are more).
+int oracle3_facets(const float* xyz, const int64_t* ext_idx, int nslots, int64_t* planes, int max_planes) {
+  std::vector<P3> pts;
+  for (int k = 0; k < nslots; ++k) {
+    int64_t i = ext_idx[k];
+    if (i < 0) continue;
+    P3 q = {(int64_t)xyz[3 * i], (int64_t)xyz[3 * i + 1], (int64_t)xyz[3 * i + 2], i};
+    bool dup = false;
+    for (const P3& r : pts)
+      if (r.x == q.x && r.y == q.y && r.z == q.z) dup = true;
+    if (!dup) pts.push_back(q);
+  }
+  std::vector<std::vector<int64_t>> found;
+  size_t u = pts.size();
+  for (size_t a = 0; a < u; ++a)
+    for (size_t b = a + 1; b < u; ++b)
+      for (size_t c = b + 1; c < u; ++c) {
+        int64_t ux = pts[b].x - pts[a].x, uy = pts[b].y - pts[a].y, uz = pts[b].z - pts[a].z;
+        int64_t vx = pts[c].x - pts[a].x, vy = pts[c].y - pts[a].y, vz = pts[c].z - pts[a].z;
+        int64_t nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+        if (nx == 0 && ny == 0 && nz == 0) continue;  // collinear
+        int64_t d = nx * pts[a].x + ny * pts[a].y + nz * pts[a].z;
+        int pos = 0, neg = 0;
+        for (size_t e = 0; e < u; ++e) {
+          int64_t s = nx * pts[e].x + ny * pts[e].y + nz * pts[e].z - d;
+          if (s > 0) ++pos;
+          if (s < 0) ++neg;
+        }
+        if (pos == 0 && neg == 0) return 0;  // every extreme on one plane: no interior
+        if (pos > 0 && neg > 0) continue;
+        if (pos > 0) { nx = -nx; ny = -ny; nz = -nz; d = -d; }  // make every extreme satisfy N.p <= d
+        int64_t g = gcd_abs(gcd_abs(nx, ny), gcd_abs(nz, d));
+        std::vector<int64_t> pl = {nx / g, ny / g, nz / g, d / g};
+        if (std::find(found.begin(), found.end(), pl) == found.end()) found.push_back(pl);
+      }
+  std::sort(found.begin(), found.end());
+  if ((int)found.size() > max_planes) return -1;
+  for (size_t k = 0; k < found.size(); ++k)
+    for (int j = 0; j < 4; ++j) planes[4 * k + j] = found[k][j];
+  return (int)found.size();
+}
+
+// O3-3D -- the points not strictly inside the polyhedron (all of them when
+// it has no facets), ascending; returns their count.
+int64_t oracle3_prefilter(const float* xyz, int64_t n, const int64_t* planes, int m, int64_t* surv_idx) {
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t x = (int64_t)xyz[3 * i], y = (int64_t)xyz[3 * i + 1], z = (int64_t)xyz[3 * i + 2];
+    bool inside = m > 0;
+    for (int k = 0; k < m && inside; ++k)
+      if (planes[4 * k] * x + planes[4 * k + 1] * y + planes[4 * k + 2] * z - planes[4 * k + 3] >= 0) inside = false;
+    if (!inside) surv_idx[c++] = i;
+  }
+  return c;
+}
+
+// Returns 1 when every coordinate is finite, integer-valued and |v| <= 2^19.
+int oracle3_check_domain(const float* xyz, int64_t n) {
+  for (int64_t i = 0; i < 3 * n; ++i) {
+    float v = xyz[i];
+    if (!std::isfinite(v) || std::fabs(v) > 524288.0f || std::floor(v) != v) return 0;
+  }
+  return 1;
 }
 
 }  // extern "C"

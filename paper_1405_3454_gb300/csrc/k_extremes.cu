@@ -541,6 +541,7 @@ __device__ __noinline__ void ext_block_result(const float* xy, const uint32_t* w
 // Blocks per SM the streaming search is compiled for (registers per thread)
 // and the stages of its shared-memory ring.
 constexpr int EXT_MIN_BLOCKS = 2;
+constexpr int64_t EXT_MIN_CHUNKS = 8;  // least chunks per block of a streaming search
 constexpr int EXT_STAGES = 6;
 
 // One set: partly dynamic shares (stream.cuh), one partial result per
@@ -1002,6 +1003,10 @@ cudaError_t launch_extremes(const Sets& S, int64_t pairs_bound, int angles, int 
     const int64_t resident = (int64_t)device_sm_count() * std::max(occ, 1);
     int64_t G = ls.grid > 0 ? ls.grid : resident * stream_waves(S.S, npairs, resident, ls.waves);
     G = std::min<int64_t>(G, MAX_STREAM_BLOCKS);
+    // small inputs: at least EXT_MIN_CHUNKS chunks per block (each block pays
+    // a set-up, a threshold warm-up and a block result; the finishing kernel
+    // one partial result per block)
+    if (ls.grid <= 0) G = std::min<int64_t>(G, ((npairs + CHUNK - 1) / CHUNK + EXT_MIN_CHUNKS - 1) / EXT_MIN_CHUNKS);
     G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
     int64_t ppb = (npairs + G - 1) / G;
     ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;

@@ -269,6 +269,7 @@ struct WarpOut {
 
 // Blocks per SM the inside test is compiled for, and its ring's stages.
 constexpr int FLT_MIN_BLOCKS = 3;
+constexpr int64_t FLT_MIN_CHUNKS = 4;  // least chunks per block of an inside test
 constexpr int FLT_STAGES = 2;
 using FilterStream = StreamSmemT<FLT_STAGES>;
 // Points per thread between two drains of the queue (8 = once per chunk).
@@ -608,6 +609,8 @@ cudaError_t stream_launch(K kernel, bool& attr_done, size_t dsmem, int64_t npair
   }
   G = grid > 0 ? grid : resident * stream_waves(sets, npairs, resident, ls.waves);
   G = std::min<int64_t>(G, MAX_STREAM_BLOCKS);
+  // small inputs: at least FLT_MIN_CHUNKS chunks per block
+  if (grid <= 0) G = std::min<int64_t>(G, ((npairs + CHUNK - 1) / CHUNK + FLT_MIN_CHUNKS - 1) / FLT_MIN_CHUNKS);
   G = std::max<int64_t>(1, std::min<int64_t>(G, (npairs + CHUNK - 1) / CHUNK));
   ppb = (npairs + G - 1) / G;
   ppb = (ppb + CHUNK - 1) / CHUNK * CHUNK;

@@ -53,6 +53,9 @@ def _get():
         lib.synth_mix64.restype = u64
         lib.synth_draw.argtypes = [u64, u64, u64, u64]
         lib.synth_draw.restype = u64
+        lib.synth_cube3.argtypes = [P, i64, u64, u64, i64]
+        lib.synth_ball3.argtypes = [P, i64, u64, u64, i64]
+        lib.synth_gauss3.argtypes = [P, i64, u64, u64, ctypes.c_double, i64]
         _lib = lib
     return _lib
 
@@ -211,3 +214,42 @@ def serving_requests(n: int, k_sets: int, seed: int = BASE_SEED):
     sets = np.fromiter((draw(seed, 62, r, 0) % k_sets for r in range(n)), dtype=np.int64, count=n)
     gaps = np.fromiter((-np.log(_unit(seed, 63, r, 0)) for r in range(n)), dtype=np.float64, count=n)
     return sets, np.cumsum(gaps)
+
+
+# ---- 3D point sets (float32 xyz [n][3], integer-valued, |v| <= 2^19) -------
+
+R19 = 1 << 19
+
+
+def _out3(n: int, out=None) -> np.ndarray:
+    if out is None:
+        return np.empty((n, 3), dtype=np.float32)
+    assert out.dtype == np.float32 and out.shape == (n, 3) and out.flags.c_contiguous
+    return out
+
+
+def cube3(n: int, seed: int = BASE_SEED, r: int = R19, stream: int = 0, out=None) -> np.ndarray:
+    """Uniform integer points in [-r, r]^3."""
+    a = _out3(n, out)
+    _get().synth_cube3(a.ctypes.data, n, seed, stream, r)
+    return a
+
+
+def ball3(n: int, seed: int = BASE_SEED, r: int = R19, stream: int = 0, out=None) -> np.ndarray:
+    """Uniform integer points in the ball of radius r (indexed rejection)."""
+    a = _out3(n, out)
+    _get().synth_ball3(a.ctypes.data, n, seed, stream, r)
+    return a
+
+
+def gauss3(n: int, seed: int = BASE_SEED, sigma: float = float(1 << 17), clip: int = R19, stream: int = 0,
+           out=None) -> np.ndarray:
+    """Integer-valued Gaussian points, sigma per axis, clipped to [-clip, clip]."""
+    a = _out3(n, out)
+    _get().synth_gauss3(a.ctypes.data, n, seed, stream, float(sigma), clip)
+    return a
+
+
+def shape3(kind: int, n: int, seed: int, stream: int = 0) -> np.ndarray:
+    """3D shape id 0 = cube r=2^19, 1 = ball r=2^19, 2 = Gaussian sigma=2^17 clipped at 2^19."""
+    return (cube3, ball3, gauss3)[kind](n, seed, stream=stream)

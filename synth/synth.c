@@ -9,6 +9,8 @@
  *
  * Output format: float32 xy interleaved, [n][2], integer-valued coordinates
  * with |v| <= 2^24 -- the domain in which orientation tests are exact in int64.
+ * The 3D generators (cube3, ball3, gauss3) write float32 xyz interleaved,
+ * [n][3], integer-valued with |v| <= 2^19, the domain of the 3D extension.
  *
  * Shapes follow the paper's data groups (section 3): uniform points in a
  * square and in a circle (the rbox data), plus Gaussian clusters standing in
@@ -195,5 +197,50 @@ void synth_set_plan(int64_t s, uint64_t seed, double lo, double hi,
     if (sz > (int64_t)hi) sz = (int64_t)hi;
     sizes[k] = sz;
     shapes[k] = (int32_t)(draw(seed, 0x5E75, (uint64_t)k, 1) % 3u);
+  }
+}
+
+/* ---- 3D point sets (float32 xyz interleaved, [n][3]) ------------------- */
+
+/* Uniform integer points in the cube [-r, r]^3. */
+void synth_cube3(float* xyz, int64_t n, uint64_t seed, uint64_t stream, int64_t r) {
+#pragma omp parallel for schedule(static) if (n > 65536)
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) xyz[3 * i + c] = (float)uni_int(draw(seed, stream, (uint64_t)i, (uint64_t)c), r);
+}
+
+/* Uniform integer points in the ball x^2 + y^2 + z^2 <= r^2 (indexed
+ * rejection from the cube, as synth_disk). */
+void synth_ball3(float* xyz, int64_t n, uint64_t seed, uint64_t stream, int64_t r) {
+#pragma omp parallel for schedule(static) if (n > 65536)
+  for (int64_t i = 0; i < n; ++i) {
+    for (uint64_t k = 0;; ++k) {
+      int64_t x = uni_int(draw(seed, stream, (uint64_t)i, 3 * k), r);
+      int64_t y = uni_int(draw(seed, stream, (uint64_t)i, 3 * k + 1), r);
+      int64_t z = uni_int(draw(seed, stream, (uint64_t)i, 3 * k + 2), r);
+      if (x * x + y * y + z * z <= r * r) {
+        xyz[3 * i] = (float)x;
+        xyz[3 * i + 1] = (float)y;
+        xyz[3 * i + 2] = (float)z;
+        break;
+      }
+    }
+  }
+}
+
+/* Integer-valued Gaussian points (Box-Muller per coordinate pair), standard
+ * deviation sigma, rounded to nearest and clipped to [-clip, clip]. */
+void synth_gauss3(float* xyz, int64_t n, uint64_t seed, uint64_t stream, double sigma, int64_t clip) {
+  const double two_pi = 6.283185307179586;
+#pragma omp parallel for schedule(static) if (n > 65536)
+  for (int64_t i = 0; i < n; ++i) {
+    double u1 = uni01(draw(seed, stream, (uint64_t)i, 0));
+    double u2 = uni01(draw(seed, stream, (uint64_t)i, 1));
+    double u3 = uni01(draw(seed, stream, (uint64_t)i, 2));
+    double u4 = uni01(draw(seed, stream, (uint64_t)i, 3));
+    double r1 = sqrt(-2.0 * log(u1)) * sigma, r2 = sqrt(-2.0 * log(u3)) * sigma;
+    xyz[3 * i] = (float)clampi(llrint(r1 * cos(two_pi * u2)), -clip, clip);
+    xyz[3 * i + 1] = (float)clampi(llrint(r1 * sin(two_pi * u2)), -clip, clip);
+    xyz[3 * i + 2] = (float)clampi(llrint(r2 * cos(two_pi * u4)), -clip, clip);
   }
 }
