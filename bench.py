@@ -247,6 +247,53 @@ def small_set_leg(cp, torch, synth, exact, fp32, steps, sh, stream):
     return res
 
 
+def three_d_leg(cp, torch, synth, fp32, exact, steps, stream, world, timed, peak):
+    """hull3_prefilter on 2^26 lattice points uniform in the ball of radius
+    2^19 (768 MB, larger than L2): Gpoints/s of both arithmetic forms, the
+    stage split, and the HBM fraction of the two streaming passes (12 B per
+    point read by each; 4 B per survivor written by the inside test)."""
+    if steps <= 0:
+        return None
+    n3 = 1 << 26
+    x3 = torch.from_numpy(synth.ball3(n3, SEED + 51)).cuda()
+    ws_b = cp.hull3_prefilter_workspace_bytes(n3)
+    ws3 = cp.workspace(ws_b)
+    s3 = torch.empty(n3, dtype=torch.int32, device="cuda")
+    c3 = torch.empty(1, dtype=torch.int64, device="cuda")
+    sh = int(stream.cuda_stream)
+
+    def step3(opt):
+        code = cp.hull3_prefilter(x3.data_ptr(), n3, ws3.data_ptr(), ws_b, s3.data_ptr(), c3.data_ptr(), 0, opt, sh)
+        if code:
+            raise cp.HullError(code, "hull3_prefilter")
+
+    out = {"workload": "2^26 points, integers uniform in the ball of radius 2^19 (768 MB, seeded)",
+           "rotation_axis": "z", "angles": "cumulative 0/30/75/120"}
+    for name, opt, k in (("fp32_filtered", fp32, steps), ("plain_exact", exact, max(2, steps // 4))):
+        for _ in range(2):
+            step3(opt)
+        ms = timed(step3, opt, k)
+        t = cp.StageTimer(max_calls=k)
+        timed(step3, opt, k, t)
+        st, calls = t.read()
+        t.close()
+        info = cp.read_polyhedron(ws3)
+        f = info["n_survivors"] / n3
+        per = {kk: v / max(calls, 1) for kk, v in st.items()}
+        out[name] = {"value": world * n3 / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                     "stages_ms": {"extremes": per["extremes"], "polyhedron": per["polygon"],
+                                   "inside_test": per["filter"]},
+                     "survivor_fraction": f, "facets": len(info["planes"]), "escalations": info["n_escalated"]}
+        if name == "fp32_filtered":
+            ext_gbs = 12.0 * n3 / (per["extremes"] * 1e-3) / 1e9
+            flt_gbs = (12.0 + 4.0 * f) * n3 / (per["filter"] * 1e-3) / 1e9
+            out[name]["extremes_hbm_frac"] = ext_gbs / peak
+            out[name]["inside_test_hbm_frac"] = flt_gbs / peak
+    del x3, ws3, s3
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -430,6 +477,9 @@ def run_ours(args):
     # writing a 256 MB buffer before every timed call).
     small = small_set_leg(cp, torch, synth, exact, fp32, args.small_steps, sh, stream)
 
+    # The 3D extension (section 5) on 2^26 points uniform in a ball.
+    three_d = three_d_leg(cp, torch, synth, fp32, exact, args.steps_3d, stream, world, timed, peak)
+
     # Batched workload: many independent sets in one hull_batch call.
     batch = None
     if args.batch_sets > 0:
@@ -572,6 +622,7 @@ def run_ours(args):
                          "prefilter_only": prefilter,
                          "near_edge": near_edge,
                          "small_set_1m": small,
+                         "three_d": three_d,
                          "batch": batch,
                          "serving": serving},
             "stages_ms_per_step": stages_out,
@@ -599,6 +650,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--small-steps", type=int, default=200, help="timed calls of the 1M-point leg (0: skip it)")
+    ap.add_argument("--steps-3d", type=int, default=20, help="timed calls of the 3D leg (0: skip it)")
     ap.add_argument("--batch-sets", type=int, default=4096, help="sets of the batched leg (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=100_000, help="requests of the serving leg (0: skip it)")

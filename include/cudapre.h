@@ -305,6 +305,53 @@ void hull_constants(double* out);
 /* ABI version of this header. */
 int32_t hull_abi_version(void);
 
+/* ---- The 3D extension (section 5) ------------------------------------- */
+
+/* Section 5 sketches the method in 3D: six extremes (min/max of x, y, z) of
+ * the point set and of copies rotated about one axis, the convex polyhedron
+ * of those points, and the discard of the points strictly inside it.  Here
+ * the axis is z and the rotations are Step 1's angle table (options.angles):
+ * x' and y' as in 2D, z' = z.
+ * Points     float32 xyz interleaved (point i at xyz[3i..3i+2]), the address
+ *            16-byte aligned; coordinates finite, integer-valued, within
+ *            [-2^19, 2^19], so every plane test is exact in int64.  Outside
+ *            that domain results are undefined unless options.validate is
+ *            set (HULL_DEVICE_DOMAIN, empty results).
+ * Extremes   24 slots, slot 6g + k for rotation group g: k = 0 argmin x',
+ *            1 argmax x', 2 argmin y', 3 argmax y', 4 argmin z', 5 argmax
+ *            z'; ties go to the lowest index.
+ * Polyhedron facet planes (Nx, Ny, Nz, d), int64: every extreme satisfies
+ *            N.p <= d; each plane once, reduced (gcd of the four absolute
+ *            values 1), in lexicographic order.  Fewer than four affinely
+ *            independent extremes give no facet, and nothing is discarded.
+ * Inside     strictly inside: N.p < d for every facet.
+ * Options    angles, filter (EXACT: binary64 projections and int64 plane
+ *            tests throughout; FP32: float32 filters with exact escalation,
+ *            identical results) and validate apply; no_prefilter does not. */
+#define HULL3_SLOTS 24
+#define HULL3_MAX_FACETS 48
+
+/* Bytes of workspace hull3_prefilter needs (a fixed 1.2 MB; n may be any). */
+size_t hull3_prefilter_workspace_bytes(int64_t n, const hull_options* opt);
+
+/* The 3D extension on one point set of n points (n in [0, 2^32 - 1]).
+ *   d_survivor_idx   room for n uint32: the points not strictly inside the
+ *                    polyhedron, in unspecified order (compare as a set).
+ *   d_n_survivors    one int64: their number.
+ *   d_extreme_idx    24 uint32 (may be NULL): the extremes, see above; all
+ *                    0xFFFFFFFF when n == 0.
+ * The polyhedron stays in the workspace (hull3_read_polyhedron). */
+hull_status hull3_prefilter(const float* d_xyz, int64_t n, void* d_ws, size_t ws_bytes, uint32_t* d_survivor_idx,
+                            int64_t* d_n_survivors, uint32_t* d_extreme_idx, const hull_options* opt, void* stream);
+
+/* The polyhedron of the last hull3_prefilter on this workspace (host
+ * memory; synchronises the stream): *h_nf facets, h_planes[4k .. 4k+3] =
+ * Nx, Ny, Nz, d of facet k (room for 4 * HULL3_MAX_FACETS int64; may be
+ * NULL), h_ext the 24 extremes (may be NULL), h_counts[3] = survivors,
+ * float32 plane tests escalated to int64, device status bits (may be NULL). */
+hull_status hull3_read_polyhedron(const void* d_ws, int32_t* h_nf, int64_t* h_planes, uint32_t* h_ext,
+                                  int64_t* h_counts, void* stream);
+
 /* ---- Instrumentation (not part of the method) -------------------------- */
 
 /* Stages of one call, in launch order: domain check (and batch set-up),

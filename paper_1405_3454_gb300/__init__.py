@@ -39,7 +39,8 @@ ABI_SYMBOLS = (
     "hull_timer_create", "hull_timer_destroy", "hull_timer_attach", "hull_timer_read", "hull_launch_count",
     "hull_compute_static", "hull_batch", "hull_batch_workspace_bytes", "hull_batch_ranges",
     "hull_selftest_wait", "hull_batch_read_set", "hull_graph_create", "hull_graph_destroy",
-    "hull_graph_batch_ranges", "hull_graph_counts",
+    "hull_graph_batch_ranges", "hull_graph_counts", "hull3_prefilter_workspace_bytes", "hull3_prefilter",
+    "hull3_read_polyhedron",
 )
 HULL_STAGES = 6
 STAGE_NAMES = ("validate", "extremes", "polygon", "filter", "hull", "final")
@@ -140,6 +141,12 @@ def load(path: str | None = None):
     lib.hull_graph_batch_ranges.restype = st
     lib.hull_graph_counts.argtypes = [P, P]
     lib.hull_graph_counts.restype = None
+    lib.hull3_prefilter_workspace_bytes.argtypes = [i64, OP]
+    lib.hull3_prefilter_workspace_bytes.restype = sz
+    lib.hull3_prefilter.argtypes = [P, i64, P, sz, P, P, P, OP, P]
+    lib.hull3_prefilter.restype = st
+    lib.hull3_read_polyhedron.argtypes = [P, P, P, P, P, P]
+    lib.hull3_read_polyhedron.restype = st
     _lib = lib
     return lib
 
@@ -386,6 +393,65 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# The 3D extension (section 5).
+
+HULL3_SLOTS = 24
+HULL3_MAX_FACETS = 48
+
+
+def hull3_prefilter_workspace_bytes(n: int, opt: Options | None = None) -> int:
+    return int(load().hull3_prefilter_workspace_bytes(n, ctypes.byref((opt or Options()).c())))
+
+
+def hull3_prefilter(d_xyz: int, n: int, d_ws: int, ws_bytes: int, d_survivor_idx: int, d_n_survivors: int,
+                    d_extreme_idx: int, opt: Options | None, stream: int) -> int:
+    o = (opt or Options()).c()
+    return load().hull3_prefilter(d_xyz or None, n, d_ws, ws_bytes, d_survivor_idx or None, d_n_survivors,
+                                  d_extreme_idx or None, ctypes.byref(o), stream or None)
+
+
+def _check_points3(xyz):
+    import torch
+    if not isinstance(xyz, torch.Tensor) or not xyz.is_cuda:
+        raise TypeError("xyz must be a CUDA torch.Tensor")
+    if xyz.dtype != torch.float32 or xyz.dim() != 2 or xyz.shape[1] != 3 or not xyz.is_contiguous():
+        raise ValueError("xyz must be a contiguous float32 tensor of shape [n, 3]")
+    return int(xyz.shape[0])
+
+
+def prefilter3(xyz, opt: Options | None = None, ws=None, stream=None):
+    """The 3D extension on one set.  Returns (survivor_idx int32 [n] (uint32
+    bits), n_survivors int64 [1], extreme_idx int32 [24] (uint32 bits), ws)."""
+    import torch
+    n = _check_points3(xyz)
+    opt = opt or Options()
+    need = hull3_prefilter_workspace_bytes(n, opt)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, xyz.device)
+    surv = torch.empty(max(n, 1), dtype=torch.int32, device=xyz.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=xyz.device)
+    ext = torch.empty(HULL3_SLOTS, dtype=torch.int32, device=xyz.device)
+    _check(hull3_prefilter(_ptr(xyz), n, _ptr(ws), ws.numel(), _ptr(surv), _ptr(cnt), _ptr(ext), opt,
+                           _stream_handle(stream)), "hull3_prefilter")
+    return surv, cnt, ext, ws
+
+
+def read_polyhedron(ws, stream=None) -> dict:
+    """The last hull3_prefilter's polyhedron: facet planes [m][4] (int),
+    extremes [24], survivors, escalations, status bits."""
+    nf = ctypes.c_int32(0)
+    planes = (ctypes.c_int64 * (4 * HULL3_MAX_FACETS))()
+    ext = (ctypes.c_uint32 * HULL3_SLOTS)()
+    counts = (ctypes.c_int64 * 3)()
+    _check(load().hull3_read_polyhedron(_ptr(ws), ctypes.byref(nf), planes, ext, counts, _stream_handle(stream)),
+           "hull3_read_polyhedron")
+    m = int(nf.value)
+    return {"planes": [[int(planes[4 * k + q]) for q in range(4)] for k in range(m)],
+            "extremes": [int(v) for v in ext], "n_survivors": int(counts[0]), "n_escalated": int(counts[1]),
+            "device_status": int(counts[2])}
 
 
 def read_counters(ws, stream=None):
