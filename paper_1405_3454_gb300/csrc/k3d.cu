@@ -19,12 +19,14 @@
 //               24 slots, the facet planes of the extremes by the definition
 //               (a plane through three extremes with all of them on one
 //               side, written once, reduced, outward), float32 plane
-//               coefficients with a static error bound, and an inscribed
-//               sphere.
-// k3_filter     the inside test and compaction: a point inside the sphere
-//               is discarded at once; otherwise every facet in float32 with
-//               escalation to int64 inside the bound (or int64 throughout in
-//               EXACT mode), a point failing a facet survives.
+//               coefficients with a static error bound, the cell grid's
+//               placement.
+// k3_cells      the 64^3 cell codes (exact): inside every facet, outside
+//               one, one facet uncertain, several.
+// k3_filter     the inside test and compaction: the point's cell decides,
+//               or its one uncertain facet in float32 with escalation to
+//               int64 inside the bound, or every facet (EXACT mode: every
+//               facet in int64 for every point).
 #include <cfloat>
 
 #include "internal.cuh"
@@ -41,6 +43,9 @@ constexpr int MAXP3 = 24;        // distinct extreme points
 constexpr int T3 = 256;          // threads of the streaming kernels
 constexpr int64_t MAX_B3 = 4096; // blocks (partial results) of the extreme search
 constexpr float COORD3 = 524288.0f;  // 2^19
+// groups of four points a thread loads at once: the float32 search, the
+// plain binary64 search (register-bound), the inside test
+constexpr int QU_EXT = 2, QU_EXACT = 1, QU_FLT = 2;
 
 template <int ANG>
 struct Dirs3 {
@@ -65,10 +70,22 @@ __device__ __forceinline__ double val64_3(int v, float x, float y, float z) {
   return v == 2 ? (double)z : value64(ANG, v2of(v), x, y);
 }
 
+// Cell grid of the inside test: CG^3 cells of 2^k lattice points per axis
+// from (gx, gy, gz), over the bounding box of the extremes (outside it a
+// point is outside the polyhedron).  A cell's byte code, exact in int64:
+// CELL3_IN every lattice point of the cell is strictly inside every facet;
+// CELL3_OUT every point of the cell fails one facet; f + 1 only facet f can
+// fail in the cell; CELL3_MANY several can.
+constexpr int CG_LOG = 6;
+constexpr int CG = 1 << CG_LOG;
+constexpr int CELLS3 = CG * CG * CG;
+constexpr uint8_t CELL3_IN = 0, CELL3_OUT = 254, CELL3_MANY = 255;
+
 struct Poly3 {
   int32_t nf;           // facets (0: nothing is strictly inside)
-  int32_t sphere_on;
-  float cx, cy, cz, r2; // inscribed sphere: (x-cx)^2+(y-cy)^2+(z-cz)^2 < r2 (float32, proven margin) => inside
+  int32_t kc;           // log2 of the cell size
+  int32_t gx, gy, gz;   // grid origin (a multiple of the cell size)
+  int32_t pad_;
   uint32_t ext[NSLOT3];
   long long pl[MAXF3][4];  // Nx, Ny, Nz, d: strictly inside iff N.p < d for every facet
   float4 fc[MAXF3];        // float32 A, B, C, D: s = fma(A, x, fma(B, y, fma(C, z, D))) ~ N.p - d
@@ -114,25 +131,58 @@ __device__ __forceinline__ bool better3(int d, float sa, uint32_t ia, float sb, 
 // ----------------------------------------------------------------------------
 // Step 1 in 3D.
 
+// The rare path of direction d over the four points w[0..3] (indices i0 ..
+// i0 + 3, in order): the running best (*best, *bidx) replaced by every point
+// strictly better than it.  Out of line: the streaming loop stays small.
+template <int ANG>
+__device__ __noinline__ uint2 slow3(int d, float w0, float w1, float w2, float w3, uint32_t i0, float b, uint32_t bi,
+                                    const float* xyz) {
+  const float w[4] = {w0, w1, w2, w3};
+  for (int p = 0; p < 4; ++p) {
+    const float sc = (d & 1) ? w[p] : -w[p];
+    if (better3<ANG>(d, sc, i0 + p, b, bi, xyz)) { b = sc; bi = i0 + p; }
+  }
+  return make_uint2(__float_as_uint(b), bi);  // (the running best, by value: it stays in registers)
+}
+
 template <int ANG, int FILTER>
 __global__ void __launch_bounds__(T3, 2) k3_extremes(const float* __restrict__ xyz, int64_t n, const uint32_t* status,
                                                   BlockBest* bres) {
   constexpr int NV = Dirs3<ANG>::NV, ND = Dirs3<ANG>::ND;
-  __shared__ float s_sc[T3 / 32][ND];
-  __shared__ uint32_t s_ix[T3 / 32][ND];
+  __shared__ float s_sc[ND][T3];
+  __shared__ uint32_t s_ix[ND][T3];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool dead = *reinterpret_cast<const volatile uint32_t*>(status) != 0;
   float best[ND];
   uint32_t bidx[ND];
+  float wthr[FILTER == HULL_FILTER_FP32 ? ND : 1];  // FP32 mode: the warp's best score minus the band
   double bd[FILTER == HULL_FILTER_FP32 ? 1 : ND];  // EXACT mode: the binary64 bests
+#pragma unroll
+  for (int d = 0; d < (FILTER == HULL_FILTER_FP32 ? ND : 1); ++d) wthr[d] = -FLT_MAX;
 #pragma unroll
   for (int d = 0; d < ND; ++d) { best[d] = -FLT_MAX; bidx[d] = NONE; }
 #pragma unroll
   for (int d = 0; d < (FILTER == HULL_FILTER_FP32 ? 1 : ND); ++d) bd[d] = -DBL_MAX;
   const int64_t nq = dead ? 0 : n / 4;
   const float4* Q = reinterpret_cast<const float4*>(xyz);
-  for (int64_t q = (int64_t)blockIdx.x * T3 + tid; q < nq; q += (int64_t)gridDim.x * T3) {
-    const float4 a = __ldcs(Q + 3 * q), b = __ldcs(Q + 3 * q + 1), c = __ldcs(Q + 3 * q + 2);
+  const int64_t stride = (int64_t)gridDim.x * T3;
+  // QU groups of four points per thread and iteration, all loads issued
+  // before any is used (more bytes in flight per thread)
+  constexpr int QU = FILTER == HULL_FILTER_FP32 ? QU_EXT : QU_EXACT;
+  // whole warps iterate together (warp votes below); a lane past the end
+  // repeats point group nq - 1 (a repeat never changes a best)
+  for (int64_t qb = (int64_t)blockIdx.x * T3 + (tid & ~31); qb < nq; qb += QU * stride) {
+    float4 A[QU], B[QU], C[QU];
+#pragma unroll
+    for (int u = 0; u < QU; ++u) {
+      const int64_t q = min(qb + lane + u * stride, nq - 1);
+      A[u] = __ldcs(Q + 3 * q); B[u] = __ldcs(Q + 3 * q + 1); C[u] = __ldcs(Q + 3 * q + 2);
+    }
+#pragma unroll
+    for (int u = 0; u < QU; ++u) {
+    if (qb + u * stride >= nq) break;
+    const int64_t q = min(qb + lane + u * stride, nq - 1);
+    const float4 a = A[u], b = B[u], c = C[u];
     const float px[4] = {a.x, a.w, b.z, c.y}, py[4] = {a.y, b.x, b.w, c.z}, pz[4] = {a.z, b.y, c.x, c.w};
     const uint32_t i0 = (uint32_t)(4 * q);
 #pragma unroll
@@ -144,22 +194,30 @@ __global__ void __launch_bounds__(T3, 2) k3_extremes(const float* __restrict__ x
         const float band = band3<ANG>(v);
         const float tmx = fmaxf(max3f(w[0], w[1], w[2]), w[3]);
         const float tmn = fminf(min3f(w[0], w[1], w[2]), w[3]);
-        // the tile's extreme may reach the best within the band: points in order
-        if (tmx >= best[2 * v + 1] - band) {
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-            if (better3<ANG>(2 * v + 1, w[p], i0 + p, best[2 * v + 1], bidx[2 * v + 1], xyz)) {
-              best[2 * v + 1] = w[p];
-              bidx[2 * v + 1] = i0 + p;
-            }
+        // the tile's extreme may reach the best within the band: the rare path
+        // a lane enters the rare path only when its tile may reach the
+        // warp's best within the band (wthr: warp-uniform), then updates its
+        // own best exactly; the warp's threshold follows
+        const bool hi = tmx >= wthr[2 * v + 1], lo = -tmn >= wthr[2 * v];
+        if (__any_sync(FULL, hi)) {
+          if (hi) {
+            const uint2 r = slow3<ANG>(2 * v + 1, w[0], w[1], w[2], w[3], i0, best[2 * v + 1], bidx[2 * v + 1], xyz);
+            best[2 * v + 1] = __uint_as_float(r.x);
+            bidx[2 * v + 1] = r.y;
+          }
+          float m = best[2 * v + 1];
+          for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, off));
+          wthr[2 * v + 1] = m - band;
         }
-        if (-tmn >= best[2 * v] - band) {
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-            if (better3<ANG>(2 * v, -w[p], i0 + p, best[2 * v], bidx[2 * v], xyz)) {
-              best[2 * v] = -w[p];
-              bidx[2 * v] = i0 + p;
-            }
+        if (__any_sync(FULL, lo)) {
+          if (lo) {
+            const uint2 r = slow3<ANG>(2 * v, w[0], w[1], w[2], w[3], i0, best[2 * v], bidx[2 * v], xyz);
+            best[2 * v] = __uint_as_float(r.x);
+            bidx[2 * v] = r.y;
+          }
+          float m = best[2 * v];
+          for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, off));
+          wthr[2 * v] = m - band;
         }
       } else {
         // the plain method: every point's binary64 value (the float32 score
@@ -176,36 +234,37 @@ __global__ void __launch_bounds__(T3, 2) k3_extremes(const float* __restrict__ x
         }
       }
     }
+    }
   }
-  // warp, then block: exact comparisons
+  // the block's result per direction: every thread's candidate through
+  // shared memory, one warp per direction (exact comparisons)
+  __syncthreads();
 #pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    float sc = best[d];
-    uint32_t ix = bidx[d];
+  for (int d = 0; d < ND; ++d) { s_sc[d][tid] = best[d]; s_ix[d][tid] = bidx[d]; }
+  __syncthreads();
+  for (int d = warp; d < ND; d += T3 / 32) {
+    float sc = s_sc[d][lane];
+    uint32_t ix = s_ix[d][lane];
+    for (int t = lane + 32; t < T3; t += 32)
+      if (better3<ANG>(d, s_sc[d][t], s_ix[d][t], sc, ix, xyz)) { sc = s_sc[d][t]; ix = s_ix[d][t]; }
     for (int off = 16; off; off >>= 1) {
       const float so = __shfl_xor_sync(FULL, sc, off);
       const uint32_t io = __shfl_xor_sync(FULL, ix, off);
       if (better3<ANG>(d, so, io, sc, ix, xyz)) { sc = so; ix = io; }
     }
-    if (lane == 0) { s_sc[warp][d] = sc; s_ix[warp][d] = ix; }
-  }
-  __syncthreads();
-  if (tid < ND) {
-    float sc = s_sc[0][tid];
-    uint32_t ix = s_ix[0][tid];
-    for (int w = 1; w < T3 / 32; ++w)
-      if (better3<ANG>(tid, s_sc[w][tid], s_ix[w][tid], sc, ix, xyz)) { sc = s_sc[w][tid]; ix = s_ix[w][tid]; }
-    BlockBest r;
-    r.idx = ix;
-    r.pad_ = 0;
-    r.s = -DBL_MAX;
-    if (ix != NONE) {
-      float x, y, z;
-      load_p3(xyz, ix, x, y, z);
-      const double e = val64_3<ANG>(tid >> 1, x, y, z);
-      r.s = (tid & 1) ? e : -e;
+    if (lane == 0) {
+      BlockBest r;
+      r.idx = ix;
+      r.pad_ = 0;
+      r.s = -DBL_MAX;
+      if (ix != NONE) {
+        float x, y, z;
+        load_p3(xyz, ix, x, y, z);
+        const double e = val64_3<ANG>(d >> 1, x, y, z);
+        r.s = (d & 1) ? e : -e;
+      }
+      bres[(size_t)blockIdx.x * ND + d] = r;
     }
-    bres[(size_t)blockIdx.x * ND + tid] = r;
   }
 }
 
@@ -402,43 +461,110 @@ __global__ void __launch_bounds__(T3) k3_finish(const float* __restrict__ xyz, i
     T = __fadd_ru(T, aD);
     P.fe[tid] = __fmul_ru(__fmul_ru(T, 0x1.000004p+3f), 0x1p-24f);  // 2 (4 + 2^-20) u T
   }
-  // inscribed sphere around the mean of the distinct extremes, when that
-  // integer point is strictly inside every facet (checked exactly): r^2 =
-  // min over facets of (N.c - d)^2 / |N|^2 in binary64, shrunk by 2^-18 and
-  // rounded down to float32 (the float32 distance test errs by far less)
+  // the cell grid: the smallest power-of-two cell size whose CG cells per
+  // axis, from an origin aligned to it, cover the extremes' bounding box
   if (tid == 0) {
-    P.sphere_on = 0;
-    P.r2 = -1.0f;
-    if (nf > 0) {
-      double sx = 0, sy = 0, sz = 0;
-      for (int k = 0; k < u; ++k) { sx += (double)s_px[k]; sy += (double)s_py[k]; sz += (double)s_pz[k]; }
-      const long long cx = llrint(sx / u), cy = llrint(sy / u), cz = llrint(sz / u);
-      double r2 = DBL_MAX;
-      bool ok = true;
-      for (int k = 0; k < nf && ok; ++k) {
-        const long long* q = P.pl[k];
-        const long long s = q[0] * cx + q[1] * cy + q[2] * cz - q[3];
-        if (s >= 0) { ok = false; break; }
-        const double nn = (double)q[0] * (double)q[0] + (double)q[1] * (double)q[1] + (double)q[2] * (double)q[2];
-        r2 = fmin(r2, ((double)s * (double)s) / nn);
-      }
-      if (ok) {
-        P.sphere_on = 1;
-        P.cx = (float)cx;
-        P.cy = (float)cy;
-        P.cz = (float)cz;
-        P.r2 = __double2float_rd(r2 * (1.0 - 0x1p-18));
-      }
+    long long lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      const long long* c = a == 0 ? s_px : (a == 1 ? s_py : s_pz);
+      lo[a] = hi[a] = u > 0 ? c[0] : 0;
+      for (int k = 1; k < u; ++k) { lo[a] = min(lo[a], c[k]); hi[a] = max(hi[a], c[k]); }
     }
+    int kc = 0;
+    auto origin = [](long long v, int k) { return (v >> k) << k; };  // floor to 2^k
+    for (;; ++kc) {
+      bool fits = true;
+      for (int a = 0; a < 3; ++a) fits = fits && hi[a] - origin(lo[a], kc) < ((long long)CG << kc);
+      if (fits) break;
+    }
+    P.kc = kc;
+    P.gx = (int32_t)origin(lo[0], kc);
+    P.gy = (int32_t)origin(lo[1], kc);
+    P.gz = (int32_t)origin(lo[2], kc);
+  }
+}
+
+// One thread per cell: its code (see Poly3), from the extreme values of
+// N.p - d over the cell's corners (the plane test is linear), the corners
+// clamped to the coordinate domain, so every product stays below 2^61.
+__global__ void __launch_bounds__(T3) k3_cells(Ws3* W, uint8_t* codes) {
+  __shared__ long long s_pl[MAXF3][4];
+  __shared__ int s_meta[5];
+  const int tid = threadIdx.x;
+  if (*reinterpret_cast<volatile uint32_t*>(&W->status) != 0) return;
+  const Poly3& P = W->poly;
+  if (tid == 0) { s_meta[0] = P.nf; s_meta[1] = P.kc; s_meta[2] = P.gx; s_meta[3] = P.gy; s_meta[4] = P.gz; }
+  for (int k = tid; k < 4 * MAXF3; k += T3) (&s_pl[0][0])[k] = (&P.pl[0][0])[k];
+  __syncthreads();
+  const int nf = s_meta[0];
+  if (nf == 0) return;
+  const int kc = s_meta[1];
+  for (int c = blockIdx.x * T3 + tid; c < CELLS3; c += gridDim.x * T3) {
+    const int ix = c & (CG - 1), iy = (c >> CG_LOG) & (CG - 1), iz = c >> (2 * CG_LOG);
+    long long lo[3], hi[3];
+    const long long base[3] = {(long long)s_meta[2] + ((long long)ix << kc), (long long)s_meta[3] + ((long long)iy << kc),
+                               (long long)s_meta[4] + ((long long)iz << kc)};
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = max(base[a], -(long long)COORD3);
+      hi[a] = min(base[a] + (1ll << kc) - 1, (long long)COORD3);
+    }
+    uint8_t code = CELL3_IN;
+    int unsure = 0, which = 0;
+    for (int f = 0; f < nf && code != CELL3_OUT; ++f) {
+      long long mx = -s_pl[f][3], mn = -s_pl[f][3];
+      for (int a = 0; a < 3; ++a) {
+        const long long p0 = s_pl[f][a] * lo[a], p1 = s_pl[f][a] * hi[a];
+        mx += max(p0, p1);
+        mn += min(p0, p1);
+      }
+      if (mn >= 0) code = CELL3_OUT;                  // every point fails facet f
+      else if (mx >= 0) { ++unsure; which = f; }     // some point may fail it
+    }
+    if (code != CELL3_OUT && lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2])
+      code = unsure == 0 ? CELL3_IN : (unsure == 1 ? (uint8_t)(which + 1) : CELL3_MANY);
+    if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]) code = CELL3_OUT;  // no point of the domain
+    codes[c] = code;
   }
 }
 
 // ----------------------------------------------------------------------------
 // Step 3 in 3D: the inside test and compaction of the survivors.
 
+// The code of the point's cell (CELL3_OUT outside the grid): cell
+// coordinates floor((v - g) 2^-kc) by round-down operations, exact for these
+// integers.
+__device__ __forceinline__ uint32_t cell_code(const uint8_t* codes, float gx, float gy, float gz, float sc, float x,
+                                              float y, float z) {
+  const int cx = __float2int_rd(__fsub_rd(x, gx) * sc), cy = __float2int_rd(__fsub_rd(y, gy) * sc);
+  const int cz = __float2int_rd(__fsub_rd(z, gz) * sc);
+  if ((unsigned)(cx | cy | cz) >= (unsigned)CG) return CELL3_OUT;  // outside the extremes' bounding box
+  return __ldg(codes + ((cz << (2 * CG_LOG)) | (cy << CG_LOG) | cx));
+}
+
+// Every facet of the polyhedron against one point: 2 * escalations +
+// (survives ? 1 : 0).  A facet the point fails ends the test.
+template <int FILTER>
+__device__ __noinline__ unsigned facets3(const long long (*pl)[4], const float4* fc, const float* fe, int nf, float x,
+                                         float y, float z) {
+  const long long X = (long long)x, Y = (long long)y, Z = (long long)z;
+  unsigned esc = 0;
+  for (int k = 0; k < nf; ++k) {
+    if (FILTER == HULL_FILTER_FP32) {
+      const float4 c = fc[k];
+      const float s = fmaf(c.x, x, fmaf(c.y, y, fmaf(c.z, z, c.w)));
+      const float e = fe[k];
+      if (s < -e) continue;
+      if (s > e) return 2 * esc + 1;
+      ++esc;
+    }
+    if (pl[k][0] * X + pl[k][1] * Y + pl[k][2] * Z - pl[k][3] >= 0) return 2 * esc + 1;
+  }
+  return 2 * esc;
+}
+
 template <int FILTER>
 __global__ void __launch_bounds__(T3) k3_filter(const float* __restrict__ xyz, int64_t n, Ws3* W,
-                                                uint32_t* __restrict__ surv) {
+                                                uint32_t* __restrict__ surv, const uint8_t* __restrict__ codes) {
   __shared__ long long s_pl[MAXF3][4];
   __shared__ float4 s_fc[MAXF3];
   __shared__ float s_fe[MAXF3];
@@ -449,7 +575,8 @@ __global__ void __launch_bounds__(T3) k3_filter(const float* __restrict__ xyz, i
   const Poly3& P = W->poly;
   if (tid == 0) {
     s_nf = P.nf;
-    s_sp[0] = P.cx; s_sp[1] = P.cy; s_sp[2] = P.cz; s_sp[3] = P.sphere_on ? P.r2 : -1.0f;
+    s_sp[0] = (float)P.gx; s_sp[1] = (float)P.gy; s_sp[2] = (float)P.gz;
+    s_sp[3] = __int_as_float((127 - P.kc) << 23);  // 2^-kc
   }
   for (int k = tid; k < MAXF3; k += T3) {
     s_pl[k][0] = P.pl[k][0]; s_pl[k][1] = P.pl[k][1]; s_pl[k][2] = P.pl[k][2]; s_pl[k][3] = P.pl[k][3];
@@ -458,39 +585,56 @@ __global__ void __launch_bounds__(T3) k3_filter(const float* __restrict__ xyz, i
   }
   __syncthreads();
   const int nf = s_nf;
-  const float cx = s_sp[0], cy = s_sp[1], cz = s_sp[2], r2 = s_sp[3];
+  const float gx = s_sp[0], gy = s_sp[1], gz = s_sp[2], sc = s_sp[3];
   unsigned esc = 0;
-  // survives: not strictly inside every facet
+  // survives: not strictly inside every facet.  FP32 mode: the point's cell
+  // decides (exact cell code; cell coordinates floor((v - g) 2^-kc) by
+  // round-down operations, exact for these integers), a cell with one
+  // uncertain facet takes one float32 test with escalation, several the
+  // full test; EXACT mode: every facet in int64.
+  // survives: not strictly inside every facet.  FP32 mode: the point's cell
+  // decides (exact cell code), a cell with one uncertain facet takes one
+  // float32 test with escalation, several the full test; EXACT mode: every
+  // facet in int64.
   auto survives = [&](float x, float y, float z) -> bool {
     if (nf == 0) return true;
     if (FILTER == HULL_FILTER_FP32) {
-      const float dx = x - cx, dy = y - cy, dz = z - cz;
-      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < r2) return false;
-    }
-    const long long X = (long long)x, Y = (long long)y, Z = (long long)z;
-    for (int k = 0; k < nf; ++k) {
-      if (FILTER == HULL_FILTER_FP32) {
-        const float4 c = s_fc[k];
+      const uint32_t code = cell_code(codes, gx, gy, gz, sc, x, y, z);
+      if (code == CELL3_IN) return false;
+      if (code == CELL3_OUT) return true;
+      if (code != CELL3_MANY) {
+        const int f = (int)code - 1;
+        const float4 c = s_fc[f];
         const float s = fmaf(c.x, x, fmaf(c.y, y, fmaf(c.z, z, c.w)));
-        const float e = s_fe[k];
-        if (s < -e) continue;
-        if (s > e) return true;
+        if (s < -s_fe[f]) return false;
+        if (s > s_fe[f]) return true;
         ++esc;
+        return s_pl[f][0] * (long long)x + s_pl[f][1] * (long long)y + s_pl[f][2] * (long long)z - s_pl[f][3] >= 0;
       }
-      if (s_pl[k][0] * X + s_pl[k][1] * Y + s_pl[k][2] * Z - s_pl[k][3] >= 0) return true;
     }
-    return false;
+    const unsigned r = facets3<FILTER>(s_pl, s_fc, s_fe, nf, x, y, z);
+    esc += r >> 1;
+    return r & 1;
   };
   const int64_t nq = n / 4;
   const float4* Q = reinterpret_cast<const float4*>(xyz);
   const int64_t stride = (int64_t)gridDim.x * T3;
   // whole warps iterate together: the survivors of the warp's 4 x 32 points
   // are placed with one atomic
-  for (int64_t qb = (int64_t)blockIdx.x * T3 + (tid & ~31); qb < nq; qb += stride) {
-    const int64_t q = qb + lane;
+  constexpr int QU = QU_FLT;
+  for (int64_t qb = (int64_t)blockIdx.x * T3 + (tid & ~31); qb < nq; qb += QU * stride) {
+    float4 A[QU], B[QU], C[QU];
+#pragma unroll
+    for (int u = 0; u < QU; ++u) {
+      const int64_t q = qb + lane + u * stride;
+      if (q < nq) { A[u] = __ldcs(Q + 3 * q); B[u] = __ldcs(Q + 3 * q + 1); C[u] = __ldcs(Q + 3 * q + 2); }
+    }
+#pragma unroll
+    for (int u = 0; u < QU; ++u) {
+    const int64_t q = qb + lane + u * stride;
     bool keep[4] = {false, false, false, false};
     if (q < nq) {
-      const float4 a = __ldcs(Q + 3 * q), b = __ldcs(Q + 3 * q + 1), c = __ldcs(Q + 3 * q + 2);
+      const float4 a = A[u], b = B[u], c = C[u];
       keep[0] = survives(a.x, a.y, a.z);
       keep[1] = survives(a.w, b.x, b.y);
       keep[2] = survives(b.z, b.w, c.x);
@@ -503,12 +647,15 @@ __global__ void __launch_bounds__(T3) k3_filter(const float* __restrict__ xyz, i
       if (lane >= off) pre += v;
     }
     const int total = __shfl_sync(FULL, pre, 31);
-    unsigned long long base = 0;
-    if (lane == 31 && total) base = atomicAdd(&W->n_surv, (unsigned long long)total);
-    base = __shfl_sync(FULL, base, 31);
-    unsigned long long pos = base + (unsigned long long)(pre - mine);
-    for (int p = 0; p < 4; ++p)
-      if (keep[p]) surv[pos++] = (uint32_t)(4 * q + p);
+    if (total) {
+      unsigned long long base = 0;
+      if (lane == 31) base = atomicAdd(&W->n_surv, (unsigned long long)total);
+      base = __shfl_sync(FULL, base, 31);
+      unsigned long long pos = base + (unsigned long long)(pre - mine);
+      for (int p = 0; p < 4; ++p)
+        if (keep[p]) surv[pos++] = (uint32_t)(4 * q + p);
+    }
+    }
   }
   // the at most three points after the last group of four
   if (blockIdx.x == 0 && tid < (int)(n - 4 * nq)) {
@@ -532,15 +679,19 @@ __global__ void k3_validate(const float* __restrict__ xyz, int64_t n3, uint32_t*
 
 __global__ void k3_count(const Ws3* W, int64_t* out) { *out = W->status ? 0 : (int64_t)W->n_surv; }
 
+// Blocks of the streaming passes: resident ones (two per SM), fewer for
+// small inputs (at least 16 groups of four points per thread).
 int64_t blocks3(int64_t n) {
   const int64_t nq = n / 4;
-  const int64_t want = (nq + 64 * T3 - 1) / (64 * T3);  // about 64 groups of four per thread
-  return std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(MAX_B3, (int64_t)device_sm_count() * 8)));
+  const int64_t want = (nq + 16 * T3 - 1) / (16 * T3);
+  return std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(MAX_B3, (int64_t)device_sm_count() * 2)));
 }
+
+constexpr size_t WS3_PARTIALS = align_up(sizeof(BlockBest) * 18 * (size_t)MAX_B3, 256);
 
 size_t ws3_bytes(int64_t n) {
   (void)n;
-  return WS3_HEADER + align_up(sizeof(BlockBest) * 18 * (size_t)MAX_B3, 256);
+  return WS3_HEADER + WS3_PARTIALS + align_up(CELLS3, 256);
 }
 
 }  // namespace
@@ -570,6 +721,7 @@ hull_status hull3_prefilter(const float* d_xyz, int64_t n, void* d_ws, size_t ws
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Ws3* W = static_cast<Ws3*>(d_ws);
   BlockBest* bres = reinterpret_cast<BlockBest*>(static_cast<char*>(d_ws) + WS3_HEADER);
+  uint8_t* codes = static_cast<uint8_t*>(d_ws) + WS3_HEADER + WS3_PARTIALS;
   stage_mark(0, st);
   if (cudaMemsetAsync(W, 0, sizeof(Ws3), st) != cudaSuccess) return HULL_ERR_CUDA;
   if (o.validate && n > 0) {
@@ -579,15 +731,16 @@ hull_status hull3_prefilter(const float* d_xyz, int64_t n, void* d_ws, size_t ws
   }
   stage_mark(1, st);
   const int64_t G = blocks3(n);
-  const int64_t Gf = std::max<int64_t>(1, std::min<int64_t>((n / 4 + T3 - 1) / T3, (int64_t)device_sm_count() * 8));
+  const int64_t Gf = std::max<int64_t>(1, std::min<int64_t>((n / 4 + T3 - 1) / T3, (int64_t)device_sm_count() * 4));
   // stage boundaries as the 2D calls: extremes | polyhedron | inside test
 #define K3(A, F)                                                                          \
   do {                                                                                    \
     k3_extremes<A, F><<<(unsigned)G, T3, 0, st>>>(d_xyz, n, &W->status, bres);            \
     stage_mark(2, st);                                                                    \
     k3_finish<A><<<1, T3, 0, st>>>(d_xyz, n, G, W, bres, d_extreme_idx);                  \
+    if (F == HULL_FILTER_FP32) k3_cells<<<CELLS3 / T3, T3, 0, st>>>(W, codes);            \
     stage_mark(3, st);                                                                    \
-    k3_filter<F><<<(unsigned)Gf, T3, 0, st>>>(d_xyz, n, W, d_survivor_idx);               \
+    k3_filter<F><<<(unsigned)Gf, T3, 0, st>>>(d_xyz, n, W, d_survivor_idx, codes);        \
     stage_mark(4, st);                                                                    \
   } while (0)
   if (o.angles == HULL_ANGLES_CUMULATIVE) {
@@ -597,7 +750,7 @@ hull_status hull3_prefilter(const float* d_xyz, int64_t n, void* d_ws, size_t ws
   }
 #undef K3
   k3_count<<<1, 1, 0, st>>>(W, d_n_survivors);
-  count_launches(4);
+  count_launches(o.filter == HULL_FILTER_FP32 ? 5 : 4);
   stage_mark(5, st);
   stage_mark(6, st);
   return cudaGetLastError() == cudaSuccess ? HULL_OK : HULL_ERR_CUDA;

@@ -30,6 +30,7 @@ from __future__ import annotations
 
 import bisect
 import collections
+import ctypes
 import time
 from dataclasses import dataclass, field
 
@@ -115,17 +116,26 @@ class Batcher:
     def take(self, room: int | None = None) -> list[tuple[int, int]]:
         while self.q and self.budget is not None and self.need(self.q[0][1], 1) > self.budget:
             self.refused.append(self.q.popleft()[0])
-        out, pts = [], 0
-        while self.q and len(out) < self.max_sets:
-            rid, size = self.q[0]
-            if out and pts + size > self.max_points:
+        # the longest prefix within the point and set caps, then (memory
+        # grows with the prefix) the longest part of it that fits `room`,
+        # found by bisection: a few memory evaluations per batch
+        k, pts, prefix = 0, 0, [0]
+        for rid, size in self.q:
+            if k >= self.max_sets or (k and pts + size > self.max_points):
                 break
-            if room is not None and self.need(pts + size, len(out) + 1) > room:
-                break
-            self.q.popleft()
-            out.append((rid, size))
+            k += 1
             pts += size
-        return out
+            prefix.append(pts)
+        if room is not None and k and self.need(prefix[k], k) > room:
+            lo, hi = 0, k  # need(prefix[lo], lo) fits (lo = 0: nothing), need(prefix[hi], hi) does not
+            while hi - lo > 1:
+                mid = (lo + hi) // 2
+                if self.need(prefix[mid], mid) <= room:
+                    lo = mid
+                else:
+                    hi = mid
+            k = lo
+        return [self.q.popleft() for _ in range(k)]
 
 
 @dataclass
@@ -160,6 +170,18 @@ def batch_bytes(cp, n_total: int, S: int, opt) -> int:
             + align_up(8 * (S + 1)) + align_up(8 * (2 * S + 1)))
 
 
+def batch_bytes_fn(cp, opt):
+    """batch_bytes with the options converted once (a call per batch size)."""
+    lib = cp.load()
+    copt = opt.c()
+    ref = ctypes.byref(copt)
+
+    def need(n_total: int, S: int) -> int:
+        return (align_up(lib.hull_batch_workspace_bytes(int(n_total), int(S), ref)) + align_up(8 * max(n_total, 1))
+                + align_up(8 * (S + 1)) + align_up(8 * (2 * S + 1)))
+    return need
+
+
 class Server:
     """Batches in flight on up to `streams` streams, their memory carved out
     of one arena of budget_bytes device bytes."""
@@ -175,6 +197,8 @@ class Server:
         self.opt = opt or cp.Options()
         self.max_points, self.max_sets = int(max_points), int(max_sets)
         self.budget = int(budget_bytes)
+        self._need = batch_bytes_fn(cp, self.opt)
+        self._copt = self.opt.c()
         dev = pool.device
         self.arena = Arena(self.budget)
         self.mem = torch.empty(self.arena.capacity, dtype=torch.uint8, device=dev)
@@ -189,7 +213,7 @@ class Server:
             })
 
     def need(self, n_total: int, S: int) -> int:
-        return batch_bytes(self.cp, n_total, S, self.opt)
+        return self._need(n_total, S)
 
     def batcher(self, max_points: int | None = None, max_sets: int | None = None) -> Batcher:
         return Batcher(max_points or self.max_points, min(max_sets or self.max_sets, self.max_sets), self.need,
@@ -220,7 +244,7 @@ class Server:
         off = self.arena.alloc(need)
         if off is None:
             return False
-        ws_bytes = cp.hull_batch_workspace_bytes(n_total, S, self.opt)
+        ws_bytes = int(cp.load().hull_batch_workspace_bytes(n_total, S, ctypes.byref(self._copt)))
         p_ws = self.base + off
         p_out = p_ws + align_up(ws_bytes)
         p_hoff = p_out + align_up(8 * max(n_total, 1))
