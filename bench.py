@@ -49,12 +49,12 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the two streaming kernels' sources with comments and
+    """Hash of the two streaming kernels' sources (and their headers) with comments and
     whitespace removed: a change of code, not of comments, makes recorded
     ncu traffic stale."""
     import re
     h = hashlib.sha256()
-    for f in ("k_extremes.cu", "k_filter.cu", "internal.cuh", "stream.cuh"):
+    for f in ("k_extremes.cu", "k_filter.cu", "internal.cuh", "stream.cuh", "proj.cuh"):
         with open(os.path.join(ROOT, "paper_1405_3454_gb300", "csrc", f), encoding="utf-8") as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
