@@ -2,9 +2,11 @@
 // the final step of the method, the hull of the points that remain (section
 // 3, case (2)).
 //
-// tiny     (one block per set, at most TINY_MAX points) bitonic sort in
-//          shared memory, then Andrew's lower and upper monotone chains.
-// One set of more points uses the whole GPU, without sorting:
+// A batch's sets of at most TINY_MAX points:
+// tiny     (one block per set) bitonic sort, then Andrew's lower and upper
+//          monotone chains in two levels.
+// One set uses the whole GPU, without sorting (its chain walk would be one
+// thread's sequence of dependent steps):
 // classify (one warp per survivor v) v is a vertex of the lower chain iff
 //          no point with equal coordinates has a lower index, and either v is
 //          the lexicographically smallest or largest point, or the most
@@ -278,11 +280,42 @@ __global__ void __launch_bounds__(SB, 1) k_small_prep(Sets S, const uint32_t* gs
 }
 
 // tiny: the whole hull of a set with at most TINY_MAX survivors in one
-// block: bitonic sort of (key, index) in shared memory, then the lower and
-// the upper monotone chain by one thread each (equal keys are adjacent and
-// the lowest index comes first, so later copies are skipped), then the
-// emission.
+// block.  A bitonic sort of (key, index) (partners closer than 32 by warp
+// shuffles, farther ones through shared memory), then Andrew's chains in two
+// levels: the lower and upper chain of each of TCH chunks of the sorted
+// points in parallel (one lane each), then one walk over the chunk chains'
+// vertices in order.  A point off its chunk's chain is no vertex of the
+// set's chain, so the second walk sees the same vertices as a walk over all
+// points, in far fewer steps.  Equal keys are adjacent with the lowest index
+// first; both walks skip a point equal to the top of their stack.
 constexpr int TB = 256;
+constexpr int TCH = 32;                 // chunks of the first level
+constexpr int TE = TINY_MAX / TB;       // sort elements per thread
+
+// Chain walk over the positions pos(0 .. len) of the sorted points (sign sg:
+// +1 lower, -1 upper) into q; returns its length.  Pops while the turn is
+// not strictly left (lower) / right (upper); the top two entries stay in
+// registers.
+template <class Pos>
+__device__ __forceinline__ int chain_walk(const int2* sp, int len, Pos pos, uint16_t* q, long long sg) {
+  int n = 0;
+  int x1 = 0, y1 = 0, x2 = 0, y2 = 0;
+  for (int t = 0; t < len; ++t) {
+    const int p = pos(t);
+    const int2 cur = sp[p];
+    if (n > 0 && cur.x == x1 && cur.y == y1) continue;  // equal points: the first (lowest index) stands
+    while (n >= 2) {
+      if (sg * cr(x1 - x2, y1 - y2, cur.x - x2, cur.y - y2) > 0) break;
+      --n;
+      x1 = x2; y1 = y2;
+      if (n >= 2) { const int2 u = sp[q[n - 2]]; x2 = u.x; y2 = u.y; }
+    }
+    q[n++] = (uint16_t)p;
+    x2 = x1; y2 = y1;
+    x1 = cur.x; y1 = cur.y;
+  }
+  return n;
+}
 
 __global__ void __launch_bounds__(TB) k_small_tiny(Sets S, const uint32_t* gstatus, int which,
                                                     const unsigned long long* __restrict__ kin_base,
@@ -290,8 +323,9 @@ __global__ void __launch_bounds__(TB) k_small_tiny(Sets S, const uint32_t* gstat
                                                     uint32_t* __restrict__ out_base, int64_t* out_n_base) {
   __shared__ unsigned long long sk[TINY_MAX];
   __shared__ uint32_t si[TINY_MAX];
-  __shared__ uint16_t st[2][TINY_MAX];
-  __shared__ unsigned long long stk[2][TINY_MAX];
+  __shared__ uint16_t sc[2][TINY_MAX];  // chunk chains, chunk c's from c * C
+  __shared__ uint16_t sq[2][TINY_MAX];  // the set's chains
+  __shared__ int s_cc[2][TCH];
   __shared__ int s_n[2];
   const int tid = threadIdx.x;
   const int set = blockIdx.x;
@@ -307,72 +341,108 @@ __global__ void __launch_bounds__(TB) k_small_tiny(Sets S, const uint32_t* gstat
   const int64_t o = S.off_at(set);
   int P2 = 2;
   while (P2 < m) P2 <<= 1;
-  for (int i = tid; i < P2; i += TB) {
-    sk[i] = i < m ? kin_base[o + i] : ~0ull;
-    si[i] = i < m ? vin_base[o + i] : ~0u;
-  }
-  __syncthreads();
-  for (int k = 2; k <= P2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < P2; i += TB) {
-        const int l = i ^ j;
-        if (l > i) {
-          const unsigned long long a = sk[i], b = sk[l];
-          const uint32_t ai = si[i], bi = si[l];
-          const bool gt = a > b || (a == b && ai > bi);
-          if (gt == ((i & k) == 0)) { sk[i] = b; sk[l] = a; si[i] = bi; si[l] = ai; }
+  {
+    // element i = r * TB + tid in registers; padding sorts last
+    const int NE = (P2 + TB - 1) / TB;
+    unsigned long long qk[TE];
+    uint32_t qv[TE];
+#pragma unroll
+    for (int r = 0; r < TE; ++r) {
+      const int i = r * TB + tid;
+      qk[r] = (r < NE && i < m) ? kin_base[o + i] : ~0ull;
+      qv[r] = (r < NE && i < m) ? vin_base[o + i] : ~0u;
+    }
+    for (int k = 2; k <= P2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        if (j >= TB) {  // partner in the same thread: element r ^ (j / TB)
+          auto in_thread = [&](auto JR) {
+            constexpr int jr = decltype(JR)::value;
+#pragma unroll
+            for (int r = 0; r < TE; ++r) {
+              const int l = r ^ jr;
+              if (l > r && l < TE && r < NE) {
+                const bool asc = ((r * TB + tid) & k) == 0;
+                const bool gt = qk[r] > qk[l] || (qk[r] == qk[l] && qv[r] > qv[l]);
+                if (gt == asc) {
+                  const unsigned long long tk = qk[r]; qk[r] = qk[l]; qk[l] = tk;
+                  const uint32_t tv = qv[r]; qv[r] = qv[l]; qv[l] = tv;
+                }
+              }
+            }
+          };
+          static_assert(TE <= 4, "in-thread partners at distances TB and 2 TB");
+          if (j == TB) in_thread(std::integral_constant<int, 1>{});
+          else in_thread(std::integral_constant<int, 2>{});
+          continue;
         }
+        if (j >= 32) {
+#pragma unroll
+          for (int r = 0; r < TE; ++r)
+            if (r < NE) { sk[r * TB + tid] = qk[r]; si[r * TB + tid] = qv[r]; }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < TE; ++r) {
+          if (r < NE) {
+            const int i = r * TB + tid;
+            unsigned long long pk;
+            uint32_t pv;
+            if (j >= 32) {
+              pk = (i ^ j) < P2 ? sk[i ^ j] : ~0ull;
+              pv = (i ^ j) < P2 ? si[i ^ j] : ~0u;
+            } else {
+              pk = __shfl_xor_sync(FULL, qk[r], j);
+              pv = __shfl_xor_sync(FULL, qv[r], j);
+            }
+            const bool asc = (i & k) == 0;
+            const bool lower = (i & j) == 0;
+            const bool pgt = pk > qk[r] || (pk == qk[r] && pv > qv[r]);
+            const bool take = lower == asc ? !pgt : pgt;
+            if (take && i < P2) { qk[r] = pk; qv[r] = pv; }
+          }
+        }
+        if (j >= 32) __syncthreads();
       }
-      __syncthreads();
     }
+    // sorted keys decoded to coordinates in place of the keys
+    int2* sp = reinterpret_cast<int2*>(sk);
+#pragma unroll
+    for (int r = 0; r < TE; ++r) {
+      const int i = r * TB + tid;
+      if (r < NE && i < m) { sp[i] = make_int2(key_x(qk[r]), key_y(qk[r])); si[i] = qv[r]; }
+    }
+    __syncthreads();
   }
-  // the sorted keys decoded in place (each thread its own slots)
-  int2* sp = reinterpret_cast<int2*>(sk);
-  for (int i = tid; i < m; i += TB) {
-    const unsigned long long k = sk[i];
-    sp[i] = make_int2(key_x(k), key_y(k));
+  const int2* sp = reinterpret_cast<const int2*>(sk);
+  // first level: warp 0 the lower chains, warp 1 the upper chains, lane c chunk c
+  const int C = (m + TCH - 1) / TCH;
+  if (tid < 64) {
+    const int c = tid & 31, s = tid >> 5;
+    const int lo = min(c * C, m), len = min(C, m - lo);
+    s_cc[s][c] = len > 0 ? chain_walk(sp, len, [&](int t) { return lo + t; }, sc[s] + c * C, s == 0 ? 1 : -1) : 0;
   }
   __syncthreads();
-  // lower chain (thread 0) and upper chain (thread 32): pop while the turn
-  // is not strictly left (lower) / not strictly right (upper).  The chain is
-  // sequential, so its latency is what counts: the next point is loaded one
-  // step ahead, the top two stack entries stay in registers (1 top, 2 below
-  // it) and the stack keeps coordinates, one load per pop.
+  // second level: thread 0 the lower chain, thread 32 the upper chain, over
+  // the chunk chains in order
   if (tid == 0 || tid == 32) {
-    const int c = tid == 0 ? 0 : 1;
-    uint16_t* q = st[c];
-    int2* cq = reinterpret_cast<int2*>(stk[c]);
-    int n = 0;
-    int x1 = 0, y1 = 0, x2 = 0, y2 = 0;
-    int2 nxt = sp[0];
-    for (int p = 0; p < m; ++p) {
-      const int2 cur = nxt;
-      if (p + 1 < m) nxt = sp[p + 1];
-      if (n > 0 && cur.x == x1 && cur.y == y1) continue;  // equal points: the first (lowest index) stands
-      while (n >= 2) {
-        const long long cr2 = (long long)(x1 - x2) * (cur.y - y2) - (long long)(y1 - y2) * (cur.x - x2);
-        if (c == 0 ? cr2 > 0 : cr2 < 0) break;
-        --n;
-        x1 = x2; y1 = y2;
-        if (n >= 2) { const int2 t = cq[n - 2]; x2 = t.x; y2 = t.y; }
-      }
-      q[n] = (uint16_t)p;
-      cq[n] = cur;
-      ++n;
-      x2 = x1; y2 = y1;
-      x1 = cur.x; y1 = cur.y;
-    }
-    s_n[c] = n;
+    const int s = tid >> 5;
+    int total = 0;
+    for (int c = 0; c < TCH; ++c) total += s_cc[s][c];
+    int c = 0, k = 0;  // the walk's cursor: chunk c, entry k
+    s_n[s] = chain_walk(sp, total, [&](int) {
+      while (k == s_cc[s][c]) { ++c; k = 0; }
+      return (int)sc[s][c * C + k++];
+    }, sq[s], s == 0 ? 1 : -1);
   }
   __syncthreads();
   uint32_t* out = out_base + o;
   const int a = s_n[0], b = s_n[1];
   if (a == 1) {  // every survivor has the same coordinates
-    if (tid == 0) { out[0] = si[st[0][0]]; out_n_base[set] = 1; }
+    if (tid == 0) { out[0] = si[sq[0][0]]; out_n_base[set] = 1; }
     return;
   }
-  for (int k = tid; k < a - 1; k += TB) out[k] = si[st[0][k]];
-  for (int k = 1 + tid; k <= b - 1; k += TB) out[(a - 1) + (b - 1 - k)] = si[st[1][k]];
+  for (int k = tid; k < a - 1; k += TB) out[k] = si[sq[0][k]];
+  for (int k = 1 + tid; k <= b - 1; k += TB) out[(a - 1) + (b - 1 - k)] = si[sq[1][k]];
   if (tid == 0) out_n_base[set] = (int64_t)(a - 1) + (b - 1);
 }
 
@@ -525,7 +595,7 @@ __global__ void __launch_bounds__(CW * 32) k_small_classify(Sets S, const uint32
   WsHeader* h = S.h(set);
   if (*reinterpret_cast<const volatile uint32_t*>(gstatus)) return;
   const int64_t m64 = count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
-  if (m64 <= TINY_MAX || m64 > SMALL_MAX) return;
+  if (m64 == 0 || m64 > SMALL_MAX) return;
   const int m = (int)m64;
   const int64_t o = S.off_at(set);
   const unsigned long long* K = kin_base + o;
@@ -605,9 +675,13 @@ __global__ void __launch_bounds__(CW * 32) k_small_rank(Sets S, const uint32_t* 
                                                          int64_t* out_n_base) {
   const int set = blockIdx.x;
   const WsHeader* h = S.h(set);
-  if (*reinterpret_cast<const volatile uint32_t*>(gstatus)) return;
-  const int64_t m64 = count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
-  if (m64 <= TINY_MAX || m64 > SMALL_MAX) return;
+  const bool dead = *reinterpret_cast<const volatile uint32_t*>(gstatus) != 0;
+  const int64_t m64 = dead ? 0 : count_of(h, which == 0 ? &h->n_surv : &h->n_surv2);
+  if (m64 == 0) {  // nothing survives (or the call is dead): an empty hull
+    if (blockIdx.y == 0 && threadIdx.x == 0) out_n_base[set] = 0;
+    return;
+  }
+  if (m64 > SMALL_MAX) return;
   const int m = (int)m64;
   const int64_t o = S.off_at(set);
   const unsigned long long* K = kin_base + o;
@@ -653,14 +727,14 @@ size_t small_hull_smem() {
 cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which, const unsigned long long* keys,
                               const uint32_t* vals, SmallWs* sw, uint32_t* out, int64_t* out_n, cudaStream_t st) {
   const unsigned nsets = (unsigned)S.S;
-  k_small_tiny<<<nsets, TB, 0, st>>>(S, gstatus, which, keys, vals, out, out_n);
   if (S.S == 1) {  // the whole GPU on one set: a warp for every possible survivor
     const unsigned gy = (unsigned)(SMALL_MAX / CW);
     k_small_classify<<<dim3(1, gy), CW * 32, 0, st>>>(S, gstatus, which, keys, vals, sw);
     k_small_rank<<<dim3(1, gy), CW * 32, 0, st>>>(S, gstatus, which, keys, vals, sw, out, out_n);
-    count_launches(3);
+    count_launches(2);
     return cudaGetLastError();
   }
+  k_small_tiny<<<nsets, TB, 0, st>>>(S, gstatus, which, keys, vals, out, out_n);
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);

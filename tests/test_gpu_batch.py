@@ -79,6 +79,47 @@ def test_batch_many_small_sets(gpu_lib):
     check(gpu_lib, sets, offsets, xy, gpu_lib.Options())
 
 
+def degenerate_sets():
+    """Sets whose survivors reach the one-block hull of a batch with
+    duplicates, collinear runs, equal coordinates across its chunks, and
+    convex position up to and past its capacity (1024 points)."""
+    rng = np.random.default_rng(9350)
+    t = np.arange(-300, 300, dtype=np.float32)
+    line = np.stack([t, 2 * t], 1)[rng.permutation(600)]
+    vline = np.stack([np.full(500, -9.0), np.repeat(np.arange(100), 5)], 1)[rng.permutation(500)]
+    g = np.arange(-3, 4, dtype=np.float32)
+    lattice = np.tile(np.stack(np.meshgrid(g, g), -1).reshape(-1, 2), (5, 1))[rng.permutation(245)]
+    pair = np.tile(np.array([[0, 0], [5, 5]], np.float32), (20, 1))
+    same = np.full((50, 2), 7, np.float32)
+    negz = np.array([[-0.0, 3], [0.0, 3], [0.0, -3], [-0.0, -3], [4, 0], [-4, 0], [0, 0]], np.float32)
+    rings = [convex_ring(k)[rng.permutation(k)] for k in (31, 32, 33, 1000, 1024, 1025)]
+    # convex ring with every point repeated: equal coordinates in adjacent chunks
+    rep = np.repeat(convex_ring(400), 2, axis=0)
+    sq = synth.square(900, 9351, 1 << 10)  # dense lattice: many equal points
+    return [line, vline, lattice, pair, same, negz, rep, sq] + rings
+
+
+@pytest.mark.parametrize("refine", [True, False])
+def test_batch_degenerate_sets(gpu_lib, refine):
+    extra = [np.ascontiguousarray(a, dtype=np.float32) for a in degenerate_sets()]
+    sets, offsets, xy = make_batch([], 0, extra=extra)
+    check(gpu_lib, sets, offsets, xy, gpu_lib.Options(refine=refine))
+    check(gpu_lib, sets, offsets, xy, gpu_lib.Options(refine=refine, filter=gpu_lib.HULL_FILTER_EXACT))
+
+
+@pytest.mark.parametrize("refine", [True, False])
+def test_single_degenerate_sets(gpu_lib, refine):
+    # the same sets one at a time: the whole-GPU hull of a single set
+    import torch
+    cp = gpu_lib
+    for k, pts in enumerate(degenerate_sets()):
+        pts = np.ascontiguousarray(pts, dtype=np.float32)
+        h, c, _ = cp.compute(torch.from_numpy(pts).cuda(), cp.Options(refine=refine))
+        torch.cuda.synchronize()
+        want = oracle.cudapre(pts)["hull"]
+        assert cp.as_index(h, int(c.item())).tolist() == want.tolist(), f"set {k}"
+
+
 def test_batch_plan_sample(gpu_lib):
     # the batch workload's own generator (log-uniform sizes, shape per set),
     # on 48 sets with sizes from 1e3 to 2e5
