@@ -124,23 +124,20 @@ __device__ void build_edges_and_box(Poly* P, int m, int lane, bool grid_on) {
     e.dy = (int32_t)dy;
     P->e[lane] = e;
   }
-  // Inner box: axis-aligned, around the vertex mean with the aspect of the
-  // bounding box, grown until a corner meets an edge (float estimate),
+  // Inner box: axis-aligned, around the centre of the bounding box with its
+  // aspect (the vertex mean lies off-centre when the extremes crowd on one
+  // side), grown until a corner meets an edge (float estimate),
   // rounded inward to integers and verified exactly (lane k checks edge k):
   // its 4 corners strictly inside make every point of the closed box
   // strictly inside.
   float box[4] = {1.0f, 0.0f, 1.0f, 0.0f};  // empty
   if (m >= 3) {
-    float cx = 0, cy = 0;
     int xl = P->vx[0], xh = P->vx[0], yl = P->vy[0], yh = P->vy[0];
     for (int k = 0; k < m; ++k) {
-      cx += (float)P->vx[k];
-      cy += (float)P->vy[k];
       xl = min(xl, P->vx[k]); xh = max(xh, P->vx[k]);
       yl = min(yl, P->vy[k]); yh = max(yh, P->vy[k]);
     }
-    cx /= (float)m;
-    cy /= (float)m;
+    const float cx = (float)(0.5 * ((double)xl + (double)xh)), cy = (float)(0.5 * ((double)yl + (double)yh));
     const float wx = 0.5f * ((float)xh - (float)xl), wy = 0.5f * ((float)yh - (float)yl);
     float t = 1.0f;
     if (lane < m) {

@@ -9,7 +9,11 @@
 // for the reserving variant of hull_compute on large sets).
 //
 // FP32 mode.  A point inside the polygon's inscribed circle (float32 test with
-// a proven margin) is discarded at once.  Every other point goes, with its
+// a proven margin) or inside the inner box around the circle's centre (a
+// box verified in int64; the float32 compares below are exact) is discarded
+// at once.  One set takes whichever of the two holds more lattice points
+// (the streaming loop is compiled for each, and a launch runs one); a batch
+// takes their union in one loop for all of its sets.  Every other point goes, with its
 // coordinates, to a per-warp queue; 32 queued points at a time take the full
 // test.  Its cell of a GRID x GRID grid over the polygon's bounding box is
 // found with two directed-rounding operations per coordinate; the cell's code
@@ -267,6 +271,9 @@ struct WarpOut {
 // test: cell lookup, then the float32 edge test(s) with exact escalation.
 // No point is read from memory twice.
 
+// The quick discard of the streaming loop.
+constexpr int QUICK_CIRCLE = 0, QUICK_BOX = 1, QUICK_UNION = 2;
+
 // Blocks per SM the inside test is compiled for, and its ring's stages.
 constexpr int FLT_MIN_BLOCKS = 3;
 constexpr int64_t FLT_MIN_CHUNKS = 4;  // least chunks per block of an inside test
@@ -333,6 +340,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
   __shared__ uint32_t s_qi[CONSUMERS / 32][QCAP];
   __shared__ __align__(16) unsigned long long s_okey[CONSUMERS / 32][KEYS ? WROW_KEY : 2];
   __shared__ __align__(16) uint32_t s_oidx[CONSUMERS / 32][WROW_IDX];
+  __shared__ float s_box[4];
   __shared__ int s_pm[5];
   __shared__ float s_circ[3];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -343,18 +351,20 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
   // claimed them first to last, so the chunks it streamed last are still in
   // L2).  A batch: static shares of the virtual pair axis, blocks and chunks
   // last-to-first for the same reason.
-  const bool dyn = S.S == 1;
+  const bool dyn = RES || S.S == 1;  // the reserving mode serves one set only
   const int64_t P = S.pp_at(S.S);
   const int64_t v0 = (int64_t)(gridDim.x - 1 - blockIdx.x) * ppb;
   const int64_t v1 = dead ? v0 : min(v0 + ppb, P);
   if (warp == PRODUCER_WARP) {
-    if (dyn)
+    if (dyn) {
       stream_produce_dynamic(SM, reinterpret_cast<const float4*>(S.xy_of(0) + 2 * S.head_of(0)), S.npairs_of(0),
                              &S.h(0)->next_group[1], true, gstatus);
-    else if (units)
-      stream_produce_units(SM, S, Split{CHUNK, 0, ppb, (int64_t)gridDim.x}, units, true, gstatus);
-    else
-      stream_produce_sets(SM, S, v0, v1, true, gstatus);
+    } else if constexpr (!RES) {
+      if (units)
+        stream_produce_units(SM, S, Split{CHUNK, 0, ppb, (int64_t)gridDim.x}, units, true, gstatus);
+      else
+        stream_produce_sets(SM, S, v0, v1, true, gstatus);
+    }
     return;
   }
   WarpOut<KEYS, RES> O;
@@ -367,7 +377,9 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
   unsigned esc = 0;
   bool all_survive = true;
   Cells C;
-  float ccx = 0.0f, ccy = 0.0f, cr2 = -1.0f;
+  // the quick discard of the set: the circle of centre (ccx, ccy) and
+  // squared radius cr2, and the box |x - ccx| <= hx, |y - ccy| <= hy
+  float ccx = 0.0f, ccy = 0.0f, cr2 = -1.0f, hx = -1.0f, hy = -1.0f;
   uint32_t ibase = 0;
   WsHeader* h = nullptr;
   // Full test of the `count` (<= 32) most recently queued points, one per lane.
@@ -402,6 +414,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
     if (tid == 0) {
       s_pm[0] = h->poly.m; s_pm[1] = h->poly.gx0; s_pm[2] = h->poly.gy0; s_pm[3] = h->poly.kx; s_pm[4] = h->poly.ky;
       s_circ[0] = h->poly.ccx; s_circ[1] = h->poly.ccy; s_circ[2] = h->poly.cr2;
+      for (int k = 0; k < 4; ++k) s_box[k] = h->poly.box[k];
     }
     consumers_sync();
     all_survive = s_pm[0] < 3;
@@ -415,14 +428,28 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
     ccx = s_circ[0];
     ccy = s_circ[1];
     cr2 = all_survive ? -1.0f : s_circ[2];
+    // Half-widths of the part of the inner box [x0, x1] x [y0, y1] centred on
+    // (ccx, ccy), in integers, at most 2^24 - 1: then for lattice points
+    // fl(|x - ccx|) <= hx implies the exact |x - ccx| <= hx (a difference
+    // that rounds is above 2^24), so x0 <= x <= x1.  Negative when there is
+    // no box or the centre lies outside it.
+    auto half = [](float c, float lo, float hi) {
+      const long long w = min((long long)c - (long long)lo, (long long)hi - (long long)c);
+      return (float)min(w, (long long)COORD_MAX - 1);
+    };
+    const bool box_ok = !all_survive && s_box[0] <= s_box[1] && s_box[2] <= s_box[3];
+    hx = box_ok ? half(ccx, s_box[0], s_box[1]) : -1.0f;
+    hy = box_ok ? half(ccy, s_box[2], s_box[3]) : -1.0f;
     O.h = h;
     O.g_idx = surv_idx + S.off_at(set);
     O.g_key = KEYS ? surv_key + S.off_at(set) : nullptr;
     esc = 0;
     ibase = (uint32_t)(S.head_of(set) + 2 * lo) + 2u * (uint32_t)tid;
   };
-  // one chunk in stage st: cnt pairs from pair f of the segment
-  auto chunk = [&](int st, int f, int cnt) {
+  // one chunk in stage st: cnt pairs from pair f of the segment, with the
+  // quick discard QUICK (QUICK_CIRCLE, QUICK_BOX or QUICK_UNION)
+  auto chunk_q = [&](auto QUICK, int st, int f, int cnt) {
+    constexpr int Q = decltype(QUICK)::value;
     const float4* sp = SM.stage[st];
     float4 v[4];
 #pragma unroll
@@ -437,7 +464,11 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
       for (int j = j0; j < j0 + FLT_DRAIN_POINTS; ++j) {
         const float x = (j & 1) ? v[j >> 1].z : v[j >> 1].x, y = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
         const float dx = x - ccx, dy = y - ccy;
-        const bool need = (j >> 1) * CONSUMERS < lim && !(fmaf(dx, dx, dy * dy) < cr2);
+        bool in;
+        if constexpr (Q == QUICK_CIRCLE) in = fmaf(dx, dx, dy * dy) < cr2;
+        else if constexpr (Q == QUICK_BOX) in = (fabsf(dx) <= hx) & (fabsf(dy) <= hy);
+        else in = (fmaf(dx, dx, dy * dy) < cr2) | ((fabsf(dx) <= hx) & (fabsf(dy) <= hy));
+        const bool need = (j >> 1) * CONSUMERS < lim && !in;
         const unsigned bal = __ballot_sync(FULL, need);
         const int slot = qn + __popc(bal & lt);
         if (need) {
@@ -458,43 +489,54 @@ __global__ void __launch_bounds__(STREAM_THREADS, FLT_MIN_BLOCKS) k_filter32(Set
     for (int off = 16; off; off >>= 1) esc += __shfl_xor_sync(FULL, esc, off);
     if (lane == 0 && esc) atomicAdd(&h->n_escalated, (unsigned long long)esc);
   };
+  using Union = std::integral_constant<int, QUICK_UNION>;
+  auto chunk = [&](int st, int f, int cnt) { chunk_q(Union{}, st, f, cnt); };
   if (dyn) {
     const int64_t np = S.npairs_of(0);
     begin_set(0, 0);
-    for (int c = 0;; ++c) {
-      const int id = stream_next_chunk(SM, c, gstatus);
-      if (id < 0) break;
-      const int f = id * CHUNK;
-      chunk(c % FilterStream::STAGES, f, (int)min((int64_t)CHUNK, np - f));
-    }
+    auto run = [&](auto QUICK) {
+      for (int c = 0;; ++c) {
+        const int id = stream_next_chunk(SM, c, gstatus);
+        if (id < 0) break;
+        const int f = id * CHUNK;
+        chunk_q(QUICK, c % FilterStream::STAGES, f, (int)min((int64_t)CHUNK, np - f));
+      }
+    };
+    // the box's lattice points against the circle's (about pi r^2)
+    if (hx >= 0.0f && hy >= 0.0f && (2.0f * hx + 1.0f) * (2.0f * hy + 1.0f) > 3.14159f * cr2)
+      run(std::integral_constant<int, QUICK_BOX>{});
+    else
+      run(std::integral_constant<int, QUICK_CIRCLE>{});
     end_set();
     O.drain_copies();
     return;
   }
-  if (units) {
-    for (int c = 0;; ++c) {
-      const ChunkMeta M = stream_next_meta(SM, c, gstatus);
-      if (M.flags & META_END) break;
-      if (M.flags & META_FIRST) begin_set(M.set, 0);
-      chunk(c % FilterStream::STAGES, M.first, M.cnt);
-      if (M.flags & META_LAST) end_set();
+  if constexpr (!RES) {
+    if (units) {
+      for (int c = 0;; ++c) {
+        const ChunkMeta M = stream_next_meta(SM, c, gstatus);
+        if (M.flags & META_END) break;
+        if (M.flags & META_FIRST) begin_set(M.set, 0);
+        chunk(c % FilterStream::STAGES, M.first, M.cnt);
+        if (M.flags & META_LAST) end_set();
+      }
+      return;
     }
-    return;
+    int c = 0;
+    bool stop = false;
+    walk_segments(S, v0, v1, true, [&](int set, int64_t lo, int n) {
+      begin_set(set, lo);
+      const int nck = nchunks(n);
+      for (int k = 0; k < nck; ++k, ++c) {
+        const int st = c % FilterStream::STAGES;
+        if (!stop && !mbar_wait_status(&SM.full[st], (unsigned)((c / FilterStream::STAGES) & 1), gstatus)) stop = true;
+        if (stop) continue;
+        const int f = chunk_first(k, nck, true);
+        chunk(st, f, min(CHUNK, n - f));
+      }
+      end_set();
+    });
   }
-  int c = 0;
-  bool stop = false;
-  walk_segments(S, v0, v1, true, [&](int set, int64_t lo, int n) {
-    begin_set(set, lo);
-    const int nck = nchunks(n);
-    for (int k = 0; k < nck; ++k, ++c) {
-      const int st = c % FilterStream::STAGES;
-      if (!stop && !mbar_wait_status(&SM.full[st], (unsigned)((c / FilterStream::STAGES) & 1), gstatus)) stop = true;
-      if (stop) continue;
-      const int f = chunk_first(k, nck, true);
-      chunk(st, f, min(CHUNK, n - f));
-    }
-    end_set();
-  });
 }
 
 // ----------------------------------------------------------------------------
