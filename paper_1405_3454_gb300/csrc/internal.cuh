@@ -300,7 +300,7 @@ cudaError_t launch_small_hull(const Sets& S, const uint32_t* gstatus, int which,
 // Sizes used by the sort and chain stages.
 constexpr int SORT_TILE = 4096;           // elements per sort tile
 constexpr int SORT_PASSES = 7;            // 8-bit digits over the 52-bit key
-constexpr int CHAIN_C0 = 1024;            // sorted elements per level-0 chunk
+constexpr int CHAIN_C0 = 512;             // sorted elements per level-0 chunk (one warp each)
 constexpr int CHAIN_FAN = 32;             // chunks merged per later-level group
 
 __host__ __device__ inline int64_t sort_tiles(int64_t cap) { return (cap + SORT_TILE - 1) / SORT_TILE; }

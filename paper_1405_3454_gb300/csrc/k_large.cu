@@ -12,7 +12,10 @@
 // level concatenates CHAIN_FAN consecutive chunk chains (still sorted) and
 // chains them again, until one chunk is left.  A hull vertex of the whole
 // set is a vertex of every chunk chain that contains it, so the last chain
-// is the hull.  Among equal keys the lowest index is kept.
+// is the hull.  Among equal keys the lowest index is kept.  Each chunk (or
+// group of chunk chains) is one warp's: it reads its input coalesced into
+// shared memory, its lanes chain short runs of it in parallel, and lane 0
+// walks only the vertices of those runs' chains (see window_chain).
 //
 // Every size is read on the device.  A job whose count is at most SMALL_MAX
 // (the one-block path has written its result) or whose status word is set
@@ -69,89 +72,6 @@ __device__ __forceinline__ long long cross_k(unsigned long long o, unsigned long
   return (long long)(key_x(a) - ox) * (key_y(b) - oy) - (long long)(key_y(a) - oy) * (key_x(b) - ox);
 }
 
-// One monotone chain as a stack of n entries in three tiers: the top WIN
-// entries in registers (wk[0] = top); below them the bottom SD entries of
-// the stack in the thread's column of shared memory; entries from SD up in
-// K[base ..], V likewise.  An entry moves down a tier only when it leaves
-// the register window and comes back when a pop brings it in again, so the
-// stacks of ordinary chunks (a few dozen entries deep at most) never wait
-// for global memory.  finish() leaves the chain in K[base .. base + n).
-// UPPER = false: lower chain (pop while the turn is not strictly left);
-// UPPER = true: upper chain walked left to right (pop while not strictly right).
-constexpr int WIN = 4;
-constexpr int SD = 12;  // shared-memory entries per stack
-// Elements a chain loads together before pushing them.
-constexpr int CB = 8;
-
-// Shared memory of the chain phases (the same dynamic buffer as the sort's):
-// per thread, CB staged input elements and two stacks' shared tiers, each
-// element i of thread t at i * LBLOCK + t (a warp's accesses fall in
-// distinct banks).
-struct ChainSmem {
-  unsigned long long keys[CB * LBLOCK];
-  uint32_t vals[CB * LBLOCK];
-  unsigned long long tk[2][SD * LBLOCK];
-  uint32_t tv[2][SD * LBLOCK];
-};
-
-template <bool UPPER>
-struct Stack {
-  unsigned long long* K;
-  uint32_t* V;
-  unsigned long long* TK;  // this stack's shared tier, thread column
-  uint32_t* TV;
-  int64_t base;
-  int64_t n;
-  unsigned long long wk[WIN];
-  uint32_t wv[WIN];
-
-  __device__ __forceinline__ void init(unsigned long long* k, uint32_t* v, int64_t b, ChainSmem& C, int which) {
-    K = k; V = v; base = b; n = 0;
-    TK = C.tk[which] + threadIdx.x;
-    TV = C.tv[which] + threadIdx.x;
-#pragma unroll
-    for (int i = 0; i < WIN; ++i) { wk[i] = 0; wv[i] = 0; }
-  }
-  __device__ __forceinline__ void put(int64_t e, unsigned long long k, uint32_t v) {
-    if (e < SD) { TK[e * LBLOCK] = k; TV[e * LBLOCK] = v; }
-    else { K[base + e] = k; V[base + e] = v; }
-  }
-  __device__ __forceinline__ void pop() {
-#pragma unroll
-    for (int i = 0; i < WIN - 1; ++i) { wk[i] = wk[i + 1]; wv[i] = wv[i + 1]; }
-    --n;
-    if (n >= WIN) {
-      const int64_t e = n - WIN;
-      if (e < SD) { wk[WIN - 1] = TK[e * LBLOCK]; wv[WIN - 1] = TV[e * LBLOCK]; }
-      else { wk[WIN - 1] = K[base + e]; wv[WIN - 1] = V[base + e]; }
-    }
-  }
-  __device__ __forceinline__ void push(unsigned long long key, uint32_t idx) {
-    if (n >= 1 && key == wk[0]) {  // equal coordinates: keep the lowest index
-      if (idx < wv[0]) wv[0] = idx;
-      return;
-    }
-    while (n >= 2) {
-      const long long c = cross_k(wk[1], wk[0], key);
-      if (UPPER ? (c < 0) : (c > 0)) break;
-      pop();
-    }
-    if (n >= WIN) put(n - WIN, wk[WIN - 1], wv[WIN - 1]);
-#pragma unroll
-    for (int i = WIN - 1; i > 0; --i) { wk[i] = wk[i - 1]; wv[i] = wv[i - 1]; }
-    wk[0] = key;
-    wv[0] = idx;
-    ++n;
-  }
-  __device__ __forceinline__ void finish() {
-#pragma unroll
-    for (int i = 0; i < WIN; ++i)
-      if (i < n) { K[base + n - 1 - i] = wk[i]; V[base + n - 1 - i] = wv[i]; }
-    const int64_t low = min(n - WIN, (int64_t)SD);  // shared-tier entries
-    for (int64_t e = 0; e < low; ++e) { K[base + e] = TK[e * LBLOCK]; V[base + e] = TV[e * LBLOCK]; }
-  }
-};
-
 // ----------------------------------------------------------------------------
 // One-sweep LSD radix sort.  Every pass reads each (key, index) once and
 // writes it once.  A block claims tiles of SORT_TILE elements in order from
@@ -195,6 +115,16 @@ struct SortSmem {
   uint32_t tile;
 };
 
+// The launch's dynamic shared memory, named inside each phase function: the
+// phases are out of line, and a struct passed by reference would reach them
+// as a generic pointer (generic accesses, and global loads kept in order
+// with the shared-memory stores they might alias).
+template <class T>
+__device__ __forceinline__ T& dyn_smem() {
+  extern __shared__ __align__(16) unsigned char k_large_smem[];
+  return *reinterpret_cast<T*>(k_large_smem);
+}
+
 // Passes whose digit varies among the keys, as a bit mask (bit p: pass p).
 __device__ __forceinline__ unsigned live_passes(const WsHeader* h) {
   const unsigned long long v = h->key_or & h->key_nor;
@@ -207,8 +137,9 @@ __device__ __forceinline__ unsigned live_passes(const WsHeader* h) {
 // One read of the keys: the digit histogram of pass `pass` (when or_too,
 // also the OR of the keys and of their complements, and the job's tile
 // status words cleared).
-__device__ __noinline__ void hist_read(SortSmem& S, const unsigned long long* keys, int64_t m, int pass, WsHeader* h,
+__device__ __noinline__ void hist_read(const unsigned long long* keys, int64_t m, int pass, WsHeader* h,
                                        bool or_too, unsigned long long* status, int64_t nstatus) {
+  SortSmem& S = dyn_smem<SortSmem>();
   // HCOPIES sub-histograms (warp w counts into copy w % HCOPIES) in the key
   // area, to spread the shared-memory atomics
   constexpr int HCOPIES = 4;
@@ -267,10 +198,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(SortSmem& S, uint32_t v) {
 // when a look-back wait gave up (nothing more is written).
 // pnext: the next pass that will run (-1: none), whose histogram is
 // counted on the way.
-__device__ __noinline__ bool sort_pass(SortSmem& S, const unsigned long long* kin, const uint32_t* vin,
+__device__ __noinline__ bool sort_pass(const unsigned long long* kin, const uint32_t* vin,
                                        unsigned long long* kout, uint32_t* vout, int64_t m, int pass, int pnext,
                                        uint32_t* hist, uint32_t* tile_next, unsigned long long* status,
                                        uint32_t* gstatus) {
+  SortSmem& S = dyn_smem<SortSmem>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, d0 = threadIdx.x;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
@@ -396,114 +328,324 @@ __device__ __noinline__ bool sort_pass(SortSmem& S, const unsigned long long* ki
   return ok;
 }
 
-// The chains read their input CB elements at a time into a per-thread
-// staging area in shared memory: one memory round trip per CB elements, and
-// the pushes read shared memory only.
-__device__ __forceinline__ void stage_in(ChainSmem& S, const unsigned long long* K, const uint32_t* V, int64_t at,
-                                         int nb) {
-#pragma unroll
-  for (int i = 0; i < CB; ++i)
-    if (i < nb) {
-      S.keys[i * LBLOCK + threadIdx.x] = K[at + i];
-      S.vals[i * LBLOCK + threadIdx.x] = V[at + i];
-    }
+// ----------------------------------------------------------------------------
+// The chains, one warp per chunk (level 0) or per group of chunk chains.
+//
+// A window of at most CHAIN_C0 + 2 entries (sorted keys with their indices)
+// is chained in two levels: lane l chains entries [l S, (l + 1) S) of it
+// (S = max(ceil(entries / 32), RUN_MIN)) on a small stack of window entries,
+// then lane 0 pushes the vertices of those run chains, in order, onto the
+// chunk's running stack.  An entry off its run's chain lies on or above
+// (lower chain; below for the upper one) the chain of a subset holding it,
+// so it is no strict vertex of any larger set's chain either; the first and
+// the last entry of every run stay.  The running stack keeps its last RING
+// entries in shared memory (slot e % RING, tagged with e); an entry leaving
+// the ring while it is still on the stack is written to its final place in
+// global memory (entry e at base + e), and finish() writes the rest, so only
+// deep stacks touch global memory before the end.
+constexpr int RUNS = 32;                                   // runs per window (one per lane)
+constexpr int RUN_MIN = 8;                                 // entries of a run at least
+constexpr int RUN_MAX = (CHAIN_C0 + 2 + RUNS - 1) / RUNS;  // entries of a run at most
+static_assert(RUN_MIN <= RUN_MAX, "run sizes");
+constexpr int RING = 128;
+static_assert((RING & (RING - 1)) == 0, "ring slots by mask");
+
+struct WarpChain {
+  unsigned long long k[CHAIN_C0];  // the chunk's elements (level 0) or the window (later levels)
+  unsigned long long rk[RING];     // ring of the running stack's last entries
+  int64_t rpos[RING];              // ... the entry each slot holds
+  uint32_t v[CHAIN_C0];
+  uint32_t rv[RING];
+  int runn[RUNS];
+  uint16_t pos[CHAIN_C0 + 2];      // level 0: the window's entries, as positions in k / v
+  uint16_t run[RUNS * RUN_MAX];    // run chains (window entries), run l's from l * S
+};
+struct ChainSmem {
+  WarpChain w[WARPS];
+};
+
+// Is key b, after o and a, a strict turn the right way (left for the lower
+// chain, right for the upper one)?
+template <bool UPPER>
+__device__ __forceinline__ bool turns(unsigned long long o, unsigned long long a, unsigned long long b) {
+  const long long c = cross_k(o, a, b);
+  return UPPER ? c < 0 : c > 0;
 }
 
-// Level 0: virtual thread g chains sorted elements [g*C0, min((g+1)*C0, m));
-// the lower chain in place in (Ks, Vs), the upper chain into (Ku, Vu) at the
-// same offsets; counts to cnt_lo[g], cnt_up[g].  Only the lowest point of an
-// x column can be a lower-chain vertex and only its highest an upper-chain
-// vertex (every other point of the column lies between them on a vertical
-// segment), so each column sends its first key (and copies of it) to the
-// lower chain and its last key (lowest index among copies) to the upper one.
-// The whole hull's lower chain must still end, and its upper chain start, at
-// the lexicographic maximum resp. minimum (the emission joins them there), so
-// every chunk also gives its last key to the lower chain and its first point
-// to the upper one.
-__device__ __noinline__ void chain0(ChainSmem& S, unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku,
-                                    uint32_t* Vu, int64_t m, uint32_t* cnt_lo, uint32_t* cnt_up) {
-  const int64_t nch = (m + CHAIN_C0 - 1) / CHAIN_C0;
-  for (int64_t g = (int64_t)blockIdx.x * LBLOCK + threadIdx.x; g < nch; g += (int64_t)gridDim.x * LBLOCK) {
-    const int64_t start = g * CHAIN_C0;
-    const int64_t end = min(start + (int64_t)CHAIN_C0, m);
-    Stack<false> lo;
-    Stack<true> up;
-    lo.init(Ks, Vs, start, S, 0);
-    up.init(Ku, Vu, start, S, 1);
-    // the lower stack is written in place over consumed input; the staged
-    // batch is already in shared memory when its elements are pushed
-    int32_t px = 0;
-    unsigned long long first = 0, pk = 0;
-    uint32_t pv = 0;
-    bool any = false;
-    for (int64_t jb = start; jb < end; jb += CB) {
-      const int nb = (int)min((int64_t)CB, end - jb);
-      stage_in(S, Ks, Vs, jb, nb);
-      for (int i = 0; i < nb; ++i) {
-        const unsigned long long k = S.keys[i * LBLOCK + threadIdx.x];
-        const uint32_t v = S.vals[i * LBLOCK + threadIdx.x];
-        const int32_t x = key_x(k);
-        if (!any || x != px) {  // a new column: its lowest point, and the previous column's highest
-          if (any) up.push(pk, pv);
-          else up.push(k, v);  // the upper chain starts at the chunk's first point
-          lo.push(k, v);
-          first = k;
-          pk = k;
-          pv = v;
-          any = true;
-          px = x;
-        } else {
-          if (k == first) lo.push(k, v);  // a copy of the column's lowest point
-          if (k == pk) { if (v < pv) pv = v; } else { pk = k; pv = v; }
-        }
+// The running stack of one chunk: push by lane 0 only, init and finish
+// warp-wide.
+template <bool UPPER>
+struct RunStack {
+  unsigned long long* K;  // output: entry e at K[base + e], V[base + e]
+  uint32_t* V;
+  int64_t base;
+  int64_t n;                  // entries
+  unsigned long long k1, k2;  // top and second keys
+  uint32_t v1;                // top index
+
+  __device__ __forceinline__ void init(WarpChain& W, unsigned long long* k, uint32_t* v, int64_t b) {
+    K = k; V = v; base = b; n = 0; k1 = k2 = 0; v1 = 0;
+    // a tag no entry position (nor n - RING) can take
+    for (int i = threadIdx.x & 31; i < RING; i += 32) W.rpos[i] = INT64_MIN;
+    __syncwarp();
+  }
+  static __device__ __forceinline__ int slot(int64_t e) { return (int)((uint64_t)e & (RING - 1)); }
+  // entry e (< n): from its ring slot, else from global memory (it left the
+  // ring while on the stack, so it was written there)
+  __device__ __forceinline__ void entry(const WarpChain& W, int64_t e, unsigned long long& k, uint32_t& v) const {
+    const int q = slot(e);
+    if (W.rpos[q] == e) { k = W.rk[q]; v = W.rv[q]; }
+    else { k = K[base + e]; v = V[base + e]; }
+  }
+  __device__ __forceinline__ void push(WarpChain& W, unsigned long long key, uint32_t val) {
+    if (n > 0 && key == k1) {  // equal coordinates: the lowest index stands
+      if (val < v1) {
+        v1 = val;
+        const int q = slot(n - 1);
+        if (W.rpos[q] == n - 1) W.rv[q] = val;
+        else V[base + n - 1] = val;
+      }
+      return;
+    }
+    while (n >= 2 && !turns<UPPER>(k2, k1, key)) {
+      --n;
+      k1 = k2;
+      unsigned long long kk;
+      entry(W, n - 1, kk, v1);
+      if (n >= 2) { uint32_t vv; entry(W, n - 2, k2, vv); }
+    }
+    const int q = slot(n);
+    if (W.rpos[q] == n - RING) {  // a stack entry leaves the ring
+      K[base + n - RING] = W.rk[q];
+      V[base + n - RING] = W.rv[q];
+    }
+    W.rk[q] = key;
+    W.rv[q] = val;
+    W.rpos[q] = n;
+    ++n;
+    k2 = k1;
+    k1 = key;
+    v1 = val;
+  }
+  // warp-wide, after lane 0's last push: the entries still in the ring to
+  // global memory; returns n
+  __device__ __forceinline__ int64_t finish(WarpChain& W) {
+    const int64_t nn = __shfl_sync(FULL, n, 0);
+    for (int64_t e = max(nn - RING, (int64_t)0) + (threadIdx.x & 31); e < nn; e += 32) {
+      const int q = slot(e);
+      if (W.rpos[q] == e) { K[base + e] = W.rk[q]; V[base + e] = W.rv[q]; }
+    }
+    __syncwarp();
+    return nn;
+  }
+};
+
+// Lane-level chain of window entries [lo, lo + len) onto q (window entries);
+// returns its length.  IND: entry e is element W.pos[e].
+template <bool UPPER, bool IND>
+__device__ __forceinline__ int run_chain(const WarpChain& W, int lo, int len, uint16_t* q) {
+  auto at = [&](int e) { return IND ? (int)W.pos[e] : e; };
+  int n = 0;
+  unsigned long long k1 = 0, k2 = 0;
+  for (int t = 0; t < len; ++t) {
+    const int e = lo + t;
+    const unsigned long long key = W.k[at(e)];
+    if (n > 0 && key == k1) {  // equal coordinates: keep the lower index
+      if (W.v[at(e)] < W.v[at(q[n - 1])]) q[n - 1] = (uint16_t)e;
+      continue;
+    }
+    while (n >= 2 && !turns<UPPER>(k2, k1, key)) {
+      --n;
+      k1 = k2;
+      if (n >= 2) k2 = W.k[at(q[n - 2])];
+    }
+    q[n++] = (uint16_t)e;
+    k2 = k1;
+    k1 = key;
+  }
+  return n;
+}
+
+// One window of `len` (<= CHAIN_C0 + 2) entries, warp-wide, onto the running
+// stack R (lane 0's).
+template <bool UPPER, bool IND>
+__device__ __forceinline__ void window_chain(WarpChain& W, int len, RunStack<UPPER>& R) {
+  const int lane = threadIdx.x & 31;
+  const int S = max((len + RUNS - 1) / RUNS, RUN_MIN);
+  const int lo = min(lane * S, len), n = max(min(S, len - lo), 0);
+  W.runn[lane] = n > 0 ? run_chain<UPPER, IND>(W, lo, n, W.run + lane * S) : 0;
+  __syncwarp();
+  if (lane == 0) {
+    const int nr = (len + S - 1) / S;
+    for (int l = 0; l < nr; ++l) {
+      const int c = W.runn[l];
+      for (int i = 0; i < c; ++i) {
+        const int e = W.run[l * S + i];
+        const int p = IND ? (int)W.pos[e] : e;
+        R.push(W, W.k[p], W.v[p]);
       }
     }
-    if (any) {
-      up.push(pk, pv);
-      lo.push(pk, pv);  // the lower chain ends at the chunk's last point
+  }
+  __syncwarp();
+}
+
+// First position of the run of keys equal to W.k[e] (within the chunk);
+// after chain0's first step its slot holds the run's lowest index.
+__device__ __forceinline__ int run_start(const WarpChain& W, int e) {
+  while (e > 0 && W.k[e - 1] == W.k[e]) --e;
+  return e;
+}
+
+// Level 0: warp w chains sorted elements [t*C0, min((t+1)*C0, m)) for its
+// chunks t; the lower chain in place in (Ks, Vs), the upper chain into (Ku,
+// Vu) at the same offsets; counts to cnt_lo[t], cnt_up[t].  Only the lowest
+// point of an x column can be a lower-chain vertex and only its highest an
+// upper-chain vertex (every other point of the column lies between them on a
+// vertical segment), so the lower chain takes the first point of every
+// column of the chunk and the upper chain the last key of every column
+// (with the lowest index among its copies).  The whole hull's lower chain
+// must still end, and its upper chain start, at the lexicographic maximum
+// resp. minimum (the emission joins them there), so every chunk also gives
+// its last key to the lower chain and its first point to the upper one.
+__device__ __noinline__ void chain0(unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku,
+                                    uint32_t* Vu, int64_t m, uint32_t* cnt_lo, uint32_t* cnt_up) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  WarpChain& W = dyn_smem<ChainSmem>().w[warp];
+  const int64_t nch = (m + CHAIN_C0 - 1) / CHAIN_C0;
+  for (int64_t t = (int64_t)blockIdx.x * WARPS + warp; t < nch; t += (int64_t)gridDim.x * WARPS) {
+    const int64_t tb = t * CHAIN_C0;
+    const int tn = (int)min((int64_t)CHAIN_C0, m - tb);
+    // the chunk in rows of 32, eight rows' loads in flight at a time
+    constexpr int R = 8;
+    for (int r0 = 0; r0 < CHAIN_C0 / 32; r0 += R) {
+      unsigned long long kk[R];
+      uint32_t vv[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = (r0 + r) * 32 + lane;
+        if (e < tn) { kk[r] = Ks[tb + e]; vv[r] = Vs[tb + e]; }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = (r0 + r) * 32 + lane;
+        if (e < tn) { W.k[e] = kk[r]; W.v[e] = vv[r]; }
+      }
     }
-    lo.finish();
-    up.finish();
-    cnt_lo[g] = (uint32_t)lo.n;
-    cnt_up[g] = (uint32_t)up.n;
+    __syncwarp();
+    // Equal keys are adjacent but their indices in no order (survivors come
+    // in compaction order): the first slot of every run of equal keys takes
+    // the run's lowest index, and the candidates below are run starts.
+    for (int e0 = 0; e0 < tn; e0 += 32) {
+      const int e = e0 + lane;
+      if (e < tn && e > 0 && W.k[e - 1] == W.k[e] && (e == tn - 1 || W.k[e + 1] != W.k[e])) {
+        int s = e;
+        uint32_t mv = W.v[e];
+        while (s > 0 && W.k[s - 1] == W.k[e]) {
+          --s;
+          mv = min(mv, W.v[s]);
+        }
+        W.v[s] = mv;
+      }
+    }
+    __syncwarp();
+    // lower chain: the first point of every column, then the chunk's last key
+    int L = 0;
+    for (int e0 = 0; e0 < tn; e0 += 32) {
+      const int e = e0 + lane;
+      const bool f = e < tn && (e == 0 || key_x(W.k[e - 1]) != key_x(W.k[e]));
+      const unsigned bal = __ballot_sync(FULL, f);
+      if (f) W.pos[L + __popc(bal & lt)] = (uint16_t)e;
+      L += __popc(bal);
+    }
+    if (lane == 0) W.pos[L] = (uint16_t)run_start(W, tn - 1);
+    ++L;
+    __syncwarp();
+    RunStack<false> rl;
+    rl.init(W, Ks, Vs, tb);
+    window_chain<false, true>(W, L, rl);
+    const int64_t nlo = rl.finish(W);
+    // upper chain: the chunk's first point, then the last key of every column
+    if (lane == 0) W.pos[0] = 0;
+    L = 1;
+    for (int e0 = 0; e0 < tn; e0 += 32) {
+      const int e = e0 + lane;
+      const bool f = e < tn && (e == tn - 1 || key_x(W.k[e + 1]) != key_x(W.k[e]));
+      const unsigned bal = __ballot_sync(FULL, f);
+      if (f) W.pos[L + __popc(bal & lt)] = (uint16_t)run_start(W, e);
+      L += __popc(bal);
+    }
+    __syncwarp();
+    RunStack<true> ru;
+    ru.init(W, Ku, Vu, tb);
+    window_chain<true, true>(W, L, ru);
+    const int64_t nup = ru.finish(W);
+    if (lane == 0) {
+      cnt_lo[t] = (uint32_t)nlo;
+      cnt_up[t] = (uint32_t)nup;
+    }
+    __syncwarp();
   }
 }
 
 // One group of a later level: the chains of chunks [c0, c1) of the previous
 // level (span `span` each, counts cin), concatenated in order (still sorted),
-// chained again in place from c0 * span.  Returns the new chain's length.
+// chained again in place from c0 * span by one warp, window by window.  An
+// unread entry j of the concatenation sits at or after c0 * span + j, and
+// the stack's entry e is written at c0 * span + e with e below the entries
+// read so far, so no write reaches input not yet read.  Returns the new
+// chain's length (lane 0).
 template <bool UPPER>
-__device__ __forceinline__ uint32_t merge_group(ChainSmem& S, unsigned long long* K, uint32_t* V, const uint32_t* cin,
+__device__ __forceinline__ uint32_t merge_group(WarpChain& W, unsigned long long* K, uint32_t* V, const uint32_t* cin,
                                                 int64_t c0, int64_t c1, int64_t span) {
-  Stack<UPPER> st;
-  st.init(K, V, c0 * span, S, 0);
-  for (int64_t c = c0; c < c1; ++c) {
-    const int64_t b = c * span, cnt = cin[c];
-    for (int64_t jb = 0; jb < cnt; jb += CB) {
-      const int nb = (int)min((int64_t)CB, cnt - jb);
-      stage_in(S, K, V, b + jb, nb);
-      for (int i = 0; i < nb; ++i) st.push(S.keys[i * LBLOCK + threadIdx.x], S.vals[i * LBLOCK + threadIdx.x]);
-    }
+  const int lane = threadIdx.x & 31;
+  const int nc = (int)(c1 - c0);  // at most CHAIN_FAN == 32
+  const int64_t cnt = lane < nc ? (int64_t)cin[c0 + lane] : 0;
+  int64_t incl = cnt;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int64_t u = __shfl_up_sync(FULL, incl, off);
+    if (lane >= off) incl += u;
   }
-  st.finish();
-  return (uint32_t)st.n;
+  const int64_t offc = incl - cnt, total = __shfl_sync(FULL, incl, 31);
+  RunStack<UPPER> R;
+  R.init(W, K, V, c0 * span);
+  for (int64_t w0 = 0; w0 < total; w0 += CHAIN_C0) {
+    const int len = (int)min((int64_t)CHAIN_C0, total - w0);
+    for (int c = 0; c < nc; ++c) {
+      const int64_t oc = __shfl_sync(FULL, offc, c), nn = __shfl_sync(FULL, cnt, c);
+      const int64_t a = max(oc, w0), b = min(oc + nn, w0 + len);
+      const int64_t src = (c0 + c) * span - oc;
+      for (int64_t j = a + lane; j < b; j += 32) {
+        W.k[j - w0] = K[src + j];
+        W.v[j - w0] = V[src + j];
+      }
+    }
+    __syncwarp();
+    window_chain<UPPER, false>(W, len, R);
+  }
+  return (uint32_t)R.finish(W);
 }
 
 // Later level: group g merges the chains of chunks [g*FAN, (g+1)*FAN) of the
-// previous level; virtual thread 2g does the lower chains, 2g+1 the upper
-// ones.
-__device__ __noinline__ void chainN(ChainSmem& S, unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku,
-                                    uint32_t* Vu, int64_t m, const uint32_t* cin_lo, const uint32_t* cin_up,
-                                    uint32_t* cout_lo, uint32_t* cout_up, int64_t nch_prev, int64_t span) {
+// previous level; warp task 2g does the lower chains, 2g+1 the upper ones.
+__device__ __noinline__ void chainN(unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku,
+                                    uint32_t* Vu, const uint32_t* cin_lo, const uint32_t* cin_up, uint32_t* cout_lo,
+                                    uint32_t* cout_up, int64_t nch_prev, int64_t span) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpChain& W = dyn_smem<ChainSmem>().w[warp];
   const int64_t ng = (nch_prev + CHAIN_FAN - 1) / CHAIN_FAN;
-  for (int64_t t = (int64_t)blockIdx.x * LBLOCK + threadIdx.x; t < 2 * ng; t += (int64_t)gridDim.x * LBLOCK) {
+  for (int64_t t = (int64_t)blockIdx.x * WARPS + warp; t < 2 * ng; t += (int64_t)gridDim.x * WARPS) {
     const int64_t g = t >> 1;
     const int64_t c0 = g * CHAIN_FAN;
     const int64_t c1 = min(c0 + (int64_t)CHAIN_FAN, nch_prev);
-    if (t & 1)
-      cout_up[g] = merge_group<true>(S, Ku, Vu, cin_up, c0, c1, span);
-    else
-      cout_lo[g] = merge_group<false>(S, Ks, Vs, cin_lo, c0, c1, span);
+    if (t & 1) {
+      const uint32_t n = merge_group<true>(W, Ku, Vu, cin_up, c0, c1, span);
+      if (lane == 0) cout_up[g] = n;
+    } else {
+      const uint32_t n = merge_group<false>(W, Ks, Vs, cin_lo, c0, c1, span);
+      if (lane == 0) cout_lo[g] = n;
+    }
+    __syncwarp();
   }
 }
 
@@ -529,9 +671,6 @@ __device__ __noinline__ void chain_emit(const uint32_t* Vs, const uint32_t* Vu, 
 
 __global__ void __launch_bounds__(LBLOCK, 2) k_large(const LargeJob* __restrict__ table, const int* njobs_dev,
                                                    LargeJob single, uint32_t* bar, uint32_t* bar_status) {
-  extern __shared__ __align__(16) unsigned char lsm[];
-  SortSmem& S = *reinterpret_cast<SortSmem*>(lsm);
-  ChainSmem& C = *reinterpret_cast<ChainSmem*>(lsm);
   const int njobs = table ? *reinterpret_cast<const volatile int*>(njobs_dev) : 1;
   for (int jb = 0; jb < njobs; ++jb) {
     const LargeJob J = table ? table[jb] : single;
@@ -539,12 +678,12 @@ __global__ void __launch_bounds__(LBLOCK, 2) k_large(const LargeJob* __restrict_
     const int64_t m = (int64_t)*reinterpret_cast<const volatile unsigned long long*>(J.count);
     if (m <= SMALL_MAX) continue;
     const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
-    hist_read(S, J.ka, m, 0, J.h, true, J.tilecnt, nt * 256);
+    hist_read(J.ka, m, 0, J.h, true, J.tilecnt, nt * 256);
     if (!grid_sync(bar, bar_status)) return;
     // the passes that move anything; the first one's histogram if not pass 0's
     const unsigned live = live_passes(J.h);
     if (live && !(live & 1u)) {
-      hist_read(S, J.ka, m, __ffs(live) - 1, J.h, false, nullptr, 0);
+      hist_read(J.ka, m, __ffs(live) - 1, J.h, false, nullptr, 0);
       if (!grid_sync(bar, bar_status)) return;
     }
     unsigned long long *kin = J.ka, *kout = J.kb;
@@ -553,7 +692,7 @@ __global__ void __launch_bounds__(LBLOCK, 2) k_large(const LargeJob* __restrict_
       if (!((live >> p) & 1u)) continue;
       const unsigned later = live & ~((2u << p) - 1u);
       const int pnext = later ? __ffs(later) - 1 : -1;
-      const bool ok = sort_pass(S, kin, vin, kout, vout, m, p, pnext, &J.h->hist[0][0], J.h->tile_next, J.tilecnt,
+      const bool ok = sort_pass(kin, vin, kout, vout, m, p, pnext, &J.h->hist[0][0], J.h->tile_next, J.tilecnt,
                                 bar_status);
       if (!grid_sync(bar, bar_status) || !ok) return;
       unsigned long long* tk = kin; kin = kout; kout = tk;
@@ -563,12 +702,12 @@ __global__ void __launch_bounds__(LBLOCK, 2) k_large(const LargeJob* __restrict_
     const int64_t nch0 = (std::max<int64_t>(J.cap, 1) + CHAIN_C0 - 1) / CHAIN_C0;
     uint32_t* lo[2] = {J.cnt, J.cnt + 2 * nch0};
     uint32_t* up[2] = {J.cnt + nch0, J.cnt + 3 * nch0};
-    chain0(C, kin, vin, kout, vout, m, lo[0], up[0]);
+    chain0(kin, vin, kout, vout, m, lo[0], up[0]);
     if (!grid_sync(bar, bar_status)) return;
     int64_t nch = (m + CHAIN_C0 - 1) / CHAIN_C0, span = CHAIN_C0;
     int par = 0;
     while (nch > 1) {
-      chainN(C, kin, vin, kout, vout, m, lo[par], up[par], lo[par ^ 1], up[par ^ 1], nch, span);
+      chainN(kin, vin, kout, vout, lo[par], up[par], lo[par ^ 1], up[par ^ 1], nch, span);
       if (!grid_sync(bar, bar_status)) return;
       par ^= 1;
       nch = (nch + CHAIN_FAN - 1) / CHAIN_FAN;
