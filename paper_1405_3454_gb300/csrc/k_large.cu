@@ -87,9 +87,9 @@ __device__ __forceinline__ long long cross_k(unsigned long long o, unsigned long
 // addresses.  Status words carry the pass number, so one clearing per job
 // serves every pass.  A pass whose digit is the same for every key moves
 // nothing and is skipped: a bit varies among the keys iff both the OR of the
-// keys and the OR of their complements have it.  The digit histogram a pass
-// needs is counted while the pass before it writes its output (the first
-// one by a read of the keys, with the two ORs).
+// keys and the OR of their complements have it.  The digit histograms of
+// all passes are counted in one read of the keys before the first pass,
+// with the two ORs.
 
 constexpr unsigned long long ST_AGG = 1ull << 62;     // the word holds the tile's own count
 constexpr unsigned long long ST_PREFIX = 2ull << 62;  // ... the inclusive prefix through the tile
@@ -110,7 +110,6 @@ struct SortSmem {
   uint32_t lstart[256];        // first position of each digit in the reordered tile
   long long delta[256];        // output position - position in the reordered tile, per digit
   uint32_t excl[256];          // elements of all keys with a smaller digit (this pass)
-  uint32_t hn[256];            // histogram of the next pass's digit, this block's part
   uint32_t wsum[WARPS];
   uint32_t tile;
 };
@@ -134,18 +133,20 @@ __device__ __forceinline__ unsigned live_passes(const WsHeader* h) {
   return mask;
 }
 
-// One read of the keys: the digit histogram of pass `pass` (when or_too,
-// also the OR of the keys and of their complements, and the job's tile
-// status words cleared).
-__device__ __noinline__ void hist_read(const unsigned long long* keys, int64_t m, int pass, WsHeader* h,
-                                       bool or_too, unsigned long long* status, int64_t nstatus) {
+// One read of the keys: the digit histograms of every pass (a histogram
+// does not depend on the order of the keys, so each pass's is known before
+// any pass runs), the OR of the keys and of their complements, and the job's
+// tile status words cleared.
+__device__ __noinline__ void hist_read(const unsigned long long* keys, int64_t m, WsHeader* h,
+                                       unsigned long long* status, int64_t nstatus) {
   SortSmem& S = dyn_smem<SortSmem>();
-  // HCOPIES sub-histograms (warp w counts into copy w % HCOPIES) in the key
-  // area, to spread the shared-memory atomics
+  // HCOPIES sub-histograms per pass (warp w counts into copy w % HCOPIES) in
+  // the key area, to spread the shared-memory atomics
   constexpr int HCOPIES = 4;
-  static_assert(HCOPIES * 256 * 4 <= (int)sizeof(S.keys), "sub-histograms fit");
+  constexpr int HN = SORT_PASSES * HCOPIES * 256;
+  static_assert(HN * 4 <= (int)sizeof(S.keys), "sub-histograms fit");
   uint32_t* hs = reinterpret_cast<uint32_t*>(S.keys);
-  for (int k = threadIdx.x; k < HCOPIES * 256; k += LBLOCK) hs[k] = 0;
+  for (int k = threadIdx.x; k < HN; k += LBLOCK) hs[k] = 0;
   __syncthreads();
   uint32_t* mine = hs + ((threadIdx.x >> 5) % HCOPIES) * 256;
   const int64_t gt = (int64_t)blockIdx.x * LBLOCK + threadIdx.x, gs = (int64_t)gridDim.x * LBLOCK;
@@ -154,25 +155,25 @@ __device__ __noinline__ void hist_read(const unsigned long long* keys, int64_t m
     const unsigned long long k = __ldcs(keys + j);
     o |= k;
     no |= ~k;
-    atomicAdd(&mine[digit(k, pass)], 1u);
+#pragma unroll
+    for (int p = 0; p < SORT_PASSES; ++p) atomicAdd(&mine[p * HCOPIES * 256 + digit(k, p)], 1u);
   }
-  if (or_too) {
-    for (int off = 16; off; off >>= 1) {
-      o |= __shfl_xor_sync(FULL, o, off);
-      no |= __shfl_xor_sync(FULL, no, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicOr(&h->key_or, o);
-      atomicOr(&h->key_nor, no);
-    }
-    for (int64_t j = gt; j < nstatus; j += gs) status[j] = 0ull;
+  for (int off = 16; off; off >>= 1) {
+    o |= __shfl_xor_sync(FULL, o, off);
+    no |= __shfl_xor_sync(FULL, no, off);
   }
+  if ((threadIdx.x & 31) == 0) {
+    atomicOr(&h->key_or, o);
+    atomicOr(&h->key_nor, no);
+  }
+  for (int64_t j = gt; j < nstatus; j += gs) status[j] = 0ull;
   __syncthreads();
-  for (int k = threadIdx.x; k < 256; k += LBLOCK) {
+  for (int k = threadIdx.x; k < SORT_PASSES * 256; k += LBLOCK) {
+    const int p = k >> 8, d = k & 255;
     uint32_t c = 0;
 #pragma unroll
-    for (int q = 0; q < HCOPIES; ++q) c += hs[q * 256 + k];
-    if (c) atomicAdd(&h->hist[pass][k], c);
+    for (int q = 0; q < HCOPIES; ++q) c += hs[(p * HCOPIES + q) * 256 + d];
+    if (c) atomicAdd(&h->hist[p][d], c);
   }
   __syncthreads();
 }
@@ -196,17 +197,14 @@ __device__ __forceinline__ uint32_t block_excl_scan(SortSmem& S, uint32_t v) {
 
 // One pass over m elements from (kin, vin) to (kout, vout).  Returns false
 // when a look-back wait gave up (nothing more is written).
-// pnext: the next pass that will run (-1: none), whose histogram is
-// counted on the way.
 __device__ __noinline__ bool sort_pass(const unsigned long long* kin, const uint32_t* vin,
-                                       unsigned long long* kout, uint32_t* vout, int64_t m, int pass, int pnext,
-                                       uint32_t* hist, uint32_t* tile_next, unsigned long long* status,
+                                       unsigned long long* kout, uint32_t* vout, int64_t m, int pass,
+                                       const uint32_t* hist, uint32_t* tile_next, unsigned long long* status,
                                        uint32_t* gstatus) {
   SortSmem& S = dyn_smem<SortSmem>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, d0 = threadIdx.x;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
-  S.hn[d0] = 0;
   // elements with a smaller digit, over the whole set (thread d0 = digit d0)
   {
     const uint32_t c = hist[pass * 256 + d0];
@@ -320,11 +318,9 @@ __device__ __noinline__ bool sort_pass(const unsigned long long* kin, const uint
       const int64_t pos = (int64_t)j + S.delta[digit(k, pass)];
       kout[pos] = k;
       vout[pos] = S.vals[j];
-      if (pnext >= 0) atomicAdd(&S.hn[digit(k, pnext)], 1u);
     }
     __syncthreads();
   }
-  if (ok && pnext >= 0 && S.hn[d0]) atomicAdd(&hist[pnext * 256 + d0], S.hn[d0]);
   return ok;
 }
 
@@ -332,108 +328,115 @@ __device__ __noinline__ bool sort_pass(const unsigned long long* kin, const uint
 // The chains, one warp per chunk (level 0) or per group of chunk chains.
 //
 // A window of at most CHAIN_C0 + 2 entries (sorted keys with their indices)
-// is chained in two levels: lane l chains entries [l S, (l + 1) S) of it
-// (S = max(ceil(entries / 32), RUN_MIN)) on a small stack of window entries,
-// then lane 0 pushes the vertices of those run chains, in order, onto the
-// chunk's running stack.  An entry off its run's chain lies on or above
-// (lower chain; below for the upper one) the chain of a subset holding it,
-// so it is no strict vertex of any larger set's chain either; the first and
-// the last entry of every run stay.  The running stack keeps its last RING
-// entries in shared memory (slot e % RING, tagged with e); an entry leaving
-// the ring while it is still on the stack is written to its final place in
-// global memory (entry e at base + e), and finish() writes the rest, so only
-// deep stacks touch global memory before the end.
-constexpr int RUNS = 32;                                   // runs per window (one per lane)
-constexpr int RUN_MIN = 8;                                 // entries of a run at least
-constexpr int RUN_MAX = (CHAIN_C0 + 2 + RUNS - 1) / RUNS;  // entries of a run at most
-static_assert(RUN_MIN <= RUN_MAX, "run sizes");
-constexpr int RING = 128;
+// is chained in two levels: each of nl lanes chains S consecutive entries of
+// it (S = max(ceil(entries / nl), RUN_MIN)) on a small stack of window
+// entries, then one lane pushes the vertices of those run chains, in order,
+// onto the chunk's running stack.  An entry off its run's chain lies on or
+// above (lower chain; below for the upper one) the chain of a subset holding
+// it, so it is no strict vertex of any larger set's chain either; the first
+// and the last entry of every run stay.  At level 0 lanes 0-15 do a chunk's
+// lower chain and lanes 16-31 its upper chain on the same instruction stream
+// (the turn's sense is a run-time sign), so lanes 0 and 16 walk the two
+// chains side by side; later levels give one chain all 32 lanes.  The
+// running stack keeps its last RING entries in shared memory (slot e % RING,
+// tagged with e); an entry leaving the ring while it is still on the stack
+// is written to its final place in global memory (entry e at base + e), and
+// finish() writes the rest, so only deep stacks touch global memory before
+// the end.
+constexpr int RUN_MIN = 8;                               // entries of a run at least
+constexpr int RUN_CAP = 16 * ((CHAIN_C0 + 2 + 15) / 16);  // run entries of a side (16 or 32 lanes)
+constexpr int RING = 64;
 static_assert((RING & (RING - 1)) == 0, "ring slots by mask");
 
 struct WarpChain {
   unsigned long long k[CHAIN_C0];  // the chunk's elements (level 0) or the window (later levels)
-  unsigned long long rk[RING];     // ring of the running stack's last entries
-  int64_t rpos[RING];              // ... the entry each slot holds
+  unsigned long long rk[2][RING];  // per side: ring of the running stack's last entries
+  int64_t rpos[2][RING];           // ... the entry each slot holds
   uint32_t v[CHAIN_C0];
-  uint32_t rv[RING];
-  int runn[RUNS];
-  uint16_t pos[CHAIN_C0 + 2];      // level 0: the window's entries, as positions in k / v
-  uint16_t run[RUNS * RUN_MAX];    // run chains (window entries), run l's from l * S
+  uint32_t rv[2][RING];
+  int runn[32];                    // run chain lengths, by lane
+  uint16_t pos[2][CHAIN_C0 + 2];   // level 0, per side: the window's entries as positions in k / v
+  uint16_t run[2][RUN_CAP];        // per side: run chains (window entries), run i's from i * S
 };
 struct ChainSmem {
   WarpChain w[WARPS];
 };
 
-// Is key b, after o and a, a strict turn the right way (left for the lower
-// chain, right for the upper one)?
-template <bool UPPER>
-__device__ __forceinline__ bool turns(unsigned long long o, unsigned long long a, unsigned long long b) {
-  const long long c = cross_k(o, a, b);
-  return UPPER ? c < 0 : c > 0;
-}
-
-// The running stack of one chunk: push by lane 0 only, init and finish
-// warp-wide.
-template <bool UPPER>
+// The running stack of one chain: push by one lane, init and finish by the
+// warp.  sg = +1: lower chain (pop while the turn is not strictly left);
+// sg = -1: upper chain (pop while it is not strictly right).
 struct RunStack {
   unsigned long long* K;  // output: entry e at K[base + e], V[base + e]
   uint32_t* V;
+  unsigned long long* rk;  // this side's ring
+  uint32_t* rv;
+  int64_t* rpos;
   int64_t base;
   int64_t n;                  // entries
   unsigned long long k1, k2;  // top and second keys
   uint32_t v1;                // top index
+  long long sg;
 
-  __device__ __forceinline__ void init(WarpChain& W, unsigned long long* k, uint32_t* v, int64_t b) {
-    K = k; V = v; base = b; n = 0; k1 = k2 = 0; v1 = 0;
-    // a tag no entry position (nor n - RING) can take
-    for (int i = threadIdx.x & 31; i < RING; i += 32) W.rpos[i] = INT64_MIN;
-    __syncwarp();
+  __device__ __forceinline__ void init(WarpChain& W, int side, unsigned long long* k, uint32_t* v, int64_t b,
+                                       long long sign) {
+    K = k; V = v; base = b; n = 0; k1 = k2 = 0; v1 = 0; sg = sign;
+    rk = W.rk[side]; rv = W.rv[side]; rpos = W.rpos[side];
+  }
+  // a tag no entry position (nor n - RING) can take; warp-wide
+  static __device__ __forceinline__ void clear(WarpChain& W, int side) {
+    for (int i = threadIdx.x & 31; i < RING; i += 32) W.rpos[side][i] = INT64_MIN;
   }
   static __device__ __forceinline__ int slot(int64_t e) { return (int)((uint64_t)e & (RING - 1)); }
   // entry e (< n): from its ring slot, else from global memory (it left the
   // ring while on the stack, so it was written there)
-  __device__ __forceinline__ void entry(const WarpChain& W, int64_t e, unsigned long long& k, uint32_t& v) const {
+  __device__ __forceinline__ void entry(int64_t e, unsigned long long& k, uint32_t& v) const {
     const int q = slot(e);
-    if (W.rpos[q] == e) { k = W.rk[q]; v = W.rv[q]; }
+    if (rpos[q] == e) { k = rk[q]; v = rv[q]; }
     else { k = K[base + e]; v = V[base + e]; }
   }
-  __device__ __forceinline__ void push(WarpChain& W, unsigned long long key, uint32_t val) {
+  __device__ __forceinline__ void push(unsigned long long key, uint32_t val) {
     if (n > 0 && key == k1) {  // equal coordinates: the lowest index stands
       if (val < v1) {
         v1 = val;
         const int q = slot(n - 1);
-        if (W.rpos[q] == n - 1) W.rv[q] = val;
+        if (rpos[q] == n - 1) rv[q] = val;
         else V[base + n - 1] = val;
       }
       return;
     }
-    while (n >= 2 && !turns<UPPER>(k2, k1, key)) {
+    while (n >= 2 && sg * cross_k(k2, k1, key) <= 0) {
       --n;
       k1 = k2;
       unsigned long long kk;
-      entry(W, n - 1, kk, v1);
-      if (n >= 2) { uint32_t vv; entry(W, n - 2, k2, vv); }
+      entry(n - 1, kk, v1);
+      if (n >= 2) { uint32_t vv; entry(n - 2, k2, vv); }
     }
     const int q = slot(n);
-    if (W.rpos[q] == n - RING) {  // a stack entry leaves the ring
-      K[base + n - RING] = W.rk[q];
-      V[base + n - RING] = W.rv[q];
+    if (rpos[q] == n - RING) {  // a stack entry leaves the ring
+      K[base + n - RING] = rk[q];
+      V[base + n - RING] = rv[q];
     }
-    W.rk[q] = key;
-    W.rv[q] = val;
-    W.rpos[q] = n;
+    rk[q] = key;
+    rv[q] = val;
+    rpos[q] = n;
     ++n;
     k2 = k1;
     k1 = key;
     v1 = val;
   }
-  // warp-wide, after lane 0's last push: the entries still in the ring to
-  // global memory; returns n
-  __device__ __forceinline__ int64_t finish(WarpChain& W) {
-    const int64_t nn = __shfl_sync(FULL, n, 0);
+  // warp-wide, after the last push (by lane `owner`): the entries still in
+  // the ring to global memory; returns n
+  __device__ __forceinline__ int64_t finish(int owner) {
+    const int64_t nn = __shfl_sync(FULL, n, owner);
+    unsigned long long* KK = reinterpret_cast<unsigned long long*>(__shfl_sync(FULL, (unsigned long long)K, owner));
+    uint32_t* VV = reinterpret_cast<uint32_t*>(__shfl_sync(FULL, (unsigned long long)V, owner));
+    const int64_t bb = __shfl_sync(FULL, base, owner);
+    unsigned long long* RK = reinterpret_cast<unsigned long long*>(__shfl_sync(FULL, (unsigned long long)rk, owner));
+    uint32_t* RV = reinterpret_cast<uint32_t*>(__shfl_sync(FULL, (unsigned long long)rv, owner));
+    int64_t* RP = reinterpret_cast<int64_t*>(__shfl_sync(FULL, (unsigned long long)rpos, owner));
     for (int64_t e = max(nn - RING, (int64_t)0) + (threadIdx.x & 31); e < nn; e += 32) {
       const int q = slot(e);
-      if (W.rpos[q] == e) { K[base + e] = W.rk[q]; V[base + e] = W.rv[q]; }
+      if (RP[q] == e) { KK[bb + e] = RK[q]; VV[bb + e] = RV[q]; }
     }
     __syncwarp();
     return nn;
@@ -441,23 +444,24 @@ struct RunStack {
 };
 
 // Lane-level chain of window entries [lo, lo + len) onto q (window entries);
-// returns its length.  IND: entry e is element W.pos[e].
-template <bool UPPER, bool IND>
-__device__ __forceinline__ int run_chain(const WarpChain& W, int lo, int len, uint16_t* q) {
-  auto at = [&](int e) { return IND ? (int)W.pos[e] : e; };
+// returns its length.  ps: entry e is element ps[e] (null: element e).
+__device__ __forceinline__ int run_chain(const WarpChain& W, const uint16_t* ps, int lo, int len, uint16_t* q,
+                                         long long sg) {
   int n = 0;
   unsigned long long k1 = 0, k2 = 0;
   for (int t = 0; t < len; ++t) {
     const int e = lo + t;
-    const unsigned long long key = W.k[at(e)];
+    const int p = ps ? (int)ps[e] : e;
+    const unsigned long long key = W.k[p];
     if (n > 0 && key == k1) {  // equal coordinates: keep the lower index
-      if (W.v[at(e)] < W.v[at(q[n - 1])]) q[n - 1] = (uint16_t)e;
+      const int pq = ps ? (int)ps[q[n - 1]] : (int)q[n - 1];
+      if (W.v[p] < W.v[pq]) q[n - 1] = (uint16_t)e;
       continue;
     }
-    while (n >= 2 && !turns<UPPER>(k2, k1, key)) {
+    while (n >= 2 && sg * cross_k(k2, k1, key) <= 0) {
       --n;
       k1 = k2;
-      if (n >= 2) k2 = W.k[at(q[n - 2])];
+      if (n >= 2) k2 = W.k[ps ? (int)ps[q[n - 2]] : (int)q[n - 2]];
     }
     q[n++] = (uint16_t)e;
     k2 = k1;
@@ -466,23 +470,25 @@ __device__ __forceinline__ int run_chain(const WarpChain& W, int lo, int len, ui
   return n;
 }
 
-// One window of `len` (<= CHAIN_C0 + 2) entries, warp-wide, onto the running
-// stack R (lane 0's).
-template <bool UPPER, bool IND>
-__device__ __forceinline__ void window_chain(WarpChain& W, int len, RunStack<UPPER>& R) {
-  const int lane = threadIdx.x & 31;
-  const int S = max((len + RUNS - 1) / RUNS, RUN_MIN);
-  const int lo = min(lane * S, len), n = max(min(S, len - lo), 0);
-  W.runn[lane] = n > 0 ? run_chain<UPPER, IND>(W, lo, n, W.run + lane * S) : 0;
+// One window of `len` (<= CHAIN_C0 + 2) entries of side `side` onto R, by
+// the nl lanes from lane0 (all lanes call it; each lane's arguments are its
+// group's); lane0 walks and owns R.
+__device__ __forceinline__ void window_chain(WarpChain& W, int side, const uint16_t* ps, int lane0, int nl, int len,
+                                             RunStack& R) {
+  const int lane = threadIdx.x & 31, li = lane - lane0;
+  const int S = max((len + nl - 1) / nl, RUN_MIN);
+  const int lo = min(li * S, len), n = max(min(S, len - lo), 0);
+  uint16_t* run = W.run[side];
+  W.runn[lane] = n > 0 ? run_chain(W, ps, lo, n, run + li * S, R.sg) : 0;
   __syncwarp();
-  if (lane == 0) {
+  if (li == 0) {
     const int nr = (len + S - 1) / S;
     for (int l = 0; l < nr; ++l) {
-      const int c = W.runn[l];
+      const int c = W.runn[lane0 + l];
       for (int i = 0; i < c; ++i) {
-        const int e = W.run[l * S + i];
-        const int p = IND ? (int)W.pos[e] : e;
-        R.push(W, W.k[p], W.v[p]);
+        const int e = run[l * S + i];
+        const int p = ps ? (int)ps[e] : e;
+        R.push(W.k[p], W.v[p]);
       }
     }
   }
@@ -517,21 +523,23 @@ __device__ __noinline__ void chain0(unsigned long long* Ks, uint32_t* Vs, unsign
     const int64_t tb = t * CHAIN_C0;
     const int tn = (int)min((int64_t)CHAIN_C0, m - tb);
     // the chunk in rows of 32, eight rows' loads in flight at a time
-    constexpr int R = 8;
-    for (int r0 = 0; r0 < CHAIN_C0 / 32; r0 += R) {
-      unsigned long long kk[R];
-      uint32_t vv[R];
+    constexpr int R8 = 8;
+    for (int r0 = 0; r0 < CHAIN_C0 / 32; r0 += R8) {
+      unsigned long long kk[R8];
+      uint32_t vv[R8];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
+      for (int r = 0; r < R8; ++r) {
         const int e = (r0 + r) * 32 + lane;
         if (e < tn) { kk[r] = Ks[tb + e]; vv[r] = Vs[tb + e]; }
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
+      for (int r = 0; r < R8; ++r) {
         const int e = (r0 + r) * 32 + lane;
         if (e < tn) { W.k[e] = kk[r]; W.v[e] = vv[r]; }
       }
     }
+    RunStack::clear(W, 0);
+    RunStack::clear(W, 1);
     __syncwarp();
     // Equal keys are adjacent but their indices in no order (survivors come
     // in compaction order): the first slot of every run of equal keys takes
@@ -549,37 +557,30 @@ __device__ __noinline__ void chain0(unsigned long long* Ks, uint32_t* Vs, unsign
       }
     }
     __syncwarp();
-    // lower chain: the first point of every column, then the chunk's last key
-    int L = 0;
+    // lower list: the first point of every column, then the chunk's last key;
+    // upper list: the chunk's first point, then the last key of every column
+    int Llo = 0, Lup = 1;
+    if (lane == 0) W.pos[1][0] = 0;
     for (int e0 = 0; e0 < tn; e0 += 32) {
       const int e = e0 + lane;
-      const bool f = e < tn && (e == 0 || key_x(W.k[e - 1]) != key_x(W.k[e]));
-      const unsigned bal = __ballot_sync(FULL, f);
-      if (f) W.pos[L + __popc(bal & lt)] = (uint16_t)e;
-      L += __popc(bal);
+      const int x = e < tn ? key_x(W.k[e]) : 0;
+      const bool flo = e < tn && (e == 0 || key_x(W.k[e - 1]) != x);
+      const bool fup = e < tn && (e == tn - 1 || key_x(W.k[e + 1]) != x);
+      const unsigned blo = __ballot_sync(FULL, flo), bup = __ballot_sync(FULL, fup);
+      if (flo) W.pos[0][Llo + __popc(blo & lt)] = (uint16_t)e;
+      if (fup) W.pos[1][Lup + __popc(bup & lt)] = (uint16_t)run_start(W, e);
+      Llo += __popc(blo);
+      Lup += __popc(bup);
     }
-    if (lane == 0) W.pos[L] = (uint16_t)run_start(W, tn - 1);
-    ++L;
+    if (lane == 0) W.pos[0][Llo] = (uint16_t)run_start(W, tn - 1);
+    ++Llo;
     __syncwarp();
-    RunStack<false> rl;
-    rl.init(W, Ks, Vs, tb);
-    window_chain<false, true>(W, L, rl);
-    const int64_t nlo = rl.finish(W);
-    // upper chain: the chunk's first point, then the last key of every column
-    if (lane == 0) W.pos[0] = 0;
-    L = 1;
-    for (int e0 = 0; e0 < tn; e0 += 32) {
-      const int e = e0 + lane;
-      const bool f = e < tn && (e == tn - 1 || key_x(W.k[e + 1]) != key_x(W.k[e]));
-      const unsigned bal = __ballot_sync(FULL, f);
-      if (f) W.pos[L + __popc(bal & lt)] = (uint16_t)run_start(W, e);
-      L += __popc(bal);
-    }
-    __syncwarp();
-    RunStack<true> ru;
-    ru.init(W, Ku, Vu, tb);
-    window_chain<true, true>(W, L, ru);
-    const int64_t nup = ru.finish(W);
+    const int side = lane >> 4;
+    RunStack R;
+    R.init(W, side, side ? Ku : Ks, side ? Vu : Vs, tb, side ? -1 : 1);
+    window_chain(W, side, W.pos[side], side * 16, 16, side ? Lup : Llo, R);
+    const int64_t nlo = R.finish(0);
+    const int64_t nup = R.finish(16);
     if (lane == 0) {
       cnt_lo[t] = (uint32_t)nlo;
       cnt_up[t] = (uint32_t)nup;
@@ -594,10 +595,9 @@ __device__ __noinline__ void chain0(unsigned long long* Ks, uint32_t* Vs, unsign
 // unread entry j of the concatenation sits at or after c0 * span + j, and
 // the stack's entry e is written at c0 * span + e with e below the entries
 // read so far, so no write reaches input not yet read.  Returns the new
-// chain's length (lane 0).
-template <bool UPPER>
+// chain's length.
 __device__ __forceinline__ uint32_t merge_group(WarpChain& W, unsigned long long* K, uint32_t* V, const uint32_t* cin,
-                                                int64_t c0, int64_t c1, int64_t span) {
+                                                int64_t c0, int64_t c1, int64_t span, long long sg) {
   const int lane = threadIdx.x & 31;
   const int nc = (int)(c1 - c0);  // at most CHAIN_FAN == 32
   const int64_t cnt = lane < nc ? (int64_t)cin[c0 + lane] : 0;
@@ -607,8 +607,10 @@ __device__ __forceinline__ uint32_t merge_group(WarpChain& W, unsigned long long
     if (lane >= off) incl += u;
   }
   const int64_t offc = incl - cnt, total = __shfl_sync(FULL, incl, 31);
-  RunStack<UPPER> R;
-  R.init(W, K, V, c0 * span);
+  RunStack::clear(W, 0);
+  RunStack R;
+  R.init(W, 0, K, V, c0 * span, sg);
+  __syncwarp();
   for (int64_t w0 = 0; w0 < total; w0 += CHAIN_C0) {
     const int len = (int)min((int64_t)CHAIN_C0, total - w0);
     for (int c = 0; c < nc; ++c) {
@@ -621,9 +623,9 @@ __device__ __forceinline__ uint32_t merge_group(WarpChain& W, unsigned long long
       }
     }
     __syncwarp();
-    window_chain<UPPER, false>(W, len, R);
+    window_chain(W, 0, nullptr, 0, 32, len, R);
   }
-  return (uint32_t)R.finish(W);
+  return (uint32_t)R.finish(0);
 }
 
 // Later level: group g merges the chains of chunks [g*FAN, (g+1)*FAN) of the
@@ -638,13 +640,9 @@ __device__ __noinline__ void chainN(unsigned long long* Ks, uint32_t* Vs, unsign
     const int64_t g = t >> 1;
     const int64_t c0 = g * CHAIN_FAN;
     const int64_t c1 = min(c0 + (int64_t)CHAIN_FAN, nch_prev);
-    if (t & 1) {
-      const uint32_t n = merge_group<true>(W, Ku, Vu, cin_up, c0, c1, span);
-      if (lane == 0) cout_up[g] = n;
-    } else {
-      const uint32_t n = merge_group<false>(W, Ks, Vs, cin_lo, c0, c1, span);
-      if (lane == 0) cout_lo[g] = n;
-    }
+    const bool up = t & 1;
+    const uint32_t n = merge_group(W, up ? Ku : Ks, up ? Vu : Vs, up ? cin_up : cin_lo, c0, c1, span, up ? -1 : 1);
+    if (lane == 0) (up ? cout_up : cout_lo)[g] = n;
     __syncwarp();
   }
 }
@@ -669,36 +667,43 @@ __device__ __noinline__ void chain_emit(const uint32_t* Vs, const uint32_t* Vu, 
   if (gt == 0) *out_n = (a - 1) + (b - 1);
 }
 
+// phase 0: the histograms and the sort passes of every job; phase 1: the
+// chains and the emission of every job (a launch of its own, so that each
+// phase gets the dynamic shared memory it needs and the sort keeps the rest
+// of the SM's memory as L1).
 __global__ void __launch_bounds__(LBLOCK, 2) k_large(const LargeJob* __restrict__ table, const int* njobs_dev,
-                                                   LargeJob single, uint32_t* bar, uint32_t* bar_status) {
+                                                   LargeJob single, uint32_t* bar, uint32_t* bar_status, int phase) {
+  if (*reinterpret_cast<const volatile uint32_t*>(bar_status) & HULL_DEVICE_TIMEOUT) return;
   const int njobs = table ? *reinterpret_cast<const volatile int*>(njobs_dev) : 1;
   for (int jb = 0; jb < njobs; ++jb) {
     const LargeJob J = table ? table[jb] : single;
     if (*reinterpret_cast<const volatile uint32_t*>(&J.h->status)) continue;
     const int64_t m = (int64_t)*reinterpret_cast<const volatile unsigned long long*>(J.count);
     if (m <= SMALL_MAX) continue;
-    const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
-    hist_read(J.ka, m, 0, J.h, true, J.tilecnt, nt * 256);
-    if (!grid_sync(bar, bar_status)) return;
-    // the passes that move anything; the first one's histogram if not pass 0's
-    const unsigned live = live_passes(J.h);
-    if (live && !(live & 1u)) {
-      hist_read(J.ka, m, __ffs(live) - 1, J.h, false, nullptr, 0);
+    if (phase == 0) {
+      const int64_t nt = (m + SORT_TILE - 1) / SORT_TILE;
+      hist_read(J.ka, m, J.h, J.tilecnt, nt * 256);
       if (!grid_sync(bar, bar_status)) return;
+      const unsigned live = live_passes(J.h);  // the passes that move anything
+      unsigned long long *kin = J.ka, *kout = J.kb;
+      uint32_t *vin = J.va, *vout = J.vb;
+      for (int p = 0; p < SORT_PASSES; ++p) {
+        if (!((live >> p) & 1u)) continue;
+        const bool ok = sort_pass(kin, vin, kout, vout, m, p, &J.h->hist[0][0], J.h->tile_next, J.tilecnt,
+                                  bar_status);
+        if (!grid_sync(bar, bar_status) || !ok) return;
+        unsigned long long* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+      }
+      // the next job uses other buffers and its own counters; the barrier
+      // words are balanced, so it needs no barrier first
+      continue;
     }
-    unsigned long long *kin = J.ka, *kout = J.kb;
-    uint32_t *vin = J.va, *vout = J.vb;
-    for (int p = 0; p < SORT_PASSES; ++p) {
-      if (!((live >> p) & 1u)) continue;
-      const unsigned later = live & ~((2u << p) - 1u);
-      const int pnext = later ? __ffs(later) - 1 : -1;
-      const bool ok = sort_pass(kin, vin, kout, vout, m, p, pnext, &J.h->hist[0][0], J.h->tile_next, J.tilecnt,
-                                bar_status);
-      if (!grid_sync(bar, bar_status) || !ok) return;
-      unsigned long long* tk = kin; kin = kout; kout = tk;
-      uint32_t* tv = vin; vin = vout; vout = tv;
-    }
-    // sorted in (kin, vin); upper chains go to (kout, vout)
+    // sorted in (kin, vin): the buffer the last live pass wrote; upper
+    // chains go to (kout, vout)
+    const bool odd = __popc(live_passes(J.h)) & 1;
+    unsigned long long *kin = odd ? J.kb : J.ka, *kout = odd ? J.ka : J.kb;
+    uint32_t *vin = odd ? J.vb : J.va, *vout = odd ? J.va : J.vb;
     const int64_t nch0 = (std::max<int64_t>(J.cap, 1) + CHAIN_C0 - 1) / CHAIN_C0;
     uint32_t* lo[2] = {J.cnt, J.cnt + 2 * nch0};
     uint32_t* up[2] = {J.cnt + nch0, J.cnt + 3 * nch0};
@@ -714,8 +719,6 @@ __global__ void __launch_bounds__(LBLOCK, 2) k_large(const LargeJob* __restrict_
       span *= CHAIN_FAN;
     }
     chain_emit(vin, vout, lo[par], up[par], J.out_idx, J.out_n);
-    // the next job uses other buffers and its own counters; the barrier
-    // words are balanced, so it needs no barrier first
   }
 }
 
@@ -730,29 +733,36 @@ int chain_levels(int64_t cap) {
 
 cudaError_t launch_large(const LargeJob* table, const int* njobs, const LargeJob& single, uint32_t* bar,
                          uint32_t* bar_status, cudaStream_t st) {
-  static int occ_cache[64] = {};
+  static int occ_cache[64][2] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  const size_t dsm = std::max(sizeof(SortSmem), sizeof(ChainSmem));
-  if (occ_cache[dev] == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+  const size_t dsm[2] = {sizeof(SortSmem), sizeof(ChainSmem)};
+  if (occ_cache[dev][0] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max(dsm[0], dsm[1]));
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_large, LBLOCK, dsm);
-    if (e != cudaSuccess) return e;
-    occ_cache[dev] = std::max(1, std::min(occ, 4));
+    for (int ph = 0; ph < 2; ++ph) {
+      int occ = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_large, LBLOCK, dsm[ph]);
+      if (e != cudaSuccess) return e;
+      occ_cache[dev][ph] = std::max(1, std::min(occ, 4));
+    }
   }
-  const unsigned G = (unsigned)(device_sm_count() * occ_cache[dev]);
   LargeJob one = single;
   const LargeJob* tab = table;
   const int* nj = njobs;
   uint32_t* b = bar;
   uint32_t* bs = bar_status;
-  void* args[] = {(void*)&tab, (void*)&nj, (void*)&one, (void*)&b, (void*)&bs};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_large, dim3(G), dim3(LBLOCK), args, dsm, st);
-  count_launches(1);
-  return e;
+  for (int ph = 0; ph < 2; ++ph) {
+    const unsigned G = (unsigned)(device_sm_count() * occ_cache[dev][ph]);
+    int phase = ph;
+    void* args[] = {(void*)&tab, (void*)&nj, (void*)&one, (void*)&b, (void*)&bs, (void*)&phase};
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_large, dim3(G), dim3(LBLOCK), args, dsm[ph], st);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace cudapre
