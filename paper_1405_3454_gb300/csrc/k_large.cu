@@ -337,7 +337,8 @@ __device__ __noinline__ bool sort_pass(const unsigned long long* kin, const uint
 // and the last entry of every run stay.  At level 0 lanes 0-15 do a chunk's
 // lower chain and lanes 16-31 its upper chain on the same instruction stream
 // (the turn's sense is a run-time sign), so lanes 0 and 16 walk the two
-// chains side by side; later levels give one chain all 32 lanes.  The
+// chains side by side; later levels do the same with a group's lower and
+// upper chains.  The
 // running stack keeps its last RING entries in shared memory (slot e % RING,
 // tagged with e); an entry leaving the ring while it is still on the stack
 // is written to its final place in global memory (entry e at base + e), and
@@ -355,6 +356,7 @@ struct WarpChain {
   uint32_t v[CHAIN_C0];
   uint32_t rv[2][RING];
   int runn[32];                    // run chain lengths, by lane
+  int64_t off[2][CHAIN_FAN + 1];   // later levels, per side: the group's chain offsets
   uint16_t pos[2][CHAIN_C0 + 2];   // level 0, per side: the window's entries as positions in k / v
   uint16_t run[2][RUN_CAP];        // per side: run chains (window entries), run i's from i * S
 };
@@ -444,24 +446,25 @@ struct RunStack {
 };
 
 // Lane-level chain of window entries [lo, lo + len) onto q (window entries);
-// returns its length.  ps: entry e is element ps[e] (null: element e).
-__device__ __forceinline__ int run_chain(const WarpChain& W, const uint16_t* ps, int lo, int len, uint16_t* q,
-                                         long long sg) {
+// returns its length.  Entry e is element ps[e], or element eb + e when ps
+// is null.
+__device__ __forceinline__ int run_chain(const WarpChain& W, const uint16_t* ps, int eb, int lo, int len,
+                                         uint16_t* q, long long sg) {
+  auto el = [&](int e) { return ps ? (int)ps[e] : eb + e; };
   int n = 0;
   unsigned long long k1 = 0, k2 = 0;
   for (int t = 0; t < len; ++t) {
     const int e = lo + t;
-    const int p = ps ? (int)ps[e] : e;
+    const int p = el(e);
     const unsigned long long key = W.k[p];
     if (n > 0 && key == k1) {  // equal coordinates: keep the lower index
-      const int pq = ps ? (int)ps[q[n - 1]] : (int)q[n - 1];
-      if (W.v[p] < W.v[pq]) q[n - 1] = (uint16_t)e;
+      if (W.v[p] < W.v[el(q[n - 1])]) q[n - 1] = (uint16_t)e;
       continue;
     }
     while (n >= 2 && sg * cross_k(k2, k1, key) <= 0) {
       --n;
       k1 = k2;
-      if (n >= 2) k2 = W.k[ps ? (int)ps[q[n - 2]] : (int)q[n - 2]];
+      if (n >= 2) k2 = W.k[el(q[n - 2])];
     }
     q[n++] = (uint16_t)e;
     k2 = k1;
@@ -472,14 +475,15 @@ __device__ __forceinline__ int run_chain(const WarpChain& W, const uint16_t* ps,
 
 // One window of `len` (<= CHAIN_C0 + 2) entries of side `side` onto R, by
 // the nl lanes from lane0 (all lanes call it; each lane's arguments are its
-// group's); lane0 walks and owns R.
-__device__ __forceinline__ void window_chain(WarpChain& W, int side, const uint16_t* ps, int lane0, int nl, int len,
-                                             RunStack& R) {
+// group's); lane0 walks and owns R.  Entry e is element ps[e], or element
+// eb + e when ps is null.
+__device__ __forceinline__ void window_chain(WarpChain& W, int side, const uint16_t* ps, int eb, int lane0, int nl,
+                                             int len, RunStack& R) {
   const int lane = threadIdx.x & 31, li = lane - lane0;
   const int S = max((len + nl - 1) / nl, RUN_MIN);
   const int lo = min(li * S, len), n = max(min(S, len - lo), 0);
   uint16_t* run = W.run[side];
-  W.runn[lane] = n > 0 ? run_chain(W, ps, lo, n, run + li * S, R.sg) : 0;
+  W.runn[lane] = n > 0 ? run_chain(W, ps, eb, lo, n, run + li * S, R.sg) : 0;
   __syncwarp();
   if (li == 0) {
     const int nr = (len + S - 1) / S;
@@ -487,7 +491,7 @@ __device__ __forceinline__ void window_chain(WarpChain& W, int side, const uint1
       const int c = W.runn[lane0 + l];
       for (int i = 0; i < c; ++i) {
         const int e = run[l * S + i];
-        const int p = ps ? (int)ps[e] : e;
+        const int p = ps ? (int)ps[e] : eb + e;
         R.push(W.k[p], W.v[p]);
       }
     }
@@ -578,7 +582,7 @@ __device__ __noinline__ void chain0(unsigned long long* Ks, uint32_t* Vs, unsign
     const int side = lane >> 4;
     RunStack R;
     R.init(W, side, side ? Ku : Ks, side ? Vu : Vs, tb, side ? -1 : 1);
-    window_chain(W, side, W.pos[side], side * 16, 16, side ? Lup : Llo, R);
+    window_chain(W, side, W.pos[side], 0, side * 16, 16, side ? Lup : Llo, R);
     const int64_t nlo = R.finish(0);
     const int64_t nup = R.finish(16);
     if (lane == 0) {
@@ -590,60 +594,74 @@ __device__ __noinline__ void chain0(unsigned long long* Ks, uint32_t* Vs, unsign
 }
 
 // One group of a later level: the chains of chunks [c0, c1) of the previous
-// level (span `span` each, counts cin), concatenated in order (still sorted),
-// chained again in place from c0 * span by one warp, window by window.  An
-// unread entry j of the concatenation sits at or after c0 * span + j, and
-// the stack's entry e is written at c0 * span + e with e below the entries
-// read so far, so no write reaches input not yet read.  Returns the new
-// chain's length.
-__device__ __forceinline__ uint32_t merge_group(WarpChain& W, unsigned long long* K, uint32_t* V, const uint32_t* cin,
-                                                int64_t c0, int64_t c1, int64_t span, long long sg) {
-  const int lane = threadIdx.x & 31;
+// level (span `span` each, counts cin_lo / cin_up), concatenated in order
+// (still sorted), chained again in place from c0 * span by one warp, lanes
+// 0-15 the lower chains and lanes 16-31 the upper ones side by side, window
+// by window (each side's window takes half of the chunk area).  An unread
+// entry j of a side's concatenation sits at or after c0 * span + j, and the
+// stack's entry e is written at c0 * span + e with e below the entries read
+// so far, so no write reaches input not yet read.
+__device__ __forceinline__ void merge_group(WarpChain& W, unsigned long long* Ks, uint32_t* Vs,
+                                            unsigned long long* Ku, uint32_t* Vu, const uint32_t* cin_lo,
+                                            const uint32_t* cin_up, int64_t c0, int64_t c1, int64_t span,
+                                            uint32_t* out_lo, uint32_t* out_up) {
+  constexpr int WCAP = CHAIN_C0 / 2;
+  const int lane = threadIdx.x & 31, side = lane >> 4, li = lane & 15;
   const int nc = (int)(c1 - c0);  // at most CHAIN_FAN == 32
-  const int64_t cnt = lane < nc ? (int64_t)cin[c0 + lane] : 0;
-  int64_t incl = cnt;
-  for (int off = 1; off < 32; off <<= 1) {
-    const int64_t u = __shfl_up_sync(FULL, incl, off);
-    if (lane >= off) incl += u;
+  for (int sd = 0; sd < 2; ++sd) {  // the chain offsets of both sides (warp-wide scans)
+    const int64_t cnt = lane < nc ? (int64_t)(sd ? cin_up : cin_lo)[c0 + lane] : 0;
+    int64_t incl = cnt;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int64_t u = __shfl_up_sync(FULL, incl, off);
+      if (lane >= off) incl += u;
+    }
+    if (lane == 0) W.off[sd][0] = 0;
+    if (lane < nc) W.off[sd][lane + 1] = incl;
   }
-  const int64_t offc = incl - cnt, total = __shfl_sync(FULL, incl, 31);
   RunStack::clear(W, 0);
-  RunStack R;
-  R.init(W, 0, K, V, c0 * span, sg);
+  RunStack::clear(W, 1);
   __syncwarp();
-  for (int64_t w0 = 0; w0 < total; w0 += CHAIN_C0) {
-    const int len = (int)min((int64_t)CHAIN_C0, total - w0);
+  unsigned long long* K = side ? Ku : Ks;
+  uint32_t* V = side ? Vu : Vs;
+  const int64_t total = W.off[side][nc];
+  const int64_t tmax = max(W.off[0][nc], W.off[1][nc]);
+  RunStack R;
+  R.init(W, side, K, V, c0 * span, side ? -1 : 1);
+  const int eb = side * WCAP;
+  for (int64_t w0 = 0; w0 < tmax; w0 += WCAP) {
+    const int len = (int)max(min((int64_t)WCAP, total - w0), (int64_t)0);
     for (int c = 0; c < nc; ++c) {
-      const int64_t oc = __shfl_sync(FULL, offc, c), nn = __shfl_sync(FULL, cnt, c);
-      const int64_t a = max(oc, w0), b = min(oc + nn, w0 + len);
+      const int64_t oc = W.off[side][c];
+      const int64_t a = max(oc, w0), b = min(W.off[side][c + 1], w0 + len);
       const int64_t src = (c0 + c) * span - oc;
-      for (int64_t j = a + lane; j < b; j += 32) {
-        W.k[j - w0] = K[src + j];
-        W.v[j - w0] = V[src + j];
+      for (int64_t j = a + li; j < b; j += 16) {
+        W.k[eb + (j - w0)] = K[src + j];
+        W.v[eb + (j - w0)] = V[src + j];
       }
     }
     __syncwarp();
-    window_chain(W, 0, nullptr, 0, 32, len, R);
+    window_chain(W, side, nullptr, eb, side * 16, 16, len, R);
   }
-  return (uint32_t)R.finish(0);
+  const int64_t nlo = R.finish(0), nup = R.finish(16);
+  if (lane == 0) {
+    *out_lo = (uint32_t)nlo;
+    *out_up = (uint32_t)nup;
+  }
+  __syncwarp();
 }
 
 // Later level: group g merges the chains of chunks [g*FAN, (g+1)*FAN) of the
-// previous level; warp task 2g does the lower chains, 2g+1 the upper ones.
+// previous level, one warp per group.
 __device__ __noinline__ void chainN(unsigned long long* Ks, uint32_t* Vs, unsigned long long* Ku,
                                     uint32_t* Vu, const uint32_t* cin_lo, const uint32_t* cin_up, uint32_t* cout_lo,
                                     uint32_t* cout_up, int64_t nch_prev, int64_t span) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   WarpChain& W = dyn_smem<ChainSmem>().w[warp];
   const int64_t ng = (nch_prev + CHAIN_FAN - 1) / CHAIN_FAN;
-  for (int64_t t = (int64_t)blockIdx.x * WARPS + warp; t < 2 * ng; t += (int64_t)gridDim.x * WARPS) {
-    const int64_t g = t >> 1;
+  for (int64_t g = (int64_t)blockIdx.x * WARPS + warp; g < ng; g += (int64_t)gridDim.x * WARPS) {
     const int64_t c0 = g * CHAIN_FAN;
     const int64_t c1 = min(c0 + (int64_t)CHAIN_FAN, nch_prev);
-    const bool up = t & 1;
-    const uint32_t n = merge_group(W, up ? Ku : Ks, up ? Vu : Vs, up ? cin_up : cin_lo, c0, c1, span, up ? -1 : 1);
-    if (lane == 0) (up ? cout_up : cout_lo)[g] = n;
-    __syncwarp();
+    merge_group(W, Ks, Vs, Ku, Vu, cin_lo, cin_up, c0, c1, span, cout_lo + g, cout_up + g);
   }
 }
 

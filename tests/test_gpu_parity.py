@@ -235,6 +235,22 @@ def test_no_prefilter_hull_equals_the_method(gpu_lib, name, n):
     assert got == want
 
 
+@pytest.mark.parametrize("name,xy", list(degenerate_sets()) + [
+    ("all_equal_large", np.tile(np.array([[-7.0, 9.0]], np.float32), (20000, 1)))],
+    ids=lambda v: v if isinstance(v, str) else "")
+def test_no_prefilter_degenerate(gpu_lib, name, xy):
+    # case (1) on sets with duplicates, collinear points and equal keys; sets
+    # beyond the one-block path make their sort keys from the points (equal
+    # points: no sort pass moves anything and the keys are written apart)
+    import torch
+    cp = gpu_lib
+    d = torch.from_numpy(np.ascontiguousarray(xy)).cuda()
+    out, cnt, ws = cp.compute(d, cp.Options(no_prefilter=True))
+    torch.cuda.synchronize()
+    assert cp.device_status(ws) == (0, 0)
+    assert cp.as_index(out, int(cnt.item())).tolist() == oracle.hull(xy).tolist()
+
+
 def test_bounded_wait_timeout_reports_and_context_survives(gpu_lib):
     # A bounded device wait that nothing releases gives up, records the
     # timeout in the workspace status and returns; the context stays usable
