@@ -305,7 +305,7 @@ hull_status hull_compute(const float* d_xy, int64_t n, void* d_ws, size_t ws_byt
   const int64_t cap = compute_capacity(n);
   // The hull of the survivors.  With refinement the survivors in (ka, va)
   // are thinned into (kb, vb) first.  Sets up to SMALL_MAX points take the
-  // one-block path; larger ones one cooperative launch of the device radix
+  // small-set path; larger ones two cooperative launches of the device radix
   // sort (7 passes, ending in the other buffer) and the chunked chain (its
   // upper chains in the input).
   const bool refine = o.refine != 0 && !o.no_prefilter;

@@ -259,9 +259,10 @@ struct LargeJob {
   int64_t* out_n;
   int64_t cap;
 };
-// One cooperative launch over `table[0 .. *njobs)` (njobs in device memory),
-// or over `single` when table is null; bar = two zeroed words for the grid
-// barrier, bar_status = where a barrier timeout is recorded.
+// Two cooperative launches (the sort, then the chains) over
+// `table[0 .. *njobs)` (njobs in device memory), or over `single` when table
+// is null; bar = two zeroed words for the grid barrier, bar_status = where a
+// barrier timeout is recorded.
 cudaError_t launch_large(const LargeJob* table, const int* njobs, const LargeJob& single, uint32_t* bar,
                          uint32_t* bar_status, cudaStream_t st);
 cudaError_t launch_copy_count(WsHeader* h, int64_t* out, cudaStream_t st);

@@ -3,8 +3,9 @@
 // Andrew's monotone chain over the sorted keys, chunked (section 3, case (2):
 // the hull of the points that remain; the paper ran Qhull on the CPU there).
 //
-// One cooperative launch does the whole stage for a list of jobs (one per
-// point set), its phases separated by a grid barrier.  The sort runs one
+// Two cooperative launches do the whole stage for a list of jobs (one per
+// point set): the sort, then the chains, each phase's steps separated by a
+// grid barrier.  The sort runs one
 // sweep per 8-bit digit of the 52-bit keys that varies among them (at most
 // 7): each sweep reads and writes every element once, tiles finding their
 // output offsets by decoupled look-back (see sort_pass).  The chain is
@@ -15,7 +16,8 @@
 // is the hull.  Among equal keys the lowest index is kept.  Each chunk (or
 // group of chunk chains) is one warp's: it reads its input coalesced into
 // shared memory, its lanes chain short runs of it in parallel, and lane 0
-// walks only the vertices of those runs' chains (see window_chain).
+// (and lane 16, for the other side) walks only the vertices of those runs'
+// chains (see window_chain).
 //
 // Every size is read on the device.  A job whose count is at most SMALL_MAX
 // (the one-block path has written its result) or whose status word is set
