@@ -487,7 +487,10 @@ __global__ void __launch_bounds__(T3) k3_finish(const float* __restrict__ xyz, i
 // One thread per cell: its code (see Poly3), from the extreme values of
 // N.p - d over the cell's corners (the plane test is linear), the corners
 // clamped to the coordinate domain, so every product stays below 2^61.
-__global__ void __launch_bounds__(T3) k3_cells(Ws3* W, uint8_t* codes) {
+// masks[c] (cells with code CELL3_MANY): bit f set when some point of the
+// cell may fail facet f; every point of the cell is strictly inside the
+// facets whose bit is clear.
+__global__ void __launch_bounds__(T3) k3_cells(Ws3* W, uint8_t* codes, unsigned long long* masks) {
   __shared__ long long s_pl[MAXF3][4];
   __shared__ int s_meta[5];
   const int tid = threadIdx.x;
@@ -510,6 +513,7 @@ __global__ void __launch_bounds__(T3) k3_cells(Ws3* W, uint8_t* codes) {
     }
     uint8_t code = CELL3_IN;
     int unsure = 0, which = 0;
+    unsigned long long mask = 0;
     for (int f = 0; f < nf && code != CELL3_OUT; ++f) {
       long long mx = -s_pl[f][3], mn = -s_pl[f][3];
       for (int a = 0; a < 3; ++a) {
@@ -518,12 +522,13 @@ __global__ void __launch_bounds__(T3) k3_cells(Ws3* W, uint8_t* codes) {
         mn += min(p0, p1);
       }
       if (mn >= 0) code = CELL3_OUT;                  // every point fails facet f
-      else if (mx >= 0) { ++unsure; which = f; }     // some point may fail it
+      else if (mx >= 0) { ++unsure; which = f; mask |= 1ull << f; }  // some point may fail it
     }
     if (code != CELL3_OUT && lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2])
       code = unsure == 0 ? CELL3_IN : (unsure == 1 ? (uint8_t)(which + 1) : CELL3_MANY);
     if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]) code = CELL3_OUT;  // no point of the domain
     codes[c] = code;
+    if (code == CELL3_MANY) masks[c] = mask;
   }
 }
 
@@ -534,11 +539,33 @@ __global__ void __launch_bounds__(T3) k3_cells(Ws3* W, uint8_t* codes) {
 // coordinates floor((v - g) 2^-kc) by round-down operations, exact for these
 // integers.
 __device__ __forceinline__ uint32_t cell_code(const uint8_t* codes, float gx, float gy, float gz, float sc, float x,
-                                              float y, float z) {
+                                              float y, float z, int& cell) {
   const int cx = __float2int_rd(__fsub_rd(x, gx) * sc), cy = __float2int_rd(__fsub_rd(y, gy) * sc);
   const int cz = __float2int_rd(__fsub_rd(z, gz) * sc);
+  cell = 0;
   if ((unsigned)(cx | cy | cz) >= (unsigned)CG) return CELL3_OUT;  // outside the extremes' bounding box
-  return __ldg(codes + ((cz << (2 * CG_LOG)) | (cy << CG_LOG) | cx));
+  cell = (cz << (2 * CG_LOG)) | (cy << CG_LOG) | cx;
+  return __ldg(codes + cell);
+}
+
+// The facets of `mask` against one point (a CELL3_MANY cell: the point is
+// strictly inside every other facet): 2 * escalations + (survives ? 1 : 0).
+__device__ __noinline__ unsigned facets3_mask(const long long (*pl)[4], const float4* fc, const float* fe,
+                                              unsigned long long mask, float x, float y, float z) {
+  unsigned esc = 0;
+  while (mask) {
+    const int k = __ffsll((long long)mask) - 1;
+    mask &= mask - 1;
+    const float4 c = fc[k];
+    const float s = fmaf(c.x, x, fmaf(c.y, y, fmaf(c.z, z, c.w)));
+    const float e = fe[k];
+    if (s < -e) continue;
+    if (s > e) return 2 * esc + 1;
+    ++esc;
+    if (pl[k][0] * (long long)x + pl[k][1] * (long long)y + pl[k][2] * (long long)z - pl[k][3] >= 0)
+      return 2 * esc + 1;
+  }
+  return 2 * esc;
 }
 
 // Every facet of the polyhedron against one point: 2 * escalations +
@@ -564,7 +591,8 @@ __device__ __noinline__ unsigned facets3(const long long (*pl)[4], const float4*
 
 template <int FILTER>
 __global__ void __launch_bounds__(T3) k3_filter(const float* __restrict__ xyz, int64_t n, Ws3* W,
-                                                uint32_t* __restrict__ surv, const uint8_t* __restrict__ codes) {
+                                                uint32_t* __restrict__ surv, const uint8_t* __restrict__ codes,
+                                                const unsigned long long* __restrict__ masks) {
   __shared__ long long s_pl[MAXF3][4];
   __shared__ float4 s_fc[MAXF3];
   __shared__ float s_fe[MAXF3];
@@ -599,9 +627,15 @@ __global__ void __launch_bounds__(T3) k3_filter(const float* __restrict__ xyz, i
   auto survives = [&](float x, float y, float z) -> bool {
     if (nf == 0) return true;
     if (FILTER == HULL_FILTER_FP32) {
-      const uint32_t code = cell_code(codes, gx, gy, gz, sc, x, y, z);
+      int cell;
+      const uint32_t code = cell_code(codes, gx, gy, gz, sc, x, y, z, cell);
       if (code == CELL3_IN) return false;
       if (code == CELL3_OUT) return true;
+      if (code == CELL3_MANY) {
+        const unsigned r = facets3_mask(s_pl, s_fc, s_fe, __ldg(masks + cell), x, y, z);
+        esc += r >> 1;
+        return r & 1;
+      }
       if (code != CELL3_MANY) {
         const int f = (int)code - 1;
         const float4 c = s_fc[f];
@@ -691,7 +725,7 @@ constexpr size_t WS3_PARTIALS = align_up(sizeof(BlockBest) * 18 * (size_t)MAX_B3
 
 size_t ws3_bytes(int64_t n) {
   (void)n;
-  return WS3_HEADER + WS3_PARTIALS + align_up(CELLS3, 256);
+  return WS3_HEADER + WS3_PARTIALS + align_up(CELLS3, 256) + sizeof(unsigned long long) * (size_t)CELLS3;
 }
 
 }  // namespace
@@ -722,6 +756,7 @@ hull_status hull3_prefilter(const float* d_xyz, int64_t n, void* d_ws, size_t ws
   Ws3* W = static_cast<Ws3*>(d_ws);
   BlockBest* bres = reinterpret_cast<BlockBest*>(static_cast<char*>(d_ws) + WS3_HEADER);
   uint8_t* codes = static_cast<uint8_t*>(d_ws) + WS3_HEADER + WS3_PARTIALS;
+  auto* masks = reinterpret_cast<unsigned long long*>(codes + align_up(CELLS3, 256));
   stage_mark(0, st);
   if (cudaMemsetAsync(W, 0, sizeof(Ws3), st) != cudaSuccess) return HULL_ERR_CUDA;
   if (o.validate && n > 0) {
@@ -738,9 +773,9 @@ hull_status hull3_prefilter(const float* d_xyz, int64_t n, void* d_ws, size_t ws
     k3_extremes<A, F><<<(unsigned)G, T3, 0, st>>>(d_xyz, n, &W->status, bres);            \
     stage_mark(2, st);                                                                    \
     k3_finish<A><<<1, T3, 0, st>>>(d_xyz, n, G, W, bres, d_extreme_idx);                  \
-    if (F == HULL_FILTER_FP32) k3_cells<<<CELLS3 / T3, T3, 0, st>>>(W, codes);            \
+    if (F == HULL_FILTER_FP32) k3_cells<<<CELLS3 / T3, T3, 0, st>>>(W, codes, masks);     \
     stage_mark(3, st);                                                                    \
-    k3_filter<F><<<(unsigned)Gf, T3, 0, st>>>(d_xyz, n, W, d_survivor_idx, codes);        \
+    k3_filter<F><<<(unsigned)Gf, T3, 0, st>>>(d_xyz, n, W, d_survivor_idx, codes, masks); \
     stage_mark(4, st);                                                                    \
   } while (0)
   if (o.angles == HULL_ANGLES_CUMULATIVE) {
