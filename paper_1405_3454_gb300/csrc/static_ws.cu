@@ -22,7 +22,7 @@
 namespace {
 
 // The workspace of hull_compute for HULL_STATIC_MAX_POINTS points is
-// 26,740,480 bytes; the margin keeps the size a whole number of MiB.
+// 27,027,456 bytes; the margin keeps the size a whole number of MiB.
 constexpr size_t STATIC_SCRATCH_BYTES = size_t(26) << 20;
 
 static __device__ __align__(256) unsigned char g_scratch[STATIC_SCRATCH_BYTES];

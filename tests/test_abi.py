@@ -117,3 +117,12 @@ def test_graph_rejects_the_default_stream_before_any_cuda_call(lib):
     lib.hull_graph_counts(g, counts)
     assert list(counts) == [0, 0, 0, 0, 0, 0]
     lib.hull_graph_destroy(g)
+
+
+def test_static_entry_point_holds_its_largest_set(lib):
+    # hull_compute_static runs hull_compute on one fixed 26 MiB array per
+    # device: the workspace of its largest set must fit there, and one point
+    # more is refused before any CUDA call
+    assert cp.hull_workspace_bytes(cp.HULL_STATIC_MAX_POINTS) <= 26 << 20
+    P = 256 * 1024
+    assert lib.hull_compute_static(P, cp.HULL_STATIC_MAX_POINTS + 1, P, P, None, 0) == 6  # HULL_ERR_BUDGET
