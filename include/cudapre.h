@@ -137,8 +137,8 @@ hull_status hull_prefilter(const float* d_xy, int64_t n, void* d_ws, size_t ws_b
 /* The whole method on one point set: Steps 1-3, compaction of the survivors,
  * then the hull of the survivors (section 3, case (2)): a second discard
  * round (option refine; points strictly inside triangles of farthest
- * survivors), then up to 8192 points a hull built in one block or on the
- * whole GPU, more a device radix sort and Andrew's monotone chain.
+ * survivors), then up to 8192 points a hull classified on the whole GPU,
+ * more a device radix sort and Andrew's monotone chain.
  *   d_ws             at least hull_workspace_bytes(n).
  *   d_hull_idx       room for n uint32: hull vertex indices, see Hull above.
  *   d_n_hull         one int64: the number of hull vertices (0 when n == 0). */

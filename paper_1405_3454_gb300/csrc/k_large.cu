@@ -20,7 +20,7 @@
 // chains (see window_chain).
 //
 // Every size is read on the device.  A job whose count is at most SMALL_MAX
-// (the one-block path has written its result) or whose status word is set
+// (the small-set path has written its result) or whose status word is set
 // is skipped by every block alike.  Barrier and look-back waits are
 // bounded: on expiry the kernel records HULL_DEVICE_TIMEOUT and returns.
 #include "internal.cuh"
