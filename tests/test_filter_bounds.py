@@ -132,3 +132,24 @@ def test_edge_sign_decided_only_outside_the_bound():
                 assert orient < 0, (ax, ay, bx, by, px, py)
                 decided += 1
     assert decided > 1000
+
+
+def test_inner_box_compare_is_exact_for_lattice_points():
+    # The inside test's quick discard by the inner box: dx = fl(x - c) in
+    # float32 (x, c integers within +-2^24), then |dx| <= h with h an integer
+    # at most 2^24 - 1.  Whenever the float32 compare passes, the exact
+    # |x - c| <= h holds (a difference that rounds exceeds 2^24 > h), so no
+    # point outside the box is discarded.  Random cases plus the edges of the
+    # domain and of the rounding range.
+    rnd = random.Random(1405)
+    B = 1 << 24
+    edge = [-B, -B + 1, -B + 2, -1, 0, 1, B - 2, B - 1, B]
+    cases = [(x, c) for x in edge for c in edge]
+    cases += [(rnd.randint(-B, B), rnd.randint(-B, B)) for _ in range(20000)]
+    cases += [(c + d, c) for c in (-B, -B + 1, 0, B - 1) for d in range(-3, 4) if abs(c + d) <= B]
+    hs = [0, 1, 2, 1000, (1 << 23) + 1, B - 3, B - 2, B - 1]
+    for x, c in cases:
+        dx = abs(rn32(Fraction(x) - Fraction(c)))  # one float32 subtraction
+        for h in hs:
+            if dx <= h:
+                assert abs(x - c) <= h, (x, c, h)
